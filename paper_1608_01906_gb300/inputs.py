@@ -1,0 +1,231 @@
+"""Seeded synthetic inputs: meshes and initial fields.
+
+This module is shared by the CUDA library's callers and by the CPU oracle's
+callers.  It holds no arithmetic of the finite-element lattice Boltzmann method
+itself (no shape functions, no mass matrix, no equilibria); it only produces
+the raw inputs the method is run on:
+
+* node coordinates and P1 triangles (structured split, jittered Delaunay),
+* node tags for no-slip walls,
+* initial density / velocity / pressure fields (tanh droplet, Rayleigh-Taylor
+  layer with a single-mode perturbation).
+
+Conventions
+-----------
+* Coordinates are float64 ``(N, 2)``; triangles are int32 ``(T, 3)`` in
+  counter-clockwise order (positive signed area under the minimum-image rule of
+  the periodic box).
+* ``box = (Lx, Ly)``: a positive length marks a periodic direction, ``0`` a
+  non-periodic one.
+* ``node_tag`` is uint8 ``(N,)``: 0 = fluid node; ``k`` in 1..8 = wall node whose
+  inward normal is the D2Q9 direction ``k`` (1=(1,0), 2=(0,1), 3=(-1,0),
+  4=(0,-1), 5=(1,1), 6=(-1,1), 7=(-1,-1), 8=(1,-1)).
+
+The droplet profile is the flat-interface equilibrium of the free-energy model
+(tanh of width ``xi``, Sec. 2.1 "Lattice Boltzmann Method", constants beta and
+kappa); the Rayleigh-Taylor perturbation is the single-mode cosine of Sec. 3.4,
+restated in 2-D.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "structured_mesh",
+    "jittered_delaunay_mesh",
+    "droplet_fields",
+    "slab_fields",
+    "rayleigh_taylor_fields",
+    "shear_wave_fields",
+]
+
+
+def _wrap(d, L):
+    """Minimum-image difference along one axis (L <= 0: not periodic)."""
+    if L > 0:
+        return d - L * np.round(d / L)
+    return d
+
+
+def structured_mesh(nx, ny, h=1.0, periodic_x=True, periodic_y=True):
+    """Unit-square lattice of ``nx * ny`` nodes split into P1 triangles.
+
+    Node ``(i, j)`` has id ``i + nx * j`` and coordinates ``(i*h, j*h)``.  Each
+    square with lower-left corner ``(i, j)`` is cut along its diagonal from
+    ``(i, j)`` to ``(i+1, j+1)`` into the triangles
+    ``[(i,j), (i+1,j), (i+1,j+1)]`` and ``[(i,j), (i+1,j+1), (i,j+1)]``.
+    A periodic direction wraps the last column / row onto the first; a
+    non-periodic y direction tags row 0 as a wall with inward normal +y
+    (tag 2) and row ny-1 with inward normal -y (tag 4).
+
+    Returns ``(xy, tri, box, node_tag)``.
+    """
+    nx, ny = int(nx), int(ny)
+    if nx < 4 or ny < 4:
+        raise ValueError("structured_mesh needs at least 4 nodes per direction")
+    if not periodic_x:
+        raise ValueError("only periodic x is supported by the generator")
+    i, j = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+    xy = np.stack([i.ravel() * h, j.ravel() * h], axis=1).astype(np.float64)
+    sq_j = ny if periodic_y else ny - 1
+    si, sj = np.meshgrid(np.arange(nx), np.arange(sq_j), indexing="xy")
+    si = si.ravel()
+    sj = sj.ravel()
+    i1 = (si + 1) % nx
+    j1 = (sj + 1) % ny
+    a = si + nx * sj
+    b = i1 + nx * sj
+    c = i1 + nx * j1
+    d = si + nx * j1
+    lower = np.stack([a, b, c], axis=1)
+    upper = np.stack([a, c, d], axis=1)
+    tri = np.empty((2 * len(a), 3), dtype=np.int32)
+    tri[0::2] = lower
+    tri[1::2] = upper
+    box = np.array([nx * h, ny * h if periodic_y else 0.0])
+    tag = np.zeros(nx * ny, dtype=np.uint8)
+    if not periodic_y:
+        tag[:nx] = 2
+        tag[nx * (ny - 1):] = 4
+    return xy, tri, box, tag
+
+
+def _incircle(ax, ay, bx, by, cx, cy, dx, dy):
+    """> 0 when d lies strictly inside the circumcircle of CCW triangle abc."""
+    adx, ady = ax - dx, ay - dy
+    bdx, bdy = bx - dx, by - dy
+    cdx, cdy = cx - dx, cy - dy
+    return ((adx * adx + ady * ady) * (bdx * cdy - cdx * bdy)
+            - (bdx * bdx + bdy * bdy) * (adx * cdy - cdx * ady)
+            + (cdx * cdx + cdy * cdy) * (adx * bdy - bdx * ady))
+
+
+def jittered_delaunay_mesh(nx, ny, jitter=0.25, seed=1608, h=1.0):
+    """Periodic ``nx * ny`` point set jittered uniformly by ``+-jitter*h``.
+
+    The points start on the unit lattice; each is moved by independent uniform
+    offsets drawn from ``numpy.random.default_rng(seed)``.  The triangulation
+    starts as the structured split of :func:`structured_mesh` (valid for
+    ``jitter < 0.5``) and Lawson edge flips are applied, with the in-circle
+    test evaluated on minimum-image coordinates, until no interior edge is
+    strictly non-Delaunay (ties keep their edge).
+
+    Returns ``(xy, tri, box, node_tag)`` with coordinates wrapped into the box.
+    """
+    if not (0.0 <= jitter < 0.5):
+        raise ValueError("jitter must lie in [0, 0.5)")
+    xy0, tri, box, tag = structured_mesh(nx, ny, h, True, True)
+    rng = np.random.default_rng(seed)
+    xy = xy0 + rng.uniform(-jitter * h, jitter * h, size=xy0.shape)
+    xy[:, 0] %= box[0]
+    xy[:, 1] %= box[1]
+    tri = [list(t) for t in tri.tolist()]
+    Lx, Ly = box
+
+    def rel(o, p):
+        return (_wrap(xy[p, 0] - xy[o, 0], Lx), _wrap(xy[p, 1] - xy[o, 1], Ly))
+
+    # edge -> (triangle, local index of the edge's first vertex); edge (u, v) is
+    # the directed edge t[k] -> t[k+1] of triangle t.
+    def build_edges():
+        e = {}
+        for ti, t in enumerate(tri):
+            for k in range(3):
+                e[(t[k], t[(k + 1) % 3])] = ti
+        return e
+
+    edges = build_edges()
+    queue = list(edges.keys())
+    flips = 0
+    while queue:
+        u, v = queue.pop()
+        t1 = edges.get((u, v))
+        t2 = edges.get((v, u))
+        if t1 is None or t2 is None:
+            continue
+        A = tri[t1]
+        B = tri[t2]
+        c = [p for p in A if p != u and p != v][0]
+        d = [p for p in B if p != u and p != v][0]
+        # coordinates relative to u: triangle (u, v, c) is CCW
+        vx, vy = rel(u, v)
+        cx, cy = rel(u, c)
+        dx, dy = rel(u, d)
+        if _incircle(0.0, 0.0, vx, vy, cx, cy, dx, dy) <= 0.0:
+            continue
+        # flip edge (u, v) -> (c, d): new CCW triangles (u, d, c) and (d, v, c)
+        for t in (A, B):
+            for k in range(3):
+                edges.pop((t[k], t[(k + 1) % 3]), None)
+        tri[t1] = [u, d, c]
+        tri[t2] = [d, v, c]
+        for ti in (t1, t2):
+            t = tri[ti]
+            for k in range(3):
+                edges[(t[k], t[(k + 1) % 3])] = ti
+        queue.extend([(u, d), (d, v), (v, c), (c, u)])
+        flips += 1
+    tri = np.asarray(tri, dtype=np.int32)
+    return xy, tri, box, tag
+
+
+def _min_image_delta(xy, center, box):
+    dx = _wrap(xy[:, 0] - center[0], box[0])
+    dy = _wrap(xy[:, 1] - center[1], box[1])
+    return dx, dy
+
+
+def droplet_fields(xy, box, center, radius, rho_l, rho_v, xi, u0=(0.0, 0.0)):
+    """Circular liquid drop of radius ``radius`` in vapour.
+
+    ``rho0(r) = (rho_l + rho_v)/2 + (rho_l - rho_v)/2 * tanh(2 (R - r) / xi)``
+    with ``r`` the minimum-image distance to ``center``; uniform velocity ``u0``
+    and zero pressure.  Returns ``(rho0, u0 (N,2), p0)`` as float64.
+    """
+    dx, dy = _min_image_delta(xy, center, box)
+    r = np.sqrt(dx * dx + dy * dy)
+    rho = 0.5 * (rho_l + rho_v) + 0.5 * (rho_l - rho_v) * np.tanh(2.0 * (radius - r) / xi)
+    u = np.zeros((len(xy), 2))
+    u[:, 0] = u0[0]
+    u[:, 1] = u0[1]
+    return rho, u, np.zeros(len(xy))
+
+
+def slab_fields(xy, box, y_lo, y_hi, rho_l, rho_v, xi):
+    """Flat liquid slab ``y_lo < y < y_hi`` (two tanh interfaces), u = 0, p = 0."""
+    y = xy[:, 1]
+    rho = (rho_v + 0.5 * (rho_l - rho_v)
+           * (np.tanh(2.0 * (y - y_lo) / xi) - np.tanh(2.0 * (y - y_hi) / xi)))
+    return rho, np.zeros((len(xy), 2)), np.zeros(len(xy))
+
+
+def rayleigh_taylor_fields(xy, width, height, rho_heavy, rho_light, xi, amplitude, g):
+    """Heavy fluid on top of light fluid, interface ``H/2 + A cos(2 pi x / W)``.
+
+    Density is the tanh profile across the perturbed interface, velocity is
+    zero and the pressure is hydrostatic for gravity ``(0, -g)``: integrated
+    column by column downward from the top row with the trapezoid rule, so
+    that ``dp/dy = -rho g``.  Nodes must lie on the structured lattice
+    (columns of equal x).  Returns ``(rho0, u0, p0)``.
+    """
+    x = xy[:, 0]
+    y = xy[:, 1]
+    yi = 0.5 * (height - 1) + amplitude * np.cos(2.0 * np.pi * x / width)
+    rho = (0.5 * (rho_heavy + rho_light)
+           + 0.5 * (rho_heavy - rho_light) * np.tanh(2.0 * (y - yi) / xi))
+    nx = int(round(width))
+    ny = len(xy) // nx
+    r2 = rho.reshape(ny, nx)
+    y2 = y.reshape(ny, nx)
+    p2 = np.zeros_like(r2)
+    for j in range(ny - 2, -1, -1):
+        dy = y2[j + 1] - y2[j]
+        p2[j] = p2[j + 1] + 0.5 * g * (r2[j] + r2[j + 1]) * dy
+    return rho, np.zeros((len(xy), 2)), p2.ravel()
+
+
+def shear_wave_fields(xy, box, rho, amplitude):
+    """Uniform density, ``u_x = U sin(2 pi y / Ly)``, ``u_y = 0``, p = 0."""
+    u = np.zeros((len(xy), 2))
+    u[:, 0] = amplitude * np.sin(2.0 * np.pi * xy[:, 1] / box[1])
+    return np.full(len(xy), float(rho)), u, np.zeros(len(xy))

@@ -1,0 +1,310 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test would fail under a plausible slip in the oracle: a dropped term,
+a wrong sign or factor, a transposed operand, a wrong lumping or weight.
+* dense brute force: M, C_e, D_e assembled by Gauss quadrature from
+  shape functions obtained by solving the nodal interpolation system
+  (Sec. 2.2.1, Eqs. galerkin_lbm, fem_matrices) on tiny meshes;
+* streaming invariants: constants, lumped-mass conservation, exact
+  translation of linear fields at interior nodes;
+* recovery (Sec. 2.3): exact for linear fields, second-order convergence;
+* the tanh profile of width xi is the equilibrium fixed by beta and kappa
+  (Sec. 2.1): mu on it vanishes as h -> 0;
+* D2Q9 moment identities of the equilibria and sources (Eqs. f_eq, g_eq, F,
+  G and the exact-difference force);
+* whole step: mass and momentum conservation, stationarity of uniform
+  states, gravity-driven uniform acceleration, shear-wave decay at
+  nu = c_s^2 tau dt (Sec. 2.1).
+"""
+import numpy as np
+import pytest
+
+from oracle.oracle import EX, EY, W, Oracle, Params
+from paper_1608_01906_gb300 import inputs
+
+CS2 = 1.0 / 3.0
+DIRS = list(zip(EX, EY))
+
+
+def nonperiodic_grid(nx, ny, h=1.0, jitter=0.0, seed=0):
+    """Unit lattice without wrap-around; optional interior jitter."""
+    i, j = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+    xy = np.stack([i.ravel() * h, j.ravel() * h], 1).astype(float)
+    if jitter:
+        rng = np.random.default_rng(seed)
+        inner = (i.ravel() > 0) & (i.ravel() < nx - 1) & (j.ravel() > 0) & (j.ravel() < ny - 1)
+        xy[inner] += rng.uniform(-jitter * h, jitter * h, size=(inner.sum(), 2))
+    tris = []
+    for b in range(ny - 1):
+        for a in range(nx - 1):
+            p, q, r, s = a + nx * b, a + 1 + nx * b, a + 1 + nx * (b + 1), a + nx * (b + 1)
+            tris += [(p, q, r), (p, r, s)]
+    boundary = (xy[:, 0] < 0.5 * h) | (xy[:, 0] > (nx - 1.5) * h) | (xy[:, 1] < 0.5 * h) | (
+        xy[:, 1] > (ny - 1.5) * h)
+    return xy, np.array(tris, dtype=np.int32), np.zeros(2), boundary
+
+
+def oracle_for(xy, tri, box, **kw):
+    return Oracle(xy, tri, box, None, Params(**kw))
+
+
+# ---------------------------------------------------------------- geometry
+def test_geometry_areas_and_lumped_mass():
+    xy, tri, box, tag = inputs.structured_mesh(8, 6)
+    o = oracle_for(xy, tri, box)
+    assert np.allclose(o.area, 0.5) and np.allclose(o.mass, 1.0)
+    xy, tri, box, tag = inputs.jittered_delaunay_mesh(12, 10, 0.25, seed=3)
+    o = oracle_for(xy, tri, box)
+    assert (o.area > 0).all()
+    assert o.area.sum() == pytest.approx(box[0] * box[1], rel=1e-13)
+    assert o.mass.sum() == pytest.approx(box[0] * box[1], rel=1e-13)
+
+
+# ------------------------------------------------- dense quadrature brute force
+def dense_operators(xy, tri, box, e):
+    """Consistent M, C_e, D_e by 3-point Gauss quadrature of explicit P1
+    shape functions (coefficients from solving [1 x y] c = delta)."""
+    N = len(xy)
+    M = np.zeros((N, N))
+    Cm = np.zeros((N, N))
+    D = np.zeros((N, N))
+    e = np.asarray(e, float)
+    bary = np.array([[2 / 3, 1 / 6, 1 / 6], [1 / 6, 2 / 3, 1 / 6], [1 / 6, 1 / 6, 2 / 3]])
+    for t in tri:
+        p = xy[t].copy()
+        for k in (1, 2):  # minimum image relative to the first vertex
+            for d in (0, 1):
+                if box[d] > 0:
+                    p[k, d] = p[0, d] + (p[k, d] - p[0, d]) - box[d] * np.round(
+                        (p[k, d] - p[0, d]) / box[d])
+        V = np.column_stack([np.ones(3), p])
+        coef = np.linalg.solve(V, np.eye(3))  # column a: N_a = c0 + c1 x + c2 y
+        area = 0.5 * abs(np.linalg.det(V))
+        grads = coef[1:, :].T  # (3, 2)
+        for q in range(3):
+            x = bary[q] @ p
+            Nv = coef[0] + coef[1] * x[0] + coef[2] * x[1]
+            wq = area / 3
+            for a in range(3):
+                for b in range(3):
+                    M[t[a], t[b]] += wq * Nv[a] * Nv[b]
+                    Cm[t[a], t[b]] += wq * Nv[a] * (e @ grads[b])
+                    D[t[a], t[b]] += wq * 0.5 * (e @ grads[a]) * (e @ grads[b])
+    return M, Cm, D
+
+
+@pytest.mark.parametrize("mesh", ["structured", "delaunay", "open"])
+def test_stream_matches_dense_quadrature(mesh):
+    if mesh == "structured":
+        xy, tri, box, _ = inputs.structured_mesh(5, 4)
+    elif mesh == "delaunay":
+        xy, tri, box, _ = inputs.jittered_delaunay_mesh(6, 5, 0.25, seed=11)
+    else:
+        xy, tri, box, _ = nonperiodic_grid(5, 5, jitter=0.2, seed=5)
+    dt = 0.37
+    o = oracle_for(xy, tri, box, dt=dt)
+    rng = np.random.default_rng(1)
+    psi = rng.normal(size=len(xy))
+    for e in DIRS:
+        M, Cm, D = dense_operators(xy, tri, box, e)
+        ML = M.sum(axis=1)  # lumped mass: row sums of the consistent mass
+        ref = psi + (-dt * Cm @ psi - dt * dt * D @ psi) / ML
+        got = o.stream(e, psi)
+        assert np.max(np.abs(got - ref)) <= 1e-12 * max(1.0, np.abs(ref).max()), e
+
+
+def test_stream_invariants():
+    xy, tri, box, _ = inputs.jittered_delaunay_mesh(10, 9, 0.25, seed=4)
+    o = oracle_for(xy, tri, box, dt=0.3)
+    rng = np.random.default_rng(2)
+    psi = rng.uniform(size=len(xy))
+    for e in DIRS:
+        out = o.stream(e, np.full(len(xy), 0.7))
+        assert np.max(np.abs(out - 0.7)) <= 1e-14
+        out = o.stream(e, psi)
+        assert abs(o.mass @ out - o.mass @ psi) <= 1e-13 * (o.mass @ psi)
+
+
+def test_stream_translates_linear_fields_at_interior_nodes():
+    xy, tri, box, boundary = nonperiodic_grid(7, 6, jitter=0.2, seed=9)
+    dt = 0.45
+    o = oracle_for(xy, tri, box, dt=dt)
+    b = np.array([0.3, -1.1])
+    psi = 2.0 + xy @ b
+    for e in DIRS:
+        out = o.stream(e, psi)
+        want = psi - dt * (np.asarray(e) @ b)
+        assert np.max(np.abs(out[~boundary] - want[~boundary])) <= 1e-13
+
+
+# -------------------------------------------------------------- recovery
+def test_recovery_exact_for_linear_fields():
+    xy, tri, box, _ = nonperiodic_grid(6, 7, jitter=0.25, seed=8)
+    o = oracle_for(xy, tri, box)
+    gx, gy = o.recover(1.5 - 0.25 * xy[:, 0] + 0.75 * xy[:, 1])
+    assert np.max(np.abs(gx + 0.25)) <= 1e-13 and np.max(np.abs(gy - 0.75)) <= 1e-13
+
+
+def test_recovery_and_laplacian_second_order():
+    errs_g, errs_l = [], []
+    for n in (32, 64, 128):
+        h = 64.0 / n
+        xy, tri, box, _ = inputs.structured_mesh(n, n, h=h)
+        o = oracle_for(xy, tri, box)
+        k = 2 * np.pi / 64
+        f = np.sin(k * xy[:, 0]) * np.cos(2 * k * xy[:, 1])
+        gx, gy = o.recover(f)
+        lap = o.recover(gx)[0] + o.recover(gy)[1]
+        errs_g.append(np.abs(gx - k * np.cos(k * xy[:, 0]) * np.cos(2 * k * xy[:, 1])).max())
+        errs_l.append(np.abs(lap + 5 * k * k * f).max())
+    for e in (errs_g, errs_l):
+        r1, r2 = e[0] / e[1], e[1] / e[2]
+        assert 3.6 < r1 < 4.4 and 3.6 < r2 < 4.4, e
+
+
+def test_tanh_profile_is_the_equilibrium():
+    # mu = mu_phi - kappa lap rho vanishes on the tanh profile of width xi
+    # only if kappa/beta = xi^2 (rho_l - rho_v)^2 / 8 (Sec. 2.1); refinement
+    # drives it to zero at second order.
+    mus = []
+    for n in (64, 128, 256):
+        h = 64.0 / n
+        xy, tri, box, _ = inputs.structured_mesh(n, 8, h=h)
+        o = oracle_for(xy, tri, box, rho_l=1.0, rho_v=0.1, sigma=0.01, xi=4.0)
+        # flat interfaces normal to x
+        x = xy[:, 0]
+        rho = 0.1 + 0.45 * (np.tanh(2 * (x - 16) / 4.0) - np.tanh(2 * (x - 48) / 4.0))
+        mus.append(np.abs(o.fields_of(rho)["mu"]).max())
+    beta = 12 * 0.01 / (4.0 * 0.9 ** 4)
+    scale = beta * 0.9 ** 3  # magnitude of mu_phi across the interface
+    assert mus[-1] < 0.02 * scale
+    assert mus[0] / mus[1] > 3.0 and mus[1] / mus[2] > 3.0, mus
+
+
+def test_stress_force_integrates_to_laplace_jump():
+    # kappa [d_i |grad rho|^2 - d_j (d_i rho d_j rho)] of a circular tanh drop
+    # integrates radially to -sigma/R in 2-D (Laplace's law, Sec. 3.1).
+    n, R = 128, 32.0
+    xy, tri, box, _ = inputs.structured_mesh(n, n)
+    o = oracle_for(xy, tri, box, rho_l=1.0, rho_v=0.1, sigma=0.01, xi=8.0)
+    rho0, _, _ = inputs.droplet_fields(xy, box, (64, 64), R, 1.0, 0.1, 8.0)
+    f = o.fields_of(rho0)
+    row = (xy[:, 1] == 64) & (xy[:, 0] >= 64)
+    integral = np.trapezoid(f["Kx"][row]) if hasattr(np, "trapezoid") else np.trapz(f["Kx"][row])
+    assert integral == pytest.approx(-0.01 / R, rel=0.03)
+
+
+# ------------------------------------------------------ local identities
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_equilibria_and_source_moments(seed):
+    rng = np.random.default_rng(seed)
+    xy, tri, box, _ = inputs.structured_mesh(4, 4)
+    dt = rng.uniform(0.2, 1.0)
+    g = rng.normal(size=2) * 1e-2
+    o = Oracle(xy, tri, box, None, Params(dt=dt, gravity=tuple(g)))
+    rho = rng.uniform(0.1, 1.0)
+    p = rng.normal() * 1e-2
+    u = rng.normal(size=2) * 0.05
+    dr = rng.normal(size=2)
+    dm = rng.normal(size=2) * 1e-2
+    K = rng.normal(size=2) * 1e-3
+    t = o.local_terms(rho, p, u, dr, dm, K)
+    E = np.stack([EX, EY])
+    # equilibria (Eqs. f_eq, g_eq)
+    assert t["heq"].sum() == pytest.approx(rho, rel=1e-14)
+    assert np.allclose(E @ t["heq"], rho * u, atol=1e-15)
+    P2 = (E * t["heq"]) @ E.T / rho
+    assert np.allclose(P2, CS2 * np.eye(2) + np.outer(u, u), atol=1e-15)
+    assert t["geq"].sum() == pytest.approx(p / CS2, abs=1e-15)
+    assert np.allclose(E @ t["geq"], rho * u, atol=1e-15)
+    # F (Eq. F): zero mass, first moment dt/2 (c_s^2 grad rho - rho grad mu)
+    assert abs(t["F"].sum()) <= 1e-15
+    assert np.allclose(E @ t["F"], 0.5 * dt * (CS2 * dr - rho * dm), atol=1e-14)
+    # G (Eq. G): zeroth moment dt/2 u.grad rho, first moment dt/2 K
+    assert t["G"].sum() == pytest.approx(0.5 * dt * u @ dr, abs=1e-14)
+    assert np.allclose(E @ t["G"], 0.5 * dt * K, atol=1e-15)
+    # exact-difference force: no mass, first moment rho g dt / 2
+    assert abs(t["B"].sum()) <= 1e-15
+    assert np.allclose(E @ t["B"], 0.5 * rho * g * dt, atol=1e-15)
+
+
+# -------------------------------------------------------------- whole step
+def droplet_oracle(mesh, ratio=10.0, **kw):
+    xy, tri, box, tag = mesh
+    n = np.sqrt(box[0] * box[1])
+    o = Oracle(xy, tri, box, tag, Params(rho_l=1.0, rho_v=1.0 / ratio, **kw))
+    rho0, u0, p0 = inputs.droplet_fields(xy, box, (box[0] / 2, box[1] / 2), n / 4, 1.0,
+                                         1.0 / ratio, 4.0)
+    o.init(rho0, u0, p0)
+    return o
+
+
+@pytest.mark.parametrize("kind", ["structured", "delaunay"])
+def test_step_conserves_mass_and_momentum(kind):
+    mesh = (inputs.structured_mesh(40, 40) if kind == "structured"
+            else inputs.jittered_delaunay_mesh(40, 40, 0.25, seed=1608))
+    o = droplet_oracle(mesh, ratio=10.0)
+    m0, _, _ = o.totals()
+    o.step(300)
+    m1, px, py = o.totals()
+    assert abs(m1 - m0) <= 1e-13 * m0
+    assert abs(px) <= 1e-13 * m0 and abs(py) <= 1e-13 * m0
+
+
+def test_uniform_states_are_stationary():
+    xy, tri, box, tag = inputs.jittered_delaunay_mesh(12, 12, 0.25, seed=2)
+    o = Oracle(xy, tri, box, tag, Params(rho_l=1.0, rho_v=0.1))
+    N = len(xy)
+    u0 = np.tile([0.05, -0.02], (N, 1))
+    o.init(np.full(N, 1.0), u0, np.full(N, 0.01))
+    o.step(50)
+    assert np.max(np.abs(o.rho - 1.0)) <= 1e-13
+    assert np.max(np.abs(o.ux - 0.05)) <= 1e-13 and np.max(np.abs(o.uy + 0.02)) <= 1e-13
+    assert np.max(np.abs(o.p - 0.01)) <= 1e-13
+
+
+def test_gravity_accelerates_uniform_fluid():
+    # periodic, uniform rho: only the body force acts; rho u grows by rho g dt
+    # per step (exact-difference force + dt/2 rho g term of Eq. velocity).
+    xy, tri, box, tag = inputs.structured_mesh(8, 8)
+    g = (2e-5, -1e-5)
+    o = Oracle(xy, tri, box, tag, Params(rho_l=1.0, rho_v=0.1, dt=0.5, gravity=g))
+    N = len(xy)
+    o.init(np.full(N, 1.0), np.zeros((N, 2)), np.zeros(N))
+    n = 40
+    o.step(n)
+    assert np.allclose(o.ux, g[0] * n * 0.5, rtol=1e-10, atol=1e-16)
+    assert np.allclose(o.uy, g[1] * n * 0.5, rtol=1e-10, atol=1e-16)
+
+
+@pytest.mark.parametrize("tau", [0.5, 0.2])
+def test_shear_wave_decays_at_model_viscosity(tau):
+    # single phase (sigma = 0, uniform rho): u_x = U sin(2 pi y / L) decays
+    # as exp(-nu k^2 t), nu = c_s^2 tau dt (Sec. 2.1).
+    L, dt = 64, 0.5
+    xy, tri, box, tag = inputs.structured_mesh(L, L)
+    o = Oracle(xy, tri, box, tag,
+               Params(rho_l=1.0, rho_v=0.5, sigma=0.0, tau_l=tau, tau_v=tau, dt=dt))
+    rho0, u0, p0 = inputs.shear_wave_fields(xy, box, 1.0, 1e-4)
+    o.init(rho0, u0, p0)
+    s = np.sin(2 * np.pi * xy[:, 1] / L)
+    a0 = (o.ux @ s) / (s @ s)
+    steps = 400
+    o.step(steps)
+    a1 = (o.ux @ s) / (s @ s)
+    rate = -np.log(a1 / a0) / (steps * dt)
+    nu = CS2 * tau * dt
+    assert rate == pytest.approx(nu * (2 * np.pi / L) ** 2, rel=0.01)
+
+
+def test_flat_interface_holds_no_pressure_jump():
+    # a flat slab carries no Laplace pressure: p is equal in both bulk phases
+    xy, tri, box, tag = inputs.structured_mesh(32, 64)
+    o = Oracle(xy, tri, box, tag, Params(rho_l=1.0, rho_v=0.1))
+    rho0, u0, p0 = inputs.slab_fields(xy, box, 16, 48, 1.0, 0.1, 4.0)
+    o.init(rho0, u0, p0)
+    o.step(1500)
+    y = xy[:, 1]
+    p_liq = o.p[(y > 28) & (y < 36)].mean()
+    p_vap = o.p[(y < 4) | (y > 60)].mean()
+    assert abs(p_liq - p_vap) < 0.02 * 0.01 / 16  # < 2% of the droplet-case jump
