@@ -1,0 +1,172 @@
+/*
+ * felbm.h -- C ABI of the GB300 finite-element lattice Boltzmann library for
+ * binary fluids (Lee-Lin free-energy model, D2Q9 populations on a 2-D P1
+ * triangle mesh).
+ *
+ * One time step (felbm_step) is the scheme of Sec. 2.2 of Matin, Misztal,
+ * Hernandez-Garcia, Mathiesen, "Evaluation of the Finite Element Lattice
+ * Boltzmann Method for Binary Fluid Flows":
+ *   1. Taylor-Galerkin streaming of the stored pre-collided distributions h
+ *      (the paper's f, zeroth moment rho) and g (pressure/momentum), P1
+ *      Bubnov-Galerkin with the lumped mass matrix (Sec. 2.2.1, Eqs.
+ *      local_formulation, galerkin_lbm, fem_matrices);
+ *   2. bounce-back at wall nodes (Sec. 3.3, no-slip by bounce-back);
+ *   3. rho, recovered grad rho, Laplacian of rho, stress force, chemical
+ *      potential mu = mu_phi - kappa lap rho and its recovered gradient
+ *      (Sec. 2.1 and Sec. 2.3);
+ *   4. velocity and pressure moments (Eqs. velocity, pressure);
+ *   5. post-streaming collision (Eqs. lbmf_post, lbmg_post) followed by the
+ *      pre-streaming collision of the next step (Eqs. lbmf_pre, lbmg_pre)
+ *      with forcing F (Eq. F), G (Eq. G) and the exact-difference body force.
+ *
+ * Conventions shared by every entry point
+ *   - All host arrays are C-contiguous, in the caller's node numbering.  The
+ *     library copies every input it needs; the caller keeps ownership of all
+ *     arrays it passes and may free them after the call returns.
+ *   - Handles are opaque, owned by the library, and released only by the
+ *     matching *_destroy call.  A state borrows its mesh: the mesh must
+ *     outlive every state created on it.
+ *   - Every int-returning call returns FELBM_OK (0) or a negative
+ *     felbm_status code; no call aborts, traps or exits.  A failed call leaves
+ *     its output handle untouched.
+ *   - D2Q9 population order: e_0 = (0,0), e_1 = (1,0), e_2 = (0,1),
+ *     e_3 = (-1,0), e_4 = (0,-1), e_5 = (1,1), e_6 = (-1,1), e_7 = (-1,-1),
+ *     e_8 = (1,-1); weights 4/9, 1/9 (1..4), 1/36 (5..8); c_s^2 = 1/3.
+ *   - Work is issued on the CUDA stream given at mesh creation (NULL = the
+ *     legacy default stream).  felbm_step returns after enqueueing; errors
+ *     detected on the device (non-finite values) are reported by the next
+ *     synchronising call (felbm_state_sync, felbm_moments_get,
+ *     felbm_state_export).
+ */
+#ifndef FELBM_H
+#define FELBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum felbm_status {
+    FELBM_OK = 0,
+    FELBM_ERR_INVALID_ARG = -1,  /* NULL handle/pointer, size out of range, bad flag */
+    FELBM_ERR_INVALID_MESH = -2, /* index out of range, non-positive area, isolated node, bad tag */
+    FELBM_ERR_OOM = -3,          /* device or host allocation refused */
+    FELBM_ERR_NONFINITE = -4,    /* a NaN/Inf moment was produced by an earlier step */
+    FELBM_ERR_TIMEOUT = -5,      /* a bounded device-side wait gave up */
+    FELBM_ERR_CUDA = -6,         /* any other CUDA runtime error */
+    FELBM_ERR_UNSUPPORTED = -7   /* valid request this build does not serve */
+} felbm_status;
+
+/* mesh flags */
+#define FELBM_PERIODIC_X 0x1u   /* box[0] > 0 is the period in x */
+#define FELBM_PERIODIC_Y 0x2u   /* box[1] > 0 is the period in y */
+#define FELBM_MESH_GENERAL 0x4u /* never use the structured-lattice kernels */
+
+/* precision of the stored distributions and of the bulk arithmetic */
+#define FELBM_FP64 0
+#define FELBM_FP32 1
+
+typedef struct felbm_mesh felbm_mesh;
+typedef struct felbm_state felbm_state;
+typedef struct felbm_batch felbm_batch;
+
+/* Physical parameters (Sec. 2.1).  beta = 12 sigma / (xi drho^4) and
+ * kappa = 3 xi sigma / (2 drho^2) with drho = rho_l - rho_v; the relaxation
+ * parameter is the C-weighted harmonic mean of tau_l and tau_v; the kinematic
+ * viscosity is nu = c_s^2 tau dt.  dt is in the mesh's length unit per unit
+ * lattice speed (|e| = 1).  gravity is the body-force acceleration applied by
+ * the exact-difference method with du = g dt.  Requirements: rho_l > rho_v > 0,
+ * sigma >= 0, xi > 0, tau_l > 0, tau_v > 0, dt > 0, all finite. */
+typedef struct felbm_params {
+    double rho_l, rho_v;
+    double sigma, xi;
+    double tau_l, tau_v;
+    double dt;
+    double gravity[2];
+    int32_t precision; /* FELBM_FP64 or FELBM_FP32 */
+    int32_t flags;     /* must be 0 */
+} felbm_params;
+
+/* Create a device-resident mesh (Sec. 2.2.1 P1 elements, Sec. 2.3 recovery).
+ *   xy        host, n_nodes x 2 doubles (x, y), node coordinates.
+ *   tri       host, n_tri x 3 int32 node ids, counter-clockwise: every
+ *             triangle must have positive area once its second and third
+ *             vertex are mapped to the minimum image of the first.
+ *   box       host, 2 doubles: period in x and y; read only for the
+ *             directions flagged periodic.  Every element edge must be shorter
+ *             than half the period.
+ *   flags     FELBM_PERIODIC_X | FELBM_PERIODIC_Y | FELBM_MESH_GENERAL.
+ *   node_tag  host, n_nodes uint8 or NULL: 0 = fluid; k in 1..8 = no-slip
+ *             wall node whose inward normal is e_k.
+ *   stream    cudaStream_t (as void*) all work of this mesh and its states is
+ *             issued on; NULL = legacy default stream.
+ * The library computes element geometry, the lumped mass, the assembled
+ * streaming/recovery coefficients and an internal node order (reverse
+ * Cuthill-McKee); a mesh that is the structured split of a unit lattice
+ * (node i at ((i mod nx) h, (i div nx) h), each square cut along its
+ * (i,j)-(i+1,j+1) diagonal, periodic in x, periodic or walled in y) is served
+ * by the structured-lattice kernels unless FELBM_MESH_GENERAL is set.
+ * Errors: INVALID_ARG (NULL pointers, n_nodes < 3, n_tri < 1, sizes above
+ * 2^31-1), INVALID_MESH, OOM, CUDA. */
+int felbm_mesh_create(const double *xy, int64_t n_nodes, const int32_t *tri, int64_t n_tri,
+                      const double box[2], uint32_t flags, const uint8_t *node_tag,
+                      void *stream, felbm_mesh **out);
+
+/* Mesh facts.  Any output pointer may be NULL.  kind: 0 = general
+ * (unstructured CSR kernels), 1 = structured lattice.  device_bytes: device
+ * memory held by the mesh. */
+int felbm_mesh_info(const felbm_mesh *mesh, int64_t *n_nodes, int64_t *n_tri, int32_t *kind,
+                    int64_t *device_bytes);
+
+void felbm_mesh_destroy(felbm_mesh *mesh);
+
+/* Create a state and initialise it (Sec. 2.2): from rho0, u0, p0 the library
+ * computes grad rho, the stress force and grad mu, takes the post-collision
+ * distributions to be the equilibria h_eq = rho Gamma(u), g_eq (Eqs. f_eq,
+ * g_eq), and stores the pre-collided values psi_eq + source.
+ *   rho0  host, n_nodes doubles, > 0.
+ *   u0    host, n_nodes x 2 doubles (ux, uy) or NULL for rest.
+ *   p0    host, n_nodes doubles or NULL for zero pressure.
+ * Device memory: 2 x 18 n_nodes values of the chosen precision plus scratch.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+int felbm_state_init(const felbm_mesh *mesh, const felbm_params *params, const double *rho0,
+                     const double *u0, const double *p0, felbm_state **out);
+
+/* Advance n_steps >= 0 time steps (asynchronous, on the mesh's stream).
+ * The moments of the last step are kept for felbm_moments_get. */
+int felbm_step(felbm_state *state, int64_t n_steps);
+
+/* Wait for the state's work and report FELBM_ERR_NONFINITE if any step
+ * produced a non-finite density, velocity or pressure. */
+int felbm_state_sync(felbm_state *state);
+
+/* Moments of the latest step (or of the initial fields before any step):
+ *   rho  n_nodes doubles, C n_nodes doubles ((rho - rho_v)/(rho_l - rho_v)),
+ *   u    n_nodes x 2 doubles, p n_nodes doubles,
+ *   totals 3 doubles: sum_i m_i rho_i, sum_i m_i rho_i ux_i, sum_i m_i rho_i uy_i
+ *   with m_i the lumped mass, accumulated in FP64 on the device.
+ * Host buffers, any may be NULL.  Synchronises the stream. */
+int felbm_moments_get(felbm_state *state, double *rho, double *C, double *u, double *p,
+                      double totals[3]);
+
+/* Checkpoint / restart of the stored pre-collided distributions: hbar and
+ * gbar are host arrays of 9 x n_nodes doubles, population-major
+ * (hbar[a * n_nodes + i]), FP64 on the host whatever the state's precision.
+ * Export synchronises the stream.  Import converts to the state's precision,
+ * clears the non-finite flag, and leaves the state without moments:
+ * felbm_moments_get returns FELBM_ERR_INVALID_ARG until the next felbm_step.
+ * Errors: INVALID_ARG (NULL pointers, non-finite imported value), CUDA. */
+int felbm_state_export(felbm_state *state, double *hbar, double *gbar);
+int felbm_state_import(felbm_state *state, const double *hbar, const double *gbar);
+
+void felbm_state_destroy(felbm_state *state);
+
+/* Short static description of a status code. */
+const char *felbm_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FELBM_H */

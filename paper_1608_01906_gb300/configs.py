@@ -1,0 +1,118 @@
+"""The five synthetic workloads and their physical parameters.
+
+Each workload is a seeded synthetic problem shaped like the paper's
+benchmarks (static droplet of Sec. 3.1, Rayleigh-Taylor layer of Sec. 3.4)
+restated in 2-D.  Readings fixed here (documented in the design notes):
+
+* dt = 0.5 in mesh units wherever a workload states dt = 1 on a unit-spacing
+  grid: the lumped Taylor-Galerkin streaming on the structured split is
+  unstable above Courant number 0.5 for the diagonal velocities that cross
+  the element diagonals (amplification 7 per step at dt = 1).  tau is the
+  dimensionless relaxation parameter (nu = c_s^2 tau dt), so "tau = 0.5" and
+  "dt = 10 tau" keep their meaning.
+* rho_l = 1, rho_v = rho_l / ratio; sigma = 0.01, xi = 4 unless stated.
+* "viscosity ratio 40" is a kinematic contrast nu_v / nu_l = 40 with the
+  larger relaxation parameter tau_v = 0.1 (dt = 10 tau), tau_l = 0.0025.
+* Rayleigh-Taylor: At = 0.5 -> rho_heavy = 1, rho_light = 1/3; lambda = W =
+  512; sqrt(lambda g) = 0.04 -> g = 3.125e-6; nu = lambda sqrt(lambda g)/Re;
+  equal kinematic viscosities; sigma = 1e-4 (the model needs sigma > 0).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import inputs
+
+CS2 = 1.0 / 3.0
+
+
+@dataclass
+class Problem:
+    name: str
+    xy: np.ndarray
+    tri: np.ndarray
+    box: np.ndarray
+    tag: np.ndarray
+    rho0: np.ndarray
+    u0: np.ndarray
+    p0: np.ndarray
+    params: dict
+    steps: int
+    precision: str
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_nodes(self):
+        return len(self.xy)
+
+
+def params(rho_l=1.0, rho_v=0.1, sigma=0.01, xi=4.0, tau_l=0.5, tau_v=0.5, dt=0.5,
+           gravity=(0.0, 0.0)):
+    return dict(rho_l=rho_l, rho_v=rho_v, sigma=sigma, xi=xi, tau_l=tau_l, tau_v=tau_v, dt=dt,
+                gravity=tuple(gravity))
+
+
+def droplet_structured(n=64, R=16.0, ratio=10.0, xi=4.0, sigma=0.01, tau_l=0.5, tau_v=0.5,
+                       dt=0.5, steps=500, precision="fp64", name="droplet"):
+    xy, tri, box, tag = inputs.structured_mesh(n, n)
+    rho_l, rho_v = 1.0, 1.0 / ratio
+    rho0, u0, p0 = inputs.droplet_fields(xy, box, (n / 2, n / 2), R, rho_l, rho_v, xi)
+    return Problem(name, xy, tri, box, tag, rho0, u0, p0,
+                   params(rho_l, rho_v, sigma, xi, tau_l, tau_v, dt), steps, precision,
+                   {"n": n, "R": R, "ratio": ratio})
+
+
+def c1_static_droplet():
+    """64x64 periodic structured split, R = 16, ratio 10, tau = 0.5, FP64, 500 steps."""
+    return droplet_structured(64, 16.0, 10.0, 4.0, 0.01, 0.5, 0.5, 0.5, 500, "fp64", "c1_droplet_64")
+
+
+def c2_unstructured_droplet(n=256, R=48.0, steps=5000, seed=1608):
+    """256x256 periodic box, jitter +-0.25, Lawson-Delaunay, ratio 1000,
+    nu_v/nu_l = 40, tau_v = 0.1, R = 48, FP32 vs FP64 oracle."""
+    xy, tri, box, tag = inputs.jittered_delaunay_mesh(n, n, 0.25, seed)
+    rho_l, rho_v = 1.0, 1.0e-3
+    rho0, u0, p0 = inputs.droplet_fields(xy, box, (n / 2, n / 2), R, rho_l, rho_v, 4.0)
+    return Problem("c2_unstructured_droplet_%d" % n, xy, tri, box, tag, rho0, u0, p0,
+                   params(rho_l, rho_v, 0.01, 4.0, 0.0025, 0.1, 0.5), steps, "fp32",
+                   {"n": n, "R": R, "ratio": 1000.0, "seed": seed})
+
+
+def rt_params(width=512, Re=3000.0, uref=0.04, dt=0.5):
+    g = uref * uref / width
+    nu = width * uref / Re
+    tau = nu / (CS2 * dt)
+    return g, nu, tau
+
+
+def c3_rayleigh_taylor(nx=512, ny=2048, steps=20000, Re=3000.0):
+    """512x2048 structured split, walls top/bottom, periodic x, At = 0.5,
+    amplitude 0.1 W, Re 3000, gravity body force, FP32."""
+    xy, tri, box, tag = inputs.structured_mesh(nx, ny, periodic_y=False)
+    rho_h, rho_lt = 1.0, 1.0 / 3.0
+    g, nu, tau = rt_params(nx, Re)
+    rho0, u0, p0 = inputs.rayleigh_taylor_fields(xy, nx, ny, rho_h, rho_lt, 4.0, 0.1 * nx, g)
+    return Problem("c3_rayleigh_taylor_%dx%d" % (nx, ny), xy, tri, box, tag, rho0, u0, p0,
+                   params(rho_h, rho_lt, 1e-4, 4.0, tau, tau, 0.5, (0.0, -g)), steps, "fp32",
+                   {"nx": nx, "ny": ny, "Re": Re, "At": 0.5, "g": g, "nu": nu})
+
+
+def batched_sides(count=64, lo=32, hi=512, seed=1609):
+    """Mesh sides log-uniform in [lo, hi] (integers, multiples of 1)."""
+    rng = np.random.default_rng(seed)
+    s = np.exp(rng.uniform(np.log(lo), np.log(hi), size=count))
+    ratios = rng.uniform(10.0, 1000.0, size=count)
+    radii = rng.uniform(0.2, 0.35, size=count)
+    return [(int(round(a)), float(b), float(c)) for a, b, c in zip(s, ratios, radii)]
+
+
+def c4_batched(count=64, seed=1609, lo=32, hi=512):
+    """64 independent periodic droplet runs, sides log-uniform in [32, 512],
+    density ratio U[10, 1000], radius U[0.2, 0.35] of the side, FP32."""
+    out = []
+    for k, (side, ratio, rfrac) in enumerate(batched_sides(count, lo, hi, seed)):
+        out.append(droplet_structured(side, rfrac * side, ratio, 4.0, 0.01, 0.1, 0.1, 0.5, 0,
+                                      "fp32", "batch_%02d_%d" % (k, side)))
+    return out

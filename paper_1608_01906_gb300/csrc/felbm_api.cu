@@ -1,0 +1,520 @@
+// C ABI of the FE-LBM library: handle management, uploads, launches.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "felbm_internal.h"
+#include "felbm_kernels.cuh"
+
+using namespace felbm;
+
+namespace felbm {
+
+__global__ void k_totals_final(int nparts, const double *__restrict__ part, double *__restrict__ out) {
+    // single warp, fixed order over lanes then shuffle tree: deterministic
+    double s0 = 0, s1 = 0, s2 = 0;
+    for (int k = threadIdx.x; k < nparts; k += 32) {
+        s0 += part[3 * k];
+        s1 += part[3 * k + 1];
+        s2 += part[3 * k + 2];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_down_sync(0xffffffffu, s0, o);
+        s1 += __shfl_down_sync(0xffffffffu, s1, o);
+        s2 += __shfl_down_sync(0xffffffffu, s2, o);
+    }
+    if (threadIdx.x == 0) {
+        out[0] = s0;
+        out[1] = s1;
+        out[2] = s2;
+    }
+}
+
+static constexpr int kTotalsBlocks = 304;  // 2 x 152 SMs
+
+static int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return FELBM_OK;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return FELBM_ERR_OOM;
+    }
+    return FELBM_ERR_CUDA;
+}
+
+#define FELBM_CK(x)                              \
+    do {                                         \
+        cudaError_t _e = (x);                    \
+        if (_e != cudaSuccess) return cuda_status(_e); \
+    } while (0)
+
+template <typename T>
+static DevCSR<T> dev_csr(const felbm_mesh *m) {
+    DevCSR<T> d;
+    d.n = (int32_t)m->n_nodes;
+    d.rowptr = m->d_rowptr;
+    d.col = m->d_col;
+    const size_t nnz = m->host.col.size();
+    const T *base;
+    if (sizeof(T) == 8)
+        base = reinterpret_cast<const T *>(m->d_coef64);
+    else
+        base = reinterpret_cast<const T *>(m->d_coef32);
+    d.ax = base;
+    d.ay = base + nnz;
+    d.bxx = base + 2 * nnz;
+    d.bxy = base + 3 * nnz;
+    d.byy = base + 4 * nnz;
+    d.tag = m->d_tag;
+    return d;
+}
+
+template <typename T>
+static Phys<T> phys_of(const felbm_params &p) {
+    const double d = p.rho_l - p.rho_v;
+    Phys<T> P;
+    P.rho_l = (T)p.rho_l;
+    P.rho_v = (T)p.rho_v;
+    P.beta = (T)(12.0 * p.sigma / (p.xi * d * d * d * d));
+    P.kappa = (T)(1.5 * p.xi * p.sigma / (d * d));
+    P.inv_tau_l = (T)(1.0 / p.tau_l);
+    P.inv_tau_v = (T)(1.0 / p.tau_v);
+    P.dt = (T)p.dt;
+    P.gx = (T)p.gravity[0];
+    P.gy = (T)p.gravity[1];
+    return P;
+}
+
+template <typename T>
+static Fields<T> fields_of(felbm_state *s) {
+    const size_t n = (size_t)s->mesh->n_nodes;
+    T *b = reinterpret_cast<T *>(s->scratch);
+    Fields<T> F;
+    F.rho = b;
+    F.drx = b + n;
+    F.dry = b + 2 * n;
+    F.mu = b + 3 * n;
+    F.kx = b + 4 * n;
+    F.ky = b + 5 * n;
+    return F;
+}
+
+static inline unsigned nblocks(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+template <typename T>
+static DevLattice<T> dev_lattice(const felbm_mesh *m) {
+    DevLattice<T> d;
+    d.n = (int32_t)m->n_nodes;
+    d.nx = m->sinfo.nx;
+    d.ny = m->sinfo.ny;
+    d.walls = m->sinfo.walls ? 1 : 0;
+    for (int k = 0; k < 3; ++k)
+        for (int o = 0; o < 6; ++o) {
+            d.c[k][o][0] = (T)m->sinfo.a[k][o][0];
+            d.c[k][o][1] = (T)m->sinfo.a[k][o][1];
+            for (int q = 0; q < 3; ++q) d.c[k][o][2 + q] = (T)m->sinfo.b[k][o][q];
+        }
+    return d;
+}
+
+// Derivative chain shared by init and step: rho (already in F.rho) ->
+// grad rho -> lap rho, K, mu.
+template <typename T, typename Topo>
+static void launch_chain(felbm_state *s, const Topo &d) {
+    const felbm_mesh *m = s->mesh;
+    const Fields<T> F = fields_of<T>(s);
+    const Phys<T> P = phys_of<T>(s->params);
+    const unsigned g = nblocks(m->n_nodes, 256);
+    k_grad<T, Topo><<<g, 256, 0, m->stream>>>(d, F);
+    k_mu<T, Topo><<<g, 256, 0, m->stream>>>(d, F, P);
+}
+
+template <typename T, typename Topo>
+static void step_topo(felbm_state *s, const Topo &d, bool write_mom) {
+    const felbm_mesh *m = s->mesh;
+    const Fields<T> F = fields_of<T>(s);
+    const Phys<T> P = phys_of<T>(s->params);
+    const unsigned g = nblocks(m->n_nodes, 256);
+    const T *fin = reinterpret_cast<const T *>(s->f[s->cur]);
+    T *fout = reinterpret_cast<T *>(s->f[s->cur ^ 1]);
+    k_rho<T, Topo><<<g, 256, 0, m->stream>>>(d, fin, P.dt, F.rho);
+    launch_chain<T, Topo>(s, d);
+    CollideArgs<T, Topo> A;
+    A.m = d;
+    A.fin = fin;
+    A.fout = fout;
+    A.F = F;
+    A.P = P;
+    A.mom = write_mom ? reinterpret_cast<T *>(s->mom) : nullptr;
+    A.flag = s->d_flag;
+    k_collide<T, Topo><<<g, 256, 0, m->stream>>>(A);
+    s->cur ^= 1;
+}
+
+template <typename T, typename Topo>
+static void init_topo(felbm_state *s, const Topo &d) {
+    const felbm_mesh *m = s->mesh;
+    const Fields<T> F = fields_of<T>(s);
+    const Phys<T> P = phys_of<T>(s->params);
+    // F.rho <- rho0 (first quarter of the moments buffer)
+    cudaMemcpyAsync(F.rho, s->mom, (size_t)m->n_nodes * sizeof(T), cudaMemcpyDeviceToDevice,
+                    m->stream);
+    launch_chain<T, Topo>(s, d);
+    const unsigned g = nblocks(m->n_nodes, 256);
+    k_init<T, Topo><<<g, 256, 0, m->stream>>>(d, reinterpret_cast<T *>(s->f[s->cur]), F, P,
+                                              reinterpret_cast<const T *>(s->mom));
+}
+
+template <typename T>
+static void do_steps(felbm_state *s, int64_t n) {
+    const felbm_mesh *m = s->mesh;
+    if (m->kind == 1) {
+        const DevLattice<T> d = dev_lattice<T>(m);
+        for (int64_t k = 0; k < n; ++k) step_topo<T>(s, d, k == n - 1);
+    } else {
+        const DevCSR<T> d = dev_csr<T>(m);
+        for (int64_t k = 0; k < n; ++k) step_topo<T>(s, d, k == n - 1);
+    }
+}
+
+template <typename T>
+static void init_any(felbm_state *s) {
+    if (s->mesh->kind == 1)
+        init_topo<T>(s, dev_lattice<T>(s->mesh));
+    else
+        init_topo<T>(s, dev_csr<T>(s->mesh));
+}
+
+template <typename T>
+static void launch_moments(felbm_state *s) {
+    const felbm_mesh *m = s->mesh;
+    const int32_t n = (int32_t)m->n_nodes;
+    const int32_t *iperm = m->kind == 1 ? nullptr : m->d_perm + n;  // d_perm holds perm | iperm
+    k_gather_moments<T><<<nblocks(n, 256), 256, 0, m->stream>>>(
+        n, reinterpret_cast<const T *>(s->mom), iperm, s->params.rho_l, s->params.rho_v, s->d_out);
+    double *part = s->d_out + 5 * (size_t)n;
+    k_totals_partial<T><<<kTotalsBlocks, 256, 0, m->stream>>>(
+        n, reinterpret_cast<const T *>(s->mom), m->d_mass, part);
+    k_totals_final<<<1, 32, 0, m->stream>>>(kTotalsBlocks, part, part + 3 * kTotalsBlocks);
+}
+
+}  // namespace felbm
+
+// ============================================================================
+extern "C" {
+
+const char *felbm_status_string(int st) {
+    switch (st) {
+        case FELBM_OK: return "ok";
+        case FELBM_ERR_INVALID_ARG: return "invalid argument";
+        case FELBM_ERR_INVALID_MESH: return "invalid mesh";
+        case FELBM_ERR_OOM: return "out of memory";
+        case FELBM_ERR_NONFINITE: return "non-finite value produced";
+        case FELBM_ERR_TIMEOUT: return "bounded device wait gave up";
+        case FELBM_ERR_CUDA: return "CUDA error";
+        case FELBM_ERR_UNSUPPORTED: return "unsupported";
+        default: return "unknown status";
+    }
+}
+
+static void mesh_free(felbm_mesh *m) {
+    if (!m) return;
+    cudaFree(m->d_rowptr);
+    cudaFree(m->d_col);
+    cudaFree(m->d_perm);
+    cudaFree(m->d_coef64);
+    cudaFree(m->d_coef32);
+    cudaFree(m->d_mass);
+    cudaFree(m->d_tag);
+    delete m;
+}
+
+int felbm_mesh_create(const double *xy, int64_t n_nodes, const int32_t *tri, int64_t n_tri,
+                      const double box[2], uint32_t flags, const uint8_t *node_tag, void *stream,
+                      felbm_mesh **out) {
+    if (!xy || !tri || !box || !out) return FELBM_ERR_INVALID_ARG;
+    if (n_nodes < 3 || n_tri < 1 || n_nodes > 0x7fffffffLL || n_tri > 0x7fffffffLL / 3)
+        return FELBM_ERR_INVALID_ARG;
+    if (flags & ~(FELBM_PERIODIC_X | FELBM_PERIODIC_Y | FELBM_MESH_GENERAL))
+        return FELBM_ERR_INVALID_ARG;
+    felbm_mesh *m = new (std::nothrow) felbm_mesh();
+    if (!m) return FELBM_ERR_OOM;
+    m->n_nodes = n_nodes;
+    m->n_tri = n_tri;
+    m->flags = flags;
+    m->stream = reinterpret_cast<cudaStream_t>(stream);
+    int st;
+    try {
+        st = build_csr(xy, n_nodes, tri, n_tri, box, flags, node_tag, m->host);
+    } catch (const std::bad_alloc &) {
+        st = FELBM_ERR_OOM;
+    }
+    if (st != FELBM_OK) {
+        delete m;
+        return st;
+    }
+    if (!(flags & FELBM_MESH_GENERAL))
+        detect_structured(xy, n_nodes, tri, n_tri, box, flags, node_tag, m->host, m->sinfo);
+    m->kind = m->sinfo.ok ? 1 : 0;
+    const HostCSR &H = m->host;
+    const size_t N = (size_t)n_nodes, nnz = H.col.size();
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void **p, size_t bytes) {
+        if (e == cudaSuccess) {
+            e = cudaMalloc(p, bytes);
+            if (e == cudaSuccess) m->device_bytes += (int64_t)bytes;
+        }
+    };
+    alloc((void **)&m->d_mass, N * sizeof(double));
+    if (m->kind == 0) {
+        alloc((void **)&m->d_rowptr, (N + 1) * sizeof(int32_t));
+        alloc((void **)&m->d_col, nnz * sizeof(int32_t));
+        alloc((void **)&m->d_perm, 2 * N * sizeof(int32_t));
+        alloc((void **)&m->d_coef64, 5 * nnz * sizeof(double));
+        alloc((void **)&m->d_coef32, 5 * nnz * sizeof(float));
+        if (!H.tag.empty()) alloc((void **)&m->d_tag, N);
+    }
+    if (e != cudaSuccess) {
+        int rs = cuda_status(e);
+        mesh_free(m);
+        return rs;
+    }
+    // uploads (synchronous: host vectors are temporaries of this call)
+    std::vector<double> mass_caller;
+    if (m->kind == 1) {
+        // structured kernels use the caller's (lattice) order
+        mass_caller.resize(N);
+        for (size_t k = 0; k < N; ++k) mass_caller[H.perm[k]] = H.mass[k];
+        e = cudaMemcpy(m->d_mass, mass_caller.data(), N * sizeof(double), cudaMemcpyHostToDevice);
+    } else {
+        e = cudaMemcpy(m->d_mass, H.mass.data(), N * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(m->d_rowptr, H.rowptr.data(), (N + 1) * sizeof(int32_t), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(m->d_col, H.col.data(), nnz * sizeof(int32_t), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(m->d_perm, H.perm.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(m->d_perm + N, H.iperm.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice);
+        std::vector<double> c64(5 * nnz);
+        std::vector<float> c32(5 * nnz);
+        const std::vector<double> *src[5] = {&H.ax, &H.ay, &H.bxx, &H.bxy, &H.byy};
+        for (int k = 0; k < 5; ++k)
+            for (size_t q = 0; q < nnz; ++q) {
+                c64[k * nnz + q] = (*src[k])[q];
+                c32[k * nnz + q] = (float)(*src[k])[q];
+            }
+        if (e == cudaSuccess)
+            e = cudaMemcpy(m->d_coef64, c64.data(), 5 * nnz * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(m->d_coef32, c32.data(), 5 * nnz * sizeof(float), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && m->d_tag)
+            e = cudaMemcpy(m->d_tag, H.tag.data(), N, cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+        int rs = cuda_status(e);
+        mesh_free(m);
+        return rs;
+    }
+    *out = m;
+    return FELBM_OK;
+}
+
+int felbm_mesh_info(const felbm_mesh *m, int64_t *n_nodes, int64_t *n_tri, int32_t *kind,
+                    int64_t *device_bytes) {
+    if (!m) return FELBM_ERR_INVALID_ARG;
+    if (n_nodes) *n_nodes = m->n_nodes;
+    if (n_tri) *n_tri = m->n_tri;
+    if (kind) *kind = m->kind;
+    if (device_bytes) *device_bytes = m->device_bytes;
+    return FELBM_OK;
+}
+
+void felbm_mesh_destroy(felbm_mesh *m) { mesh_free(m); }
+
+static void state_free(felbm_state *s) {
+    if (!s) return;
+    cudaFree(s->f[0]);
+    cudaFree(s->f[1]);
+    cudaFree(s->scratch);
+    cudaFree(s->mom);
+    cudaFree(s->d_out);
+    cudaFree(s->d_flag);
+    delete s;
+}
+
+static bool params_ok(const felbm_params *p) {
+    const double v[] = {p->rho_l, p->rho_v, p->sigma, p->xi, p->tau_l, p->tau_v, p->dt,
+                        p->gravity[0], p->gravity[1]};
+    for (double x : v)
+        if (!std::isfinite(x)) return false;
+    return p->rho_l > p->rho_v && p->rho_v > 0.0 && p->sigma >= 0.0 && p->xi > 0.0 &&
+           p->tau_l > 0.0 && p->tau_v > 0.0 && p->dt > 0.0 &&
+           (p->precision == FELBM_FP64 || p->precision == FELBM_FP32) && p->flags == 0;
+}
+
+int felbm_state_init(const felbm_mesh *mesh, const felbm_params *params, const double *rho0,
+                     const double *u0, const double *p0, felbm_state **out) {
+    if (!mesh || !params || !rho0 || !out) return FELBM_ERR_INVALID_ARG;
+    if (!params_ok(params)) return FELBM_ERR_INVALID_ARG;
+    const size_t N = (size_t)mesh->n_nodes;
+    for (size_t i = 0; i < N; ++i)
+        if (!(rho0[i] > 0.0) || !std::isfinite(rho0[i])) return FELBM_ERR_INVALID_ARG;
+    felbm_state *s = new (std::nothrow) felbm_state();
+    if (!s) return FELBM_ERR_OOM;
+    s->mesh = mesh;
+    s->params = *params;
+    s->precision = params->precision;
+    s->esize = params->precision == FELBM_FP64 ? 8 : 4;
+    const size_t es = s->esize;
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void **p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+    };
+    alloc(&s->f[0], 18 * N * es);
+    alloc(&s->f[1], 18 * N * es);
+    alloc(&s->scratch, 6 * N * es);
+    alloc(&s->mom, 4 * N * es);
+    alloc((void **)&s->d_out, (5 * N + 3 * (kTotalsBlocks + 1)) * sizeof(double));
+    alloc((void **)&s->d_flag, sizeof(int));
+    if (e != cudaSuccess) {
+        int rs = cuda_status(e);
+        state_free(s);
+        return rs;
+    }
+    // initial moments in the kernels' node order and precision
+    const bool perm = mesh->kind == 0;
+    std::vector<unsigned char> hm(4 * N * es);
+    for (size_t k = 0; k < N; ++k) {
+        const size_t c = perm ? (size_t)mesh->host.perm[k] : k;
+        const double v[4] = {rho0[c], u0 ? u0[2 * c] : 0.0, u0 ? u0[2 * c + 1] : 0.0,
+                             p0 ? p0[c] : 0.0};
+        for (int q = 0; q < 4; ++q) {
+            if (!std::isfinite(v[q])) {
+                state_free(s);
+                return FELBM_ERR_INVALID_ARG;
+            }
+            if (es == 8)
+                reinterpret_cast<double *>(hm.data())[q * N + k] = v[q];
+            else
+                reinterpret_cast<float *>(hm.data())[q * N + k] = (float)v[q];
+        }
+    }
+    e = cudaMemcpyAsync(s->mom, hm.data(), hm.size(), cudaMemcpyHostToDevice, mesh->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_flag, 0, sizeof(int), mesh->stream);
+    if (e == cudaSuccess) {
+        if (es == 8)
+            init_any<double>(s);
+        else
+            init_any<float>(s);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(mesh->stream);  // hm is a temporary
+    if (e != cudaSuccess) {
+        int rs = cuda_status(e);
+        state_free(s);
+        return rs;
+    }
+    s->have_moments = true;
+    *out = s;
+    return FELBM_OK;
+}
+
+int felbm_step(felbm_state *s, int64_t n_steps) {
+    if (!s || n_steps < 0) return FELBM_ERR_INVALID_ARG;
+    if (n_steps == 0) return FELBM_OK;
+    if (s->esize == 8)
+        do_steps<double>(s, n_steps);
+    else
+        do_steps<float>(s, n_steps);
+    s->steps_done += n_steps;
+    s->have_moments = true;
+    return cuda_status(cudaGetLastError());
+}
+
+static int check_flag(felbm_state *s) {
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, s->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s->mesh->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->mesh->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    return h ? FELBM_ERR_NONFINITE : FELBM_OK;
+}
+
+int felbm_state_sync(felbm_state *s) {
+    if (!s) return FELBM_ERR_INVALID_ARG;
+    return check_flag(s);
+}
+
+int felbm_moments_get(felbm_state *s, double *rho, double *C, double *u, double *p, double totals[3]) {
+    if (!s) return FELBM_ERR_INVALID_ARG;
+    if (!s->have_moments) return FELBM_ERR_INVALID_ARG;
+    const size_t N = (size_t)s->mesh->n_nodes;
+    const cudaStream_t st = s->mesh->stream;
+    if (s->esize == 8)
+        launch_moments<double>(s);
+    else
+        launch_moments<float>(s);
+    cudaError_t e = cudaGetLastError();
+    double *o = s->d_out;
+    if (e == cudaSuccess && rho) e = cudaMemcpyAsync(rho, o, N * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && C) e = cudaMemcpyAsync(C, o + N, N * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && u) e = cudaMemcpyAsync(u, o + 2 * N, 2 * N * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && p) e = cudaMemcpyAsync(p, o + 4 * N, N * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && totals)
+        e = cudaMemcpyAsync(totals, o + 5 * N + 3 * kTotalsBlocks, 3 * 8, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    return check_flag(s);
+}
+
+int felbm_state_export(felbm_state *s, double *hbar, double *gbar) {
+    if (!s || !hbar || !gbar) return FELBM_ERR_INVALID_ARG;
+    const size_t N = (size_t)s->mesh->n_nodes, es = s->esize;
+    std::vector<unsigned char> buf(18 * N * es);
+    cudaError_t e = cudaMemcpyAsync(buf.data(), s->f[s->cur], buf.size(), cudaMemcpyDeviceToHost,
+                                    s->mesh->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->mesh->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    const bool perm = s->mesh->kind == 0;
+    for (int a = 0; a < 18; ++a)
+        for (size_t k = 0; k < N; ++k) {
+            const size_t c = perm ? (size_t)s->mesh->host.perm[k] : k;
+            const double v = es == 8 ? reinterpret_cast<double *>(buf.data())[a * N + k]
+                                     : (double)reinterpret_cast<float *>(buf.data())[a * N + k];
+            (a < 9 ? hbar : gbar)[(a % 9) * N + c] = v;
+        }
+    return check_flag(s);
+}
+
+int felbm_state_import(felbm_state *s, const double *hbar, const double *gbar) {
+    if (!s || !hbar || !gbar) return FELBM_ERR_INVALID_ARG;
+    const size_t N = (size_t)s->mesh->n_nodes, es = s->esize;
+    std::vector<unsigned char> buf(18 * N * es);
+    const bool perm = s->mesh->kind == 0;
+    for (int a = 0; a < 18; ++a)
+        for (size_t k = 0; k < N; ++k) {
+            const size_t c = perm ? (size_t)s->mesh->host.perm[k] : k;
+            const double v = (a < 9 ? hbar : gbar)[(a % 9) * N + c];
+            if (!std::isfinite(v)) return FELBM_ERR_INVALID_ARG;
+            if (es == 8)
+                reinterpret_cast<double *>(buf.data())[a * N + k] = v;
+            else
+                reinterpret_cast<float *>(buf.data())[a * N + k] = (float)v;
+        }
+    cudaError_t e = cudaMemcpyAsync(s->f[s->cur], buf.data(), buf.size(), cudaMemcpyHostToDevice,
+                                    s->mesh->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_flag, 0, sizeof(int), s->mesh->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->mesh->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    s->have_moments = false;
+    return FELBM_OK;
+}
+
+void felbm_state_destroy(felbm_state *s) {
+    if (!s) return;
+    cudaStreamSynchronize(s->mesh->stream);
+    state_free(s);
+}
+
+}  // extern "C"

@@ -1,0 +1,160 @@
+// Internal declarations of the FE-LBM library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/felbm.h"
+
+namespace felbm {
+
+// ---- host-side mesh preprocessing (felbm_mesh.cu) -------------------------
+
+// Assembled per-node operators in the internal (reverse Cuthill-McKee) order.
+// For node i and each neighbour j != i sharing a triangle:
+//   a_ij = sum_{T∋i,j} |T| grad N_j^T / (3 m_i)                 (2-vector)
+//   b_ij = sum_{T∋i,j} |T| / m_i * sym(grad N_i^T (x) grad N_j^T)  (2x2, symmetric part)
+// so that, with sum_j a_ij = 0 and sum_j b_ij = 0 (P1 partition of unity),
+//   recovered gradient  (R f)_i   = sum_{j!=i} a_ij (f_j - f_i)
+//   lumped TG streaming psi*_i    = psi_i - dt sum_{j!=i} (e.a_ij + dt/2 e.b_ij.e)(psi_j - psi_i)
+struct HostCSR {
+    int32_t n = 0;
+    std::vector<int32_t> rowptr, col;
+    std::vector<double> ax, ay, bxx, bxy, byy;
+    std::vector<double> mass;      // lumped mass, internal order
+    std::vector<uint8_t> tag;      // internal order, empty if no walls
+    std::vector<int32_t> perm;     // perm[internal] = caller id
+    std::vector<int32_t> iperm;    // iperm[caller] = internal id
+};
+
+struct StructuredInfo {
+    bool ok = false;
+    int32_t nx = 0, ny = 0;
+    bool walls = false;  // non-periodic y with walls on the first and last row
+    double h = 1.0;
+    // 6 neighbour offsets (dx, dy) and their assembled a/b coefficients of an
+    // interior node; wall rows get their own sets (bottom, top).
+    double a[3][6][2];
+    double b[3][6][3];
+};
+
+int build_csr(const double *xy, int64_t n_nodes, const int32_t *tri, int64_t n_tri,
+              const double box[2], uint32_t flags, const uint8_t *tag, HostCSR &out);
+void detect_structured(const double *xy, int64_t n_nodes, const int32_t *tri, int64_t n_tri,
+                       const double box[2], uint32_t flags, const uint8_t *tag,
+                       const HostCSR &csr, StructuredInfo &info);
+
+// ---- device-side views --------------------------------------------------
+
+// Neighbour topologies.  for_each(i, fn) calls fn(j, ax, ay, bxx, bxy, byy)
+// for every neighbour j != i of node i with the assembled coefficients a_ij,
+// b_ij; tag_of(i) is the wall tag (0 = fluid).
+
+// General mesh: CSR in reverse Cuthill-McKee order.
+template <typename T>
+struct DevCSR {
+    int32_t n;
+    const int32_t *rowptr;
+    const int32_t *col;
+    const T *ax, *ay, *bxx, *bxy, *byy;
+    const uint8_t *tag;  // nullptr if no walls
+#ifdef __CUDACC__
+    template <typename Fn>
+    __device__ __forceinline__ void for_each(int32_t i, Fn &&fn) const {
+        const int32_t p1 = __ldg(rowptr + i + 1);
+        for (int32_t p = __ldg(rowptr + i); p < p1; ++p)
+            fn(__ldg(col + p), __ldg(ax + p), __ldg(ay + p), __ldg(bxx + p), __ldg(bxy + p),
+               __ldg(byy + p));
+    }
+    __device__ __forceinline__ int tag_of(int32_t i) const { return tag ? (int)tag[i] : 0; }
+#endif
+};
+
+// Structured lattice split (node i = x + nx*y): six neighbours at fixed
+// offsets, coefficients of three row kinds (0 interior, 1 bottom wall row,
+// 2 top wall row) held in the kernel parameters.
+// offsets o = 0..5: (1,0), (1,1), (0,1), (-1,0), (-1,-1), (0,-1)
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+constexpr int lat_dx(int o) { return o == 0 || o == 1 ? 1 : (o == 3 || o == 4 ? -1 : 0); }
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+constexpr int lat_dy(int o) { return o == 1 || o == 2 ? 1 : (o == 4 || o == 5 ? -1 : 0); }
+
+template <typename T>
+struct DevLattice {
+    int32_t n, nx, ny, walls;
+    T c[3][6][5];  // ax, ay, bxx, bxy, byy
+#ifdef __CUDACC__
+    template <typename Fn>
+    __device__ __forceinline__ void for_each(int32_t i, Fn &&fn) const {
+        const int32_t y = i / nx, x = i - y * nx;
+        const int kind = walls ? (y == 0 ? 1 : (y == ny - 1 ? 2 : 0)) : 0;
+#pragma unroll
+        for (int o = 0; o < 6; ++o) {
+            int32_t yy = y + lat_dy(o);
+            if (walls && (yy < 0 || yy >= ny)) continue;
+            yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
+            int32_t xx = x + lat_dx(o);
+            xx = xx < 0 ? xx + nx : (xx >= nx ? xx - nx : xx);
+            fn(xx + nx * yy, c[kind][o][0], c[kind][o][1], c[kind][o][2], c[kind][o][3],
+               c[kind][o][4]);
+        }
+    }
+    __device__ __forceinline__ int tag_of(int32_t i) const {
+        if (!walls) return 0;
+        const int32_t y = i / nx;
+        return y == 0 ? 2 : (y == ny - 1 ? 4 : 0);
+    }
+#endif
+};
+
+// Model constants of one state (Sec. 2.1), in the state's precision.
+template <typename T>
+struct Phys {
+    T rho_l, rho_v, beta, kappa, inv_tau_l, inv_tau_v, dt, gx, gy;
+};
+
+template <typename T>
+struct Fields {
+    T *rho, *drx, *dry, *mu, *kx, *ky;  // N each
+};
+
+}  // namespace felbm
+
+// ---- opaque handles ---------------------------------------------------------
+
+struct felbm_mesh {
+    int64_t n_nodes = 0, n_tri = 0;
+    uint32_t flags = 0;
+    cudaStream_t stream = nullptr;
+    int kind = 0;  // 0 general, 1 structured
+    felbm::HostCSR host;
+    felbm::StructuredInfo sinfo;
+    // device arrays
+    int32_t *d_rowptr = nullptr, *d_col = nullptr, *d_perm = nullptr;
+    double *d_coef64 = nullptr;  // 5 * nnz, SoA: ax, ay, bxx, bxy, byy
+    float *d_coef32 = nullptr;
+    double *d_mass = nullptr;
+    uint8_t *d_tag = nullptr;
+    int64_t device_bytes = 0;
+};
+
+struct felbm_state {
+    const felbm_mesh *mesh = nullptr;
+    felbm_params params{};
+    int precision = FELBM_FP64;
+    size_t esize = 8;
+    void *f[2] = {nullptr, nullptr};  // 18 N each: h_0..h_8, g_0..g_8
+    int cur = 0;
+    void *scratch = nullptr;          // 6 N: rho, drx, dry, mu, kx, ky
+    void *mom = nullptr;              // 4 N: rho, ux, uy, p (internal order)
+    double *d_out = nullptr;          // 5 N staging in caller order + reduction partials
+    int *d_flag = nullptr;
+    bool have_moments = false;
+    int64_t steps_done = 0;
+};

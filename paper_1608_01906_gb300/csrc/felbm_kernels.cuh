@@ -1,0 +1,382 @@
+// Device kernels of one FE-LBM time step, general (unstructured CSR) path.
+//
+// One step = four dependent neighbour passes, each a gather over the
+// assembled per-node operators (HostCSR in felbm_internal.h):
+//   k_rho      Taylor-Galerkin streaming of the 9 h populations (Sec. 2.2.1,
+//              Eq. galerkin_lbm with the lumped mass), wall bounce-back,
+//              rho = sum_a h_a.
+//   k_grad     recovered grad rho (Sec. 2.3).
+//   k_mu       Laplacian of rho (recovery of the recovered gradient), the
+//              stress force K = kappa [d_i |grad rho|^2 - d_j (d_i rho d_j rho)]
+//              and mu = mu_phi(rho) - kappa lap rho (Sec. 2.1).
+//   k_collide  recovered grad mu; streaming of all 18 populations; bounce-back;
+//              moments (Eqs. velocity, pressure); post-streaming collision and
+//              the next pre-streaming collision (Sec. 2.2) in one update.
+// Operators use the difference form sum_{j != i} c_ij (f_j - f_i), exact for
+// constant fields in any precision.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "felbm_internal.h"
+
+namespace felbm {
+
+// D2Q9 velocity components, weights, opposite directions.
+__host__ __device__ constexpr int kEx(int a) { return a == 1 || a == 5 || a == 8 ? 1 : (a == 3 || a == 6 || a == 7 ? -1 : 0); }
+__host__ __device__ constexpr int kEy(int a) { return a == 2 || a == 5 || a == 6 ? 1 : (a == 4 || a == 7 || a == 8 ? -1 : 0); }
+__host__ __device__ constexpr int kOpp(int a) { return a == 0 ? 0 : (a <= 4 ? ((a + 1) % 4) + 1 : ((a - 5 + 2) % 4) + 5); }
+template <typename T>
+__host__ __device__ constexpr T kW(int a) { return a == 0 ? T(4) / T(9) : (a <= 4 ? T(1) / T(9) : T(1) / T(36)); }
+
+template <typename T>
+__device__ __forceinline__ bool finite_val(T v) { return isfinite(v); }
+
+// Streaming coefficient of direction a from the assembled tensors:
+//   c = e.a_ij + (dt/2) e.b_ij.e
+template <typename T, int A>
+__device__ __forceinline__ T stream_coef(T ax, T ay, T hbxx, T hbxy, T hbyy) {
+    constexpr int ex = kEx(A), ey = kEy(A);
+    T c = T(0);
+    if (ex) c += T(ex) * ax + hbxx;
+    if (ey) c += T(ey) * ay + hbyy;
+    if (ex && ey) c += T(2 * ex * ey) * hbxy;
+    return c;
+}
+
+// Accumulate sum_j c^a_ij (psi_j - psi_i) for the populations [A0, A1) of the
+// block starting at pops (SoA, stride n).
+template <typename T, int A0, int A1>
+struct StreamAcc {
+    template <typename Topo>
+    __device__ __forceinline__ static void run(const Topo &m, const T *__restrict__ pops,
+                                               int32_t i, T dt, const T *self, T *acc) {
+        const T hdt = T(0.5) * dt;
+        const int32_t n = m.n;
+        m.for_each(i, [&](int32_t j, T ax, T ay, T bxx, T bxy, T byy) {
+            const T hbxx = hdt * bxx, hbxy = hdt * bxy, hbyy = hdt * byy;
+#pragma unroll
+            for (int a = A0; a < A1; ++a) {
+                if (a == 0 || a == 9) continue;
+                const int d = a % 9;
+                T c;
+                switch (d) {
+                    case 1: c = stream_coef<T, 1>(ax, ay, hbxx, hbxy, hbyy); break;
+                    case 2: c = stream_coef<T, 2>(ax, ay, hbxx, hbxy, hbyy); break;
+                    case 3: c = stream_coef<T, 3>(ax, ay, hbxx, hbxy, hbyy); break;
+                    case 4: c = stream_coef<T, 4>(ax, ay, hbxx, hbxy, hbyy); break;
+                    case 5: c = stream_coef<T, 5>(ax, ay, hbxx, hbxy, hbyy); break;
+                    case 6: c = stream_coef<T, 6>(ax, ay, hbxx, hbxy, hbyy); break;
+                    case 7: c = stream_coef<T, 7>(ax, ay, hbxx, hbxy, hbyy); break;
+                    default: c = stream_coef<T, 8>(ax, ay, hbxx, hbxy, hbyy); break;
+                }
+                acc[a - A0] += c * (__ldg(pops + (size_t)a * n + j) - self[a - A0]);
+            }
+        });
+    }
+};
+
+// Bounce-back at a wall node with inward normal e_k: every population with
+// e_a . e_k > 0 takes the value of its opposite.  psi holds 9 populations.
+template <typename T>
+__device__ __forceinline__ void bounce_back(int k, T *psi) {
+    const int nx = kEx(k), ny = kEy(k);
+#pragma unroll
+    for (int a = 1; a < 9; ++a)
+        if (kEx(a) * nx + kEy(a) * ny > 0) psi[a] = psi[kOpp(a)];
+}
+
+template <typename T, typename Topo>
+__global__ void __launch_bounds__(256) k_rho(Topo m, const T *__restrict__ f, T dt,
+                                             T *__restrict__ rho) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m.n) return;
+    const size_t n = (size_t)m.n;
+    T h[9], acc[9];
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        h[a] = f[a * n + i];
+        acc[a] = T(0);
+    }
+    StreamAcc<T, 0, 9>::run(m, f, i, dt, h, acc);
+#pragma unroll
+    for (int a = 1; a < 9; ++a) h[a] -= dt * acc[a];
+    {
+        const int k = m.tag_of(i);
+        if (k) bounce_back<T>(k, h);
+    }
+    T r = T(0);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) r += h[a];
+    rho[i] = r;
+}
+
+// Recovered gradient of a scalar field.
+template <typename T, typename Topo>
+__device__ __forceinline__ void recover(const Topo &m, const T *__restrict__ f, int32_t i,
+                                        T &gx, T &gy) {
+    const T fi = f[i];
+    T sx = T(0), sy = T(0);
+    m.for_each(i, [&](int32_t j, T ax, T ay, T, T, T) {
+        const T d = __ldg(f + j) - fi;
+        sx += ax * d;
+        sy += ay * d;
+    });
+    gx = sx;
+    gy = sy;
+}
+
+template <typename T, typename Topo>
+__global__ void __launch_bounds__(256) k_grad(Topo m, Fields<T> F) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m.n) return;
+    T gx, gy;
+    recover(m, F.rho, i, gx, gy);
+    F.drx[i] = gx;
+    F.dry[i] = gy;
+}
+
+// lap rho = R_x(d_x rho) + R_y(d_y rho);
+// K_x = kappa [R_x((d_y rho)^2) - R_y(d_x rho d_y rho)],
+// K_y = kappa [R_y((d_x rho)^2) - R_x(d_x rho d_y rho)]
+// (the printed form d_i(|grad rho|^2) - d_j(d_i rho d_j rho) with the
+// identical (d_i rho)^2 contributions cancelled, R linear);
+// mu = 4 beta (rho - rho_v)(rho - rho_l)(rho - (rho_v + rho_l)/2) - kappa lap rho.
+template <typename T, typename Topo>
+__global__ void __launch_bounds__(256) k_mu(Topo m, Fields<T> F, Phys<T> P) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m.n) return;
+    const T gxi = F.drx[i], gyi = F.dry[i];
+    const T xxi = gxi * gxi, xyi = gxi * gyi, yyi = gyi * gyi;
+    T lap = T(0), kx = T(0), ky = T(0);
+    m.for_each(i, [&](int32_t j, T ax, T ay, T, T, T) {
+        const T gxj = __ldg(F.drx + j), gyj = __ldg(F.dry + j);
+        lap += ax * (gxj - gxi) + ay * (gyj - gyi);
+        const T dxx = gxj * gxj - xxi, dxy = gxj * gyj - xyi, dyy = gyj * gyj - yyi;
+        kx += ax * dyy - ay * dxy;
+        ky += ay * dxx - ax * dxy;
+    });
+    const T r = F.rho[i];
+    const T mub = T(4) * P.beta * (r - P.rho_v) * (r - P.rho_l) * (r - T(0.5) * (P.rho_v + P.rho_l));
+    F.mu[i] = mub - P.kappa * lap;
+    F.kx[i] = P.kappa * kx;
+    F.ky[i] = P.kappa * ky;
+}
+
+// Local collision of one node (Sec. 2.2).  In: streamed h*, g* (9 each),
+// rho, grad rho, grad mu, K.  Out: next stored pre-collided values, moments.
+// With eq and source S of the node, the post-streaming collision
+//   psi = psi* + 2tau/(2tau+1) (-(psi* - eq)/(2tau) + S)
+// followed by the pre-streaming collision
+//   psibar = psi + (-(psi - eq)/(2tau) + S)
+// equals psibar = eq + S + w (psi* - eq + S), w = (2tau - 1)/(2tau + 1).
+template <typename T>
+__device__ __forceinline__ void collide_node(const Phys<T> &P, const T *hs, const T *gs, T r,
+                                             T drx, T dry, T dmx, T dmy, T kx, T ky, T *hout,
+                                             T *gout, T &ux, T &uy, T &p) {
+    constexpr T cs2 = T(1) / T(3);
+    T mx = T(0), my = T(0), sg = T(0);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        sg += gs[a];
+        if (kEx(a)) mx += T(kEx(a)) * gs[a];
+        if (kEy(a)) my += T(kEy(a)) * gs[a];
+    }
+    const T hdt = T(0.5) * P.dt;
+    const T inv_r = T(1) / r;
+    ux = (mx + hdt * kx + hdt * r * P.gx) * inv_r;
+    uy = (my + hdt * ky + hdt * r * P.gy) * inv_r;
+    p = cs2 * (sg + hdt * (ux * drx + uy * dry));
+    T C = (r - P.rho_v) / (P.rho_l - P.rho_v);
+    C = C < T(0) ? T(0) : (C > T(1) ? T(1) : C);
+    const T tau = T(1) / (C * P.inv_tau_l + (T(1) - C) * P.inv_tau_v);
+    const T w = (T(2) * tau - T(1)) / (T(2) * tau + T(1));
+    // force vectors
+    const T Xx = cs2 * drx - r * dmx, Xy = cs2 * dry - r * dmy;  // F: c_s^2 grad rho - rho grad mu
+    const T uX = ux * Xx + uy * Xy, uD = ux * drx + uy * dry, uK = ux * kx + uy * ky;
+    const T uu = ux * ux + uy * uy;
+    const T dux = P.gx * P.dt, duy = P.gy * P.dt;  // exact-difference du = g dt
+    const T udu = dux * (T(2) * ux + dux) + duy * (T(2) * uy + duy);
+    const T p3 = T(3) * p;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        const int ex = kEx(a), ey = kEy(a);
+        const T wa = kW<T>(a);
+        const T eu = T(ex) * ux + T(ey) * uy;
+        // Gamma - w computed directly: forming Gamma ~ w first and subtracting
+        // w would cancel away the momentum part rho w 3 e.u in FP32.
+        const T gmw = wa * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * uu);
+        const T gam = wa + gmw;
+        const T eX = T(ex) * Xx + T(ey) * Xy;
+        const T eD = T(ex) * drx + T(ey) * dry;
+        const T eK = T(ex) * kx + T(ey) * ky;
+        const T edu = T(ex) * dux + T(ey) * duy;
+        const T heq = r * gam;
+        const T geq = wa * p3 + r * gmw;
+        const T Fa = hdt * T(3) * (eX - uX) * gam;
+        const T Ga = hdt * (eD - uD) * gmw + hdt * T(3) * (eK - uK) * gam;
+        // 1/2 [g_eq(u + du) - g_eq(u)] = rho/2 [Gamma(u + du) - Gamma(u)]
+        const T Ba = T(0.5) * r * wa *
+                     (T(3) * edu + T(4.5) * edu * (T(2) * eu + edu) - T(1.5) * udu);
+        const T Sh = Fa, Sg = Ga + Ba;
+        hout[a] = heq + Sh + w * (hs[a] - heq + Sh);
+        gout[a] = geq + Sg + w * (gs[a] - geq + Sg);
+    }
+}
+
+template <typename T, typename Topo>
+struct CollideArgs {
+    Topo m;
+    const T *fin;
+    T *fout;
+    Fields<T> F;
+    Phys<T> P;
+    T *mom;  // 4N or nullptr
+    int *flag;
+};
+
+template <typename T, typename Topo>
+__global__ void __launch_bounds__(256) k_collide(CollideArgs<T, Topo> A) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const Topo &m = A.m;
+    if (i >= m.n) return;
+    const size_t n = (size_t)m.n;
+    T dmx, dmy;
+    recover(m, A.F.mu, i, dmx, dmy);
+    T hs[9], gs[9];
+    {
+        T self[18], acc[18];
+#pragma unroll
+        for (int a = 0; a < 18; ++a) {
+            self[a] = A.fin[a * n + i];
+            acc[a] = T(0);
+        }
+        StreamAcc<T, 0, 18>::run(m, A.fin, i, A.P.dt, self, acc);
+#pragma unroll
+        for (int a = 0; a < 9; ++a) {
+            hs[a] = self[a] - A.P.dt * acc[a];
+            gs[a] = self[9 + a] - A.P.dt * acc[9 + a];
+        }
+    }
+    {
+        const int k = m.tag_of(i);
+        if (k) {
+            bounce_back<T>(k, hs);
+            bounce_back<T>(k, gs);
+        }
+    }
+    const T r = A.F.rho[i];
+    T hout[9], gout[9], ux, uy, p;
+    collide_node<T>(A.P, hs, gs, r, A.F.drx[i], A.F.dry[i], dmx, dmy, A.F.kx[i], A.F.ky[i], hout,
+                    gout, ux, uy, p);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        A.fout[a * n + i] = hout[a];
+        A.fout[(9 + a) * n + i] = gout[a];
+    }
+    if (!(finite_val(r) && finite_val(ux) && finite_val(uy) && finite_val(p))) atomicOr(A.flag, 1);
+    if (A.mom) {
+        A.mom[i] = r;
+        A.mom[n + i] = ux;
+        A.mom[2 * n + i] = uy;
+        A.mom[3 * n + i] = p;
+    }
+}
+
+// Initial state: post-collision distributions are the equilibria of
+// (rho0, u0, p0); stored value psibar = eq + S (Omega(eq) = 0).
+template <typename T, typename Topo>
+__global__ void __launch_bounds__(256) k_init(Topo m, T *__restrict__ fout, Fields<T> F,
+                                              Phys<T> P, const T *__restrict__ mom) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m.n) return;
+    const size_t n = (size_t)m.n;
+    T dmx, dmy;
+    recover(m, F.mu, i, dmx, dmy);
+    const T r = mom[i], ux = mom[n + i], uy = mom[2 * n + i], p = mom[3 * n + i];
+    const T drx = F.drx[i], dry = F.dry[i], kx = F.kx[i], ky = F.ky[i];
+    const T hdt = T(0.5) * P.dt;
+    const T Xx = T(1) / T(3) * drx - r * dmx, Xy = T(1) / T(3) * dry - r * dmy;
+    const T uX = ux * Xx + uy * Xy, uD = ux * drx + uy * dry, uK = ux * kx + uy * ky;
+    const T uu = ux * ux + uy * uy;
+    const T dux = P.gx * P.dt, duy = P.gy * P.dt;
+    const T udu = dux * (T(2) * ux + dux) + duy * (T(2) * uy + duy);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        const int ex = kEx(a), ey = kEy(a);
+        const T wa = kW<T>(a);
+        const T eu = T(ex) * ux + T(ey) * uy;
+        const T gmw = wa * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * uu);  // Gamma - w
+        const T gam = wa + gmw;
+        const T eX = T(ex) * Xx + T(ey) * Xy;
+        const T eD = T(ex) * drx + T(ey) * dry;
+        const T eK = T(ex) * kx + T(ey) * ky;
+        const T edu = T(ex) * dux + T(ey) * duy;
+        const T Fa = hdt * T(3) * (eX - uX) * gam;
+        const T Ga = hdt * (eD - uD) * gmw + hdt * T(3) * (eK - uK) * gam;
+        const T Ba = T(0.5) * r * wa * (T(3) * edu + T(4.5) * edu * (T(2) * eu + edu) - T(1.5) * udu);
+        fout[a * n + i] = r * gam + Fa;
+        fout[(9 + a) * n + i] = wa * T(3) * p + r * gmw + Ga + Ba;
+    }
+}
+
+// Moments in caller order, FP64: out[0..N) rho, [N..2N) C, [2N..4N) u
+// interleaved (ux, uy), [4N..5N) p.
+template <typename T>
+__global__ void k_gather_moments(int32_t n, const T *__restrict__ mom, const int32_t *__restrict__ iperm,
+                                 double rho_l, double rho_v, double *__restrict__ out) {
+    const int32_t c = blockIdx.x * blockDim.x + threadIdx.x;  // caller id
+    if (c >= n) return;
+    const int32_t k = iperm ? iperm[c] : c;
+    const double r = (double)mom[k];
+    out[c] = r;
+    out[(size_t)n + c] = (r - rho_v) / (rho_l - rho_v);
+    out[2 * (size_t)n + 2 * (size_t)c] = (double)mom[(size_t)n + k];
+    out[2 * (size_t)n + 2 * (size_t)c + 1] = (double)mom[2 * (size_t)n + k];
+    out[4 * (size_t)n + c] = (double)mom[3 * (size_t)n + k];
+}
+
+// FP64 totals: sum m rho, sum m rho ux, sum m rho uy.  Deterministic two-pass
+// reduction: block partials (warp shuffles + shared memory), then one block.
+template <typename T>
+__global__ void __launch_bounds__(256) k_totals_partial(int32_t n, const T *__restrict__ mom,
+                                                        const double *__restrict__ mass,
+                                                        double *__restrict__ part) {
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double mr = mass[i] * (double)mom[i];
+        s0 += mr;
+        s1 += mr * (double)mom[(size_t)n + i];
+        s2 += mr * (double)mom[2 * (size_t)n + i];
+    }
+    __shared__ double sh[3][8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_down_sync(0xffffffffu, s0, o);
+        s1 += __shfl_down_sync(0xffffffffu, s1, o);
+        s2 += __shfl_down_sync(0xffffffffu, s2, o);
+    }
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        sh[0][wid] = s0;
+        sh[1][wid] = s1;
+        sh[2][wid] = s2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t0 = 0, t1 = 0, t2 = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            t0 += sh[0][w];
+            t1 += sh[1][w];
+            t2 += sh[2][w];
+        }
+        part[3 * blockIdx.x] = t0;
+        part[3 * blockIdx.x + 1] = t1;
+        part[3 * blockIdx.x + 2] = t2;
+    }
+}
+
+__global__ void k_totals_final(int nparts, const double *__restrict__ part, double *__restrict__ out);
+
+}  // namespace felbm

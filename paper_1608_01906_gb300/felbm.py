@@ -1,0 +1,261 @@
+"""ctypes binding of the C ABI in ``include/felbm.h`` (argument marshalling only).
+
+Every function of the header is exposed under the same name; the ``Mesh`` and
+``State`` classes own the opaque handles.  Every computation runs inside
+``libfelbm.so``; this module never computes a physical quantity.  Loading
+fails loudly (``FelbmError``) when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfelbm.so")
+
+FELBM_OK = 0
+FELBM_ERR_INVALID_ARG = -1
+FELBM_ERR_INVALID_MESH = -2
+FELBM_ERR_OOM = -3
+FELBM_ERR_NONFINITE = -4
+FELBM_ERR_TIMEOUT = -5
+FELBM_ERR_CUDA = -6
+FELBM_ERR_UNSUPPORTED = -7
+
+FELBM_PERIODIC_X = 0x1
+FELBM_PERIODIC_Y = 0x2
+FELBM_MESH_GENERAL = 0x4
+FELBM_FP64 = 0
+FELBM_FP32 = 1
+
+EXPORTED = [
+    "felbm_mesh_create", "felbm_mesh_info", "felbm_mesh_destroy", "felbm_state_init",
+    "felbm_step", "felbm_state_sync", "felbm_moments_get", "felbm_state_export",
+    "felbm_state_import", "felbm_state_destroy", "felbm_status_string",
+]
+
+
+class FelbmError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = status
+        msg = status_string(status) if _lib is not None else str(status)
+        super().__init__(f"{where}: {msg} ({status})")
+
+
+class felbm_params(C.Structure):
+    _fields_ = [
+        ("rho_l", C.c_double), ("rho_v", C.c_double),
+        ("sigma", C.c_double), ("xi", C.c_double),
+        ("tau_l", C.c_double), ("tau_v", C.c_double),
+        ("dt", C.c_double), ("gravity", C.c_double * 2),
+        ("precision", C.c_int32), ("flags", C.c_int32),
+    ]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libfelbm.so and declare the prototypes of every exported symbol."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise FelbmError(FELBM_ERR_UNSUPPORTED,
+                         f"CUDA library {path} is missing; run paper_1608_01906_gb300.build")
+    lib = C.CDLL(path)
+    vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int32
+    pp = C.POINTER(C.c_void_p)
+    lib.felbm_mesh_create.restype = C.c_int
+    lib.felbm_mesh_create.argtypes = [vp, i64, vp, i64, vp, C.c_uint32, vp, vp, pp]
+    lib.felbm_mesh_info.restype = C.c_int
+    lib.felbm_mesh_info.argtypes = [vp, vp, vp, vp, vp]
+    lib.felbm_mesh_destroy.restype = None
+    lib.felbm_mesh_destroy.argtypes = [vp]
+    lib.felbm_state_init.restype = C.c_int
+    lib.felbm_state_init.argtypes = [vp, C.POINTER(felbm_params), vp, vp, vp, pp]
+    lib.felbm_step.restype = C.c_int
+    lib.felbm_step.argtypes = [vp, i64]
+    lib.felbm_state_sync.restype = C.c_int
+    lib.felbm_state_sync.argtypes = [vp]
+    lib.felbm_moments_get.restype = C.c_int
+    lib.felbm_moments_get.argtypes = [vp, vp, vp, vp, vp, vp]
+    lib.felbm_state_export.restype = C.c_int
+    lib.felbm_state_export.argtypes = [vp, vp, vp]
+    lib.felbm_state_import.restype = C.c_int
+    lib.felbm_state_import.argtypes = [vp, vp, vp]
+    lib.felbm_state_destroy.restype = None
+    lib.felbm_state_destroy.argtypes = [vp]
+    lib.felbm_status_string.restype = C.c_char_p
+    lib.felbm_status_string.argtypes = [C.c_int]
+    _lib = lib
+    _declare_extra(lib)
+    return lib
+
+
+def _declare_extra(lib):
+    """Prototypes of optional entry points (batched launch), when present."""
+    vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int32
+    pp = C.POINTER(C.c_void_p)
+    if hasattr(lib, "felbm_batch_create"):
+        lib.felbm_batch_create.restype = C.c_int
+        lib.felbm_batch_create.argtypes = [C.POINTER(C.c_void_p), i32, C.c_uint32, pp]
+        lib.felbm_batch_step.restype = C.c_int
+        lib.felbm_batch_step.argtypes = [vp, i64]
+        lib.felbm_batch_destroy.restype = None
+        lib.felbm_batch_destroy.argtypes = [vp]
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _check(st, where):
+    if st != FELBM_OK:
+        raise FelbmError(st, where)
+
+
+def status_string(st: int) -> str:
+    return load().felbm_status_string(int(st)).decode()
+
+
+felbm_status_string = status_string
+
+
+# ---- raw ABI functions (same names as the header) -------------------------
+
+def felbm_mesh_create(xy, tri, box, flags, node_tag=None, stream=None):
+    lib = load()
+    xy = np.ascontiguousarray(xy, dtype=np.float64)
+    tri = np.ascontiguousarray(tri, dtype=np.int32)
+    box = np.ascontiguousarray(box, dtype=np.float64)
+    tag = None if node_tag is None else np.ascontiguousarray(node_tag, dtype=np.uint8)
+    out = C.c_void_p()
+    st = lib.felbm_mesh_create(_p(xy), len(xy), _p(tri), len(tri), _p(box), int(flags), _p(tag),
+                               C.c_void_p(stream) if stream else None, C.byref(out))
+    return st, out
+
+
+def felbm_state_init(mesh, params: felbm_params, rho0, u0=None, p0=None):
+    lib = load()
+    rho0 = np.ascontiguousarray(rho0, dtype=np.float64)
+    u0 = None if u0 is None else np.ascontiguousarray(u0, dtype=np.float64)
+    p0 = None if p0 is None else np.ascontiguousarray(p0, dtype=np.float64)
+    out = C.c_void_p()
+    st = lib.felbm_state_init(mesh, C.byref(params), _p(rho0), _p(u0), _p(p0), C.byref(out))
+    return st, out
+
+
+def felbm_step(state, n_steps):
+    return load().felbm_step(state, int(n_steps))
+
+
+def felbm_state_sync(state):
+    return load().felbm_state_sync(state)
+
+
+def felbm_moments_get(state, rho=None, Cf=None, u=None, p=None, totals=None):
+    return load().felbm_moments_get(state, _p(rho), _p(Cf), _p(u), _p(p), _p(totals))
+
+
+def felbm_state_export(state, hbar, gbar):
+    return load().felbm_state_export(state, _p(hbar), _p(gbar))
+
+
+def felbm_state_import(state, hbar, gbar):
+    return load().felbm_state_import(state, _p(hbar), _p(gbar))
+
+
+# ---- owning wrappers ------------------------------------------------------
+
+def flags_for(box, general=False):
+    f = 0
+    if box[0] > 0:
+        f |= FELBM_PERIODIC_X
+    if box[1] > 0:
+        f |= FELBM_PERIODIC_Y
+    if general:
+        f |= FELBM_MESH_GENERAL
+    return f
+
+
+class Mesh:
+    def __init__(self, xy, tri, box, node_tag=None, general=False, stream=None):
+        self.n_nodes = len(xy)
+        st, h = felbm_mesh_create(xy, tri, box, flags_for(box, general), node_tag, stream)
+        _check(st, "felbm_mesh_create")
+        self.handle = h
+
+    def info(self):
+        n, t, k, b = C.c_int64(), C.c_int64(), C.c_int32(), C.c_int64()
+        _check(load().felbm_mesh_info(self.handle, C.byref(n), C.byref(t), C.byref(k),
+                                      C.byref(b)), "felbm_mesh_info")
+        return {"n_nodes": n.value, "n_tri": t.value, "kind": k.value, "device_bytes": b.value}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().felbm_mesh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_params(rho_l, rho_v, sigma, xi, tau_l, tau_v, dt, gravity=(0.0, 0.0), precision="fp64"):
+    p = felbm_params()
+    p.rho_l, p.rho_v, p.sigma, p.xi = rho_l, rho_v, sigma, xi
+    p.tau_l, p.tau_v, p.dt = tau_l, tau_v, dt
+    p.gravity[0], p.gravity[1] = gravity
+    p.precision = FELBM_FP64 if precision in ("fp64", FELBM_FP64) else FELBM_FP32
+    p.flags = 0
+    return p
+
+
+class State:
+    def __init__(self, mesh: Mesh, params: felbm_params, rho0, u0=None, p0=None):
+        self.mesh = mesh
+        self.n = mesh.n_nodes
+        st, h = felbm_state_init(mesh.handle, params, rho0, u0, p0)
+        _check(st, "felbm_state_init")
+        self.handle = h
+
+    def step(self, n=1):
+        _check(felbm_step(self.handle, n), "felbm_step")
+
+    def sync(self):
+        _check(felbm_state_sync(self.handle), "felbm_state_sync")
+
+    def moments(self):
+        n = self.n
+        rho, Cf, p = np.empty(n), np.empty(n), np.empty(n)
+        u = np.empty((n, 2))
+        tot = np.empty(3)
+        _check(felbm_moments_get(self.handle, rho, Cf, u, p, tot), "felbm_moments_get")
+        return {"rho": rho, "C": Cf, "u": u, "p": p, "totals": tot}
+
+    def export(self):
+        h = np.empty((9, self.n))
+        g = np.empty((9, self.n))
+        _check(felbm_state_export(self.handle, h, g), "felbm_state_export")
+        return h, g
+
+    def import_(self, h, g):
+        h = np.ascontiguousarray(h, dtype=np.float64)
+        g = np.ascontiguousarray(g, dtype=np.float64)
+        _check(felbm_state_import(self.handle, h, g), "felbm_state_import")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().felbm_state_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,171 @@
+"""GPU path vs FP64 oracle, element by element, through the C ABI.
+
+Tolerances (relative L2 over all nodes, per field):
+* FP64 GPU run: <= 1e-12 (reordered sums only).
+* FP32 GPU run: <= 1e-5 in velocity and C after 1000 steps (droplet cases).
+"""
+import numpy as np
+import pytest
+
+from conftest import rel_l2
+from oracle.oracle import Oracle, Params
+from paper_1608_01906_gb300 import configs, felbm, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1608_01906_gb300 import build
+
+    build.build()
+    felbm.load()
+
+
+def run_gpu(prob, precision, steps, general=False):
+    mesh = felbm.Mesh(prob.xy, prob.tri, prob.box, prob.tag, general=general)
+    st = felbm.State(mesh, felbm.make_params(precision=precision, **prob.params), prob.rho0,
+                     prob.u0, prob.p0)
+    st.step(steps)
+    m = st.moments()
+    kind = mesh.info()["kind"]
+    st.close()
+    mesh.close()
+    return m, kind
+
+
+def run_oracle(prob, steps):
+    o = Oracle(prob.xy, prob.tri, prob.box, prob.tag, Params(**prob.params))
+    o.init(prob.rho0, prob.u0, prob.p0)
+    o.step(steps)
+    return o
+
+
+def errors(m, o):
+    return {
+        "rho": rel_l2(m["rho"], o.rho),
+        "C": rel_l2(m["C"], o.C),
+        "u": rel_l2(m["u"], np.stack([o.ux, o.uy], 1)),
+        "p": rel_l2(m["p"], o.p),
+    }
+
+
+def _droplet(nx, ny, R, ratio=10.0):
+    xy, tri, box, tag = inputs.structured_mesh(nx, ny)
+    rho0, u0, p0 = inputs.droplet_fields(xy, box, (nx / 2, ny / 2), R, 1.0, 1.0 / ratio, 4.0)
+    return configs.Problem("d", xy, tri, box, tag, rho0, u0, p0,
+                           configs.params(1.0, 1.0 / ratio), 0, "fp64")
+
+
+@pytest.mark.parametrize("general", [False, True])
+def test_fp64_structured_ragged(general):
+    # 44 x 36 = 1584 nodes: several 256-node blocks and a ragged tail
+    prob = _droplet(44, 36, 11.0)
+    m, kind = run_gpu(prob, "fp64", 60, general=general)
+    assert kind == (0 if general else 1)
+    o = run_oracle(prob, 60)
+    e = errors(m, o)
+    assert max(e.values()) <= 1e-12, e
+
+
+def test_fp64_unstructured_delaunay():
+    xy, tri, box, tag = inputs.jittered_delaunay_mesh(40, 36, 0.25, seed=7)
+    rho0, u0, p0 = inputs.droplet_fields(xy, box, (20, 18), 10.0, 1.0, 0.1, 4.0)
+    prob = configs.Problem("u", xy, tri, box, tag, rho0, u0, p0, configs.params(), 0, "fp64")
+    m, kind = run_gpu(prob, "fp64", 60)
+    assert kind == 0
+    o = run_oracle(prob, 60)
+    e = errors(m, o)
+    assert max(e.values()) <= 1e-12, e
+
+
+def test_fp64_walls_rayleigh_taylor_small():
+    prob = configs.c3_rayleigh_taylor(nx=32, ny=64, steps=0)
+    prob.params["gravity"] = (0.0, -1e-4)
+    m, kind = run_gpu(prob, "fp64", 80)
+    assert kind == 1
+    o = run_oracle(prob, 80)
+    e = errors(m, o)
+    assert max(e.values()) <= 1e-12, e
+
+
+def test_fp64_mass_momentum_conserved_gpu():
+    prob = _droplet(48, 48, 12.0)
+    mesh = felbm.Mesh(prob.xy, prob.tri, prob.box, prob.tag)
+    st = felbm.State(mesh, felbm.make_params(precision="fp64", **prob.params), prob.rho0)
+    t0 = st.moments()["totals"]
+    st.step(300)
+    t1 = st.moments()["totals"]
+    assert abs(t1[0] - t0[0]) / t0[0] <= 1e-13
+    assert abs(t1[1]) / t0[0] <= 1e-13 and abs(t1[2]) / t0[0] <= 1e-13
+
+
+def test_fp32_droplet_1000_steps():
+    prob = configs.droplet_structured(64, 16.0, 10.0, steps=1000, precision="fp32")
+    m, _ = run_gpu(prob, "fp32", 1000)
+    o = run_oracle(prob, 1000)
+    e = errors(m, o)
+    print("fp32 1000-step errors", e)
+    assert e["C"] <= 1e-5 and e["u"] <= 1e-5, e
+
+
+def test_checkpoint_restart_bitwise():
+    prob = _droplet(40, 40, 10.0)
+    mesh = felbm.Mesh(prob.xy, prob.tri, prob.box, prob.tag)
+    pr = felbm.make_params(precision="fp64", **prob.params)
+    a = felbm.State(mesh, pr, prob.rho0)
+    a.step(40)
+    ma = a.moments()
+    b = felbm.State(mesh, pr, prob.rho0)
+    b.step(20)
+    h, g = b.export()
+    c = felbm.State(mesh, pr, np.ones(prob.n_nodes))
+    c.import_(h, g)
+    c.step(20)
+    mc = c.moments()
+    for k in ("rho", "u", "p"):
+        assert np.array_equal(ma[k], mc[k]), k
+
+
+def test_invalid_inputs_rejected():
+    xy, tri, box, tag = inputs.structured_mesh(8, 8)
+    bad = tri.copy()
+    bad[0] = bad[0][::-1]  # clockwise -> negative area
+    st, _ = felbm.felbm_mesh_create(xy, bad, box, felbm.flags_for(box))
+    assert st == felbm.FELBM_ERR_INVALID_MESH
+    mesh = felbm.Mesh(xy, tri, box)
+    rho = np.ones(64)
+    rho[3] = np.nan
+    st, _ = felbm.felbm_state_init(mesh.handle, felbm.make_params(1.0, 0.1, 0.01, 4, 0.5, 0.5, 0.5),
+                                   rho)
+    assert st == felbm.FELBM_ERR_INVALID_ARG
+
+
+def test_nonfinite_detected():
+    # an unstable time step (Courant 3) blows up to inf/nan without any fault
+    prob = _droplet(16, 16, 4.0)
+    prob.params["dt"] = 3.0
+    mesh = felbm.Mesh(prob.xy, prob.tri, prob.box, prob.tag)
+    st = felbm.State(mesh, felbm.make_params(precision="fp32", **prob.params), prob.rho0)
+    st.step(2000)
+    assert felbm.felbm_state_sync(st.handle) == felbm.FELBM_ERR_NONFINITE
+
+
+def test_fullsize_rayleigh_taylor_fp32_steps():
+    prob = configs.c3_rayleigh_taylor()
+    m, kind = run_gpu(prob, "fp32", 4)
+    assert kind == 1
+    o = run_oracle(prob, 4)
+    e = errors(m, o)
+    print("c3 4-step fp32 errors", e)
+    assert e["rho"] <= 1e-6 and e["u"] <= 1e-5 and e["p"] <= 1e-5, e
+
+
+def test_fullsize_unstructured_fp32_steps():
+    prob = configs.c2_unstructured_droplet()
+    m, kind = run_gpu(prob, "fp32", 50)
+    assert kind == 0
+    o = run_oracle(prob, 50)
+    e = errors(m, o)
+    print("c2 50-step fp32 errors", e)
+    assert e["C"] <= 1e-5 and e["u"] <= 1e-4, e
