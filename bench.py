@@ -1,0 +1,321 @@
+#!/usr/bin/env python
+"""Throughput of the FE-LBM binary-fluid time step on GB300.
+
+One "step" is one full time step of the method (streaming of 18 D2Q9
+populations, density-gradient / Laplacian / chemical-potential recovery,
+moments and the split collision) over the Rayleigh-Taylor workload:
+512 x 2048 structured P1 triangulation (1,048,576 nodes), walls top and
+bottom, periodic in x, Atwood 0.5, amplitude 0.1 W, Re 3000, gravity, FP32.
+
+Metric: MNUPS (million node updates per second), whole job over all ranks.
+Multi-GPU runs are independent replicas (the method's runs do not exchange
+data), so scaling is weak.  Prints one JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl felbm|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MNUPS"
+UNIT = "MNUPS"
+ALGO_BYTES_PER_NODE = {"fp32": 144, "fp64": 288}  # 18 populations read + 18 written
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="felbm", choices=["felbm", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def csrc_hash():
+    import hashlib
+
+    d = os.path.join(ROOT, "paper_1608_01906_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        h.update(f.encode())
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        for k in ("hbm_gbs", "hbm_copy_gbs", "hbm_GBps"):
+            if k in d:
+                return float(d[k]), "measured"
+    except (OSError, ValueError):
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.15)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload():
+    from paper_1608_01906_gb300 import configs
+
+    return configs.c3_rayleigh_taylor()
+
+
+def config_dict(prob, precision):
+    return {"workload": "rayleigh_taylor_512x2048", "nodes": prob.n_nodes,
+            "triangles": int(len(prob.tri)), "mesh": "structured P1 split, walls y, periodic x",
+            "lattice": "D2Q9", "precision": precision, "Re": 3000, "atwood": 0.5,
+            "dt": prob.params["dt"],
+            "l2": "inputs > L2: double-buffered state %.0f MB vs 126 MB L2, no flush"
+                  % (2 * 18 * prob.n_nodes * (4 if precision == "fp32" else 8) / 1e6),
+            "parallelism": "replicas"}
+
+
+# --------------------------------------------------------------------- oracle
+def oracle_rate(prob, seconds, max_steps=None):
+    """Time the FP64 oracle as it stands on this host (one thread)."""
+    from oracle.oracle import Oracle, Params
+
+    o = Oracle(prob.xy, prob.tri, prob.box, prob.tag, Params(**prob.params))
+    o.init(prob.rho0, prob.u0, prob.p0)
+    t = time.perf_counter()
+    o.step(1)
+    one = time.perf_counter() - t
+    n = max(1, int(seconds / max(one, 1e-9)))
+    if max_steps:
+        n = min(n, max_steps)
+    t = time.perf_counter()
+    o.step(n)
+    el = time.perf_counter() - t
+    return prob.n_nodes * n / el / 1e6, n, el
+
+
+def run_reference(args):
+    world, rank, local = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle as orc
+    from paper_1608_01906_gb300 import configs
+
+    orc.build()
+    from oracle.oracle import Oracle, Params
+
+    full = workload()
+    # each step: one oracle time step of a bounded sample of the same workload
+    # (a 64 x 256 window of the Rayleigh-Taylor problem, same physics)
+    samp = configs.c3_rayleigh_taylor(nx=64, ny=256)
+    g_full = full.params["gravity"]
+    samp.params["gravity"] = g_full
+    o = Oracle(samp.xy, samp.tri, samp.box, samp.tag, Params(**samp.params))
+    o.init(samp.rho0, samp.u0, samp.p0)
+    o.step(args.warmup)
+    t = time.perf_counter()
+    o.step(args.steps)
+    el = time.perf_counter() - t
+    v = samp.n_nodes * args.steps / el / 1e6
+    sample = ("oracle (FP64 C, 1 thread) time step on a 64x256 window of the 512x2048 "
+              "Rayleigh-Taylor problem (16,384 nodes) per step")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(full, "fp64"),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    world, rank, local = dist_env()
+    import torch
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1608_01906_gb300 import felbm
+
+    prob = workload()
+    stream = torch.cuda.Stream()
+    mesh = felbm.Mesh(prob.xy, prob.tri, prob.box, prob.tag, stream=stream.cuda_stream)
+    params = felbm.make_params(precision=args.precision, **prob.params)
+    st = felbm.State(mesh, params, prob.rho0, prob.u0, prob.p0)
+    st.step(args.warmup)
+    st.sync()
+    kind = mesh.info()["kind"]
+
+    # ---- timed region: K steps, device events on the library's stream
+    st.profile_enable(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local) if rank == 0 else None
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    ms = e0.elapsed_time(e1)
+    prof = st.profile_read()
+    st.sync()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    value = world * prob.n_nodes * args.steps / (ms * 1e-3) / 1e6
+    launches = int(sum(v[2] for v in prof.values()))
+
+    # ---- dominant kernel roofline (event-timed launches of the region)
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_ms, dom_timed, _) = dom
+    dom_avg_ms = dom_ms / max(dom_timed, 1)
+    peak, peak_kind = hbm_peak()
+    algo = ALGO_BYTES_PER_NODE[args.precision] * prob.n_nodes
+    achieved = algo / (dom_avg_ms * 1e-3) / 1e9
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tr_path):
+        with open(tr_path) as f:
+            tr = json.load(f)
+        ent = tr.get(dom_name + ":" + args.precision)
+        # counters are valid only for the kernel sources they were taken on
+        if ent and ent.get("csrc_sha256_16") == csrc_hash():
+            traffic = ent["bytes_per_launch"]
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": dom_name,
+                "kernel_ms": dom_avg_ms, "peak_source": peak_kind + " copy bandwidth",
+                "step_gbs": algo * args.steps / (ms * 1e-3) / 1e9,
+                "kernel_share": dom_ms / max(sum(v[0] for v in prof.values()), 1e-12)}
+
+    # ---- end to end through the C ABI with host buffers
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st2 = felbm.State(mesh, params, prob.rho0, prob.u0, prob.p0)
+    st2.step(args.steps)
+    mom = st2.moments()
+    t1 = time.perf_counter()
+    st2.close()
+    e2e_val = world * prob.n_nodes * args.steps / (t1 - t0) / 1e6
+    if dist:
+        t = torch.tensor([t1 - t0], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_val = world * prob.n_nodes * args.steps / float(t.item()) / 1e6
+    n = prob.n_nodes
+    h2d = (n * 8 + 2 * n * 8 + n * 8) / args.steps
+    d2h = (5 * n * 8 + 3 * 8) / args.steps
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, nsteps, el = oracle_rate(prob, args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "FP64 C oracle (1 thread), full 512x2048 mesh, %d time steps, %.1f s"
+                         % (nsteps, el)}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
+                "data": "synthetic", "config": dict(config_dict(prob, args.precision),
+                                                    mesh_kind=kind),
+                "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches * world, "clocks": clocks,
+                "kernels": {k: {"ms": v[0], "timed": v[1], "launches": v[2]}
+                            for k, v in prof.items() if v[2]},
+                "mass": float(mom["totals"][0])}
+        print(json.dumps(line), flush=True)
+    st.close()
+    mesh.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -162,6 +162,29 @@ int felbm_state_import(felbm_state *state, const double *hbar, const double *gba
 
 void felbm_state_destroy(felbm_state *state);
 
+/* ---- profiling aid (no counterpart in the paper) ------------------------
+ * Kernel kinds issued by felbm_step, reported by felbm_profile_read:
+ *   0 stream h + rho, 1 grad rho, 2 lap rho / stress / mu,
+ *   3 grad mu + stream + collide (the general four-pass step),
+ *   4 fused lattice step (one launch per step on structured meshes),
+ *   5 lattice density pre-pass. */
+#define FELBM_PROFILE_KINDS 8
+
+/* on != 0: every kernel launched by later felbm_step calls is bracketed by a
+ * pair of CUDA events on the state's stream, for the first 4096 launches after
+ * the call (later launches are counted, not timed).  on == 0 stops
+ * recording.  Errors: INVALID_ARG, OOM (event creation), CUDA. */
+int felbm_profile_enable(felbm_state *state, int on);
+
+/* Synchronise, then report per kernel kind the summed device milliseconds of
+ * the timed launches (ms), how many launches were timed (timed) and how many
+ * were issued in total since the last read or enable (launches); arrays of
+ * FELBM_PROFILE_KINDS entries, any may be NULL.  Resets the counters. */
+int felbm_profile_read(felbm_state *state, double *ms, int64_t *timed, int64_t *launches);
+
+/* Static name of kernel kind k (NULL when out of range). */
+const char *felbm_profile_kind_name(int k);
+
 /* Short static description of a status code. */
 const char *felbm_status_string(int status);
 

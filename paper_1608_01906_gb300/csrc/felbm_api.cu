@@ -103,6 +103,21 @@ static Fields<T> fields_of(felbm_state *s) {
 
 static inline unsigned nblocks(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+static constexpr size_t kProfMaxLaunches = 4096;
+
+int prof_begin(felbm_state *s, int kind) {
+    s->launches[kind]++;
+    if (!s->prof_on || s->prof_used >= kProfMaxLaunches) return -1;
+    const size_t slot = s->prof_used++;
+    s->prof_kind[slot] = kind;
+    cudaEventRecord(s->prof_ev[2 * slot], s->mesh->stream);
+    return (int)slot;
+}
+
+void prof_end(felbm_state *s, int slot) {
+    if (slot >= 0) cudaEventRecord(s->prof_ev[2 * slot + 1], s->mesh->stream);
+}
+
 template <typename T>
 static DevLattice<T> dev_lattice(const felbm_mesh *m) {
     DevLattice<T> d;
@@ -127,8 +142,12 @@ static void launch_chain(felbm_state *s, const Topo &d) {
     const Fields<T> F = fields_of<T>(s);
     const Phys<T> P = phys_of<T>(s->params);
     const unsigned g = nblocks(m->n_nodes, 256);
+    int sl = prof_begin(s, 1);
     k_grad<T, Topo><<<g, 256, 0, m->stream>>>(d, F);
+    prof_end(s, sl);
+    sl = prof_begin(s, 2);
     k_mu<T, Topo><<<g, 256, 0, m->stream>>>(d, F, P);
+    prof_end(s, sl);
 }
 
 template <typename T, typename Topo>
@@ -139,7 +158,9 @@ static void step_topo(felbm_state *s, const Topo &d, bool write_mom) {
     const unsigned g = nblocks(m->n_nodes, 256);
     const T *fin = reinterpret_cast<const T *>(s->f[s->cur]);
     T *fout = reinterpret_cast<T *>(s->f[s->cur ^ 1]);
+    int sl = prof_begin(s, 0);
     k_rho<T, Topo><<<g, 256, 0, m->stream>>>(d, fin, P.dt, F.rho);
+    prof_end(s, sl);
     launch_chain<T, Topo>(s, d);
     CollideArgs<T, Topo> A;
     A.m = d;
@@ -149,7 +170,9 @@ static void step_topo(felbm_state *s, const Topo &d, bool write_mom) {
     A.P = P;
     A.mom = write_mom ? reinterpret_cast<T *>(s->mom) : nullptr;
     A.flag = s->d_flag;
+    sl = prof_begin(s, 3);
     k_collide<T, Topo><<<g, 256, 0, m->stream>>>(A);
+    prof_end(s, sl);
     s->cur ^= 1;
 }
 
@@ -336,6 +359,8 @@ void felbm_mesh_destroy(felbm_mesh *m) { mesh_free(m); }
 
 static void state_free(felbm_state *s) {
     if (!s) return;
+    for (auto &e : s->prof_ev)
+        if (e) cudaEventDestroy(e);
     cudaFree(s->f[0]);
     cudaFree(s->f[1]);
     cudaFree(s->scratch);
@@ -515,6 +540,56 @@ void felbm_state_destroy(felbm_state *s) {
     if (!s) return;
     cudaStreamSynchronize(s->mesh->stream);
     state_free(s);
+}
+
+int felbm_profile_enable(felbm_state *s, int on) {
+    if (!s) return FELBM_ERR_INVALID_ARG;
+    if (on && s->prof_ev.empty()) {
+        try {
+            s->prof_ev.assign(2 * kProfMaxLaunches, nullptr);
+            s->prof_kind.assign(kProfMaxLaunches, 0);
+        } catch (const std::bad_alloc &) {
+            return FELBM_ERR_OOM;
+        }
+        for (auto &e : s->prof_ev) {
+            cudaError_t r = cudaEventCreate(&e);
+            if (r != cudaSuccess) return cuda_status(r);
+        }
+    }
+    s->prof_on = on != 0;
+    s->prof_used = 0;
+    for (auto &c : s->launches) c = 0;
+    return FELBM_OK;
+}
+
+int felbm_profile_read(felbm_state *s, double *ms, int64_t *timed, int64_t *launches) {
+    if (!s) return FELBM_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize(s->mesh->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    double acc[8] = {0};
+    int64_t cnt[8] = {0};
+    for (size_t k = 0; k < s->prof_used; ++k) {
+        float t = 0.f;
+        e = cudaEventElapsedTime(&t, s->prof_ev[2 * k], s->prof_ev[2 * k + 1]);
+        if (e != cudaSuccess) return cuda_status(e);
+        acc[s->prof_kind[k]] += t;
+        cnt[s->prof_kind[k]]++;
+    }
+    for (int k = 0; k < FELBM_PROFILE_KINDS; ++k) {
+        if (ms) ms[k] = acc[k];
+        if (timed) timed[k] = cnt[k];
+        if (launches) launches[k] = s->launches[k];
+        s->launches[k] = 0;
+    }
+    s->prof_used = 0;
+    return FELBM_OK;
+}
+
+const char *felbm_profile_kind_name(int k) {
+    static const char *names[FELBM_PROFILE_KINDS] = {
+        "k_rho", "k_grad", "k_mu", "k_collide", "k_lattice_step", "k_lattice_rho", "unused6",
+        "unused7"};
+    return (k >= 0 && k < FELBM_PROFILE_KINDS) ? names[k] : nullptr;
 }
 
 }  // extern "C"

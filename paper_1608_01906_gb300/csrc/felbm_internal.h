@@ -157,4 +157,17 @@ struct felbm_state {
     int *d_flag = nullptr;
     bool have_moments = false;
     int64_t steps_done = 0;
+    // profiling: event pairs around launches (felbm_profile_enable)
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_ev;     // 2 per timed launch
+    std::vector<int> prof_kind;           // kind of each timed launch
+    size_t prof_used = 0;
+    int64_t launches[8] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
+
+namespace felbm {
+// Record the launch of a kernel of the given kind; when profiling, the
+// returned event index brackets it (-1: not timed).
+int prof_begin(felbm_state *s, int kind);
+void prof_end(felbm_state *s, int slot);
+}  // namespace felbm

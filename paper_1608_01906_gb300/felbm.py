@@ -34,7 +34,9 @@ EXPORTED = [
     "felbm_mesh_create", "felbm_mesh_info", "felbm_mesh_destroy", "felbm_state_init",
     "felbm_step", "felbm_state_sync", "felbm_moments_get", "felbm_state_export",
     "felbm_state_import", "felbm_state_destroy", "felbm_status_string",
+    "felbm_profile_enable", "felbm_profile_read", "felbm_profile_kind_name",
 ]
+FELBM_PROFILE_KINDS = 8
 
 
 class FelbmError(RuntimeError):
@@ -90,6 +92,12 @@ def load(path: str = LIB_PATH):
     lib.felbm_state_destroy.argtypes = [vp]
     lib.felbm_status_string.restype = C.c_char_p
     lib.felbm_status_string.argtypes = [C.c_int]
+    lib.felbm_profile_enable.restype = C.c_int
+    lib.felbm_profile_enable.argtypes = [vp, C.c_int]
+    lib.felbm_profile_read.restype = C.c_int
+    lib.felbm_profile_read.argtypes = [vp, vp, vp, vp]
+    lib.felbm_profile_kind_name.restype = C.c_char_p
+    lib.felbm_profile_kind_name.argtypes = [C.c_int]
     _lib = lib
     _declare_extra(lib)
     return lib
@@ -248,6 +256,20 @@ class State:
         h = np.ascontiguousarray(h, dtype=np.float64)
         g = np.ascontiguousarray(g, dtype=np.float64)
         _check(felbm_state_import(self.handle, h, g), "felbm_state_import")
+
+    def profile_enable(self, on=True):
+        _check(load().felbm_profile_enable(self.handle, 1 if on else 0), "felbm_profile_enable")
+
+    def profile_read(self):
+        """Per kernel kind: (summed ms of timed launches, timed, issued)."""
+        k = FELBM_PROFILE_KINDS
+        ms = np.zeros(k)
+        timed = np.zeros(k, dtype=np.int64)
+        issued = np.zeros(k, dtype=np.int64)
+        _check(load().felbm_profile_read(self.handle, _p(ms), _p(timed), _p(issued)),
+               "felbm_profile_read")
+        names = [load().felbm_profile_kind_name(i).decode() for i in range(k)]
+        return {names[i]: (float(ms[i]), int(timed[i]), int(issued[i])) for i in range(k)}
 
     def close(self):
         if getattr(self, "handle", None):
