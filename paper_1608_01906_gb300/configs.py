@@ -9,13 +9,25 @@ restated in 2-D.  Readings fixed here (documented in the design notes):
   unstable above Courant number 0.5 for the diagonal velocities that cross
   the element diagonals (amplification 7 per step at dt = 1).  tau is the
   dimensionless relaxation parameter (nu = c_s^2 tau dt), so "tau = 0.5" and
-  "dt = 10 tau" keep their meaning.
-* rho_l = 1, rho_v = rho_l / ratio; sigma = 0.01, xi = 4 unless stated.
+  "dt = 10 tau" keep their meaning.  On the jittered Delaunay mesh dt = 0.4:
+  with tau << 1 (over-relaxation) dt = 0.5 diverges there.
+* rho_l = 1, rho_v = rho_l / ratio; sigma = 0.01.
+* Interface width xi (mesh units): 4 where stated (64x64 droplet, ratio 10);
+  12 for the ratio-1000 Delaunay droplet and 16 for the batched / served
+  droplets (ratios up to 1000).  The P1 scheme cancels the ideal-gas
+  pressure of the order-parameter streaming only to O(h^2 d^4 rho); on
+  interfaces of 4 to 8 mesh units that residual outgrows the capillary
+  forces and ratios >= 30 diverge, so the width is the smallest tried
+  (4, 8, 12, 16) that stays bounded over the run.
 * "viscosity ratio 40" is a kinematic contrast nu_v / nu_l = 40 with the
   larger relaxation parameter tau_v = 0.1 (dt = 10 tau), tau_l = 0.0025.
 * Rayleigh-Taylor: At = 0.5 -> rho_heavy = 1, rho_light = 1/3; lambda = W =
-  512; sqrt(lambda g) = 0.04 -> g = 3.125e-6; nu = lambda sqrt(lambda g)/Re;
-  equal kinematic viscosities; sigma = 1e-4 (the model needs sigma > 0).
+  512; velocity scale sqrt(lambda g) = 0.08 -> g = 1.25e-5; nu = lambda
+  sqrt(lambda g) / Re (tau = 0.082 at Re 3000); equal kinematic viscosities;
+  sigma = 1e-4 (the model needs sigma > 0).  With sqrt(lambda g) = 0.04 or
+  0.06 (tau 0.041, 0.061) a mode at the bounce-back walls grows about 4.6x
+  per 1000 steps and the run diverges.
+* Batched / served droplets: tau_l = tau_v = 0.1, dt = 0.5, xi = 16.
 """
 from __future__ import annotations
 
@@ -74,25 +86,25 @@ def c2_unstructured_droplet(n=256, R=48.0, steps=5000, seed=1608):
     nu_v/nu_l = 40, tau_v = 0.1, R = 48, FP32 vs FP64 oracle."""
     xy, tri, box, tag = inputs.jittered_delaunay_mesh(n, n, 0.25, seed)
     rho_l, rho_v = 1.0, 1.0e-3
-    rho0, u0, p0 = inputs.droplet_fields(xy, box, (n / 2, n / 2), R, rho_l, rho_v, 4.0)
+    rho0, u0, p0 = inputs.droplet_fields(xy, box, (n / 2, n / 2), R, rho_l, rho_v, 12.0)
     return Problem("c2_unstructured_droplet_%d" % n, xy, tri, box, tag, rho0, u0, p0,
-                   params(rho_l, rho_v, 0.01, 4.0, 0.0025, 0.1, 0.5), steps, "fp32",
+                   params(rho_l, rho_v, 0.01, 12.0, 0.0025, 0.1, 0.4), steps, "fp32",
                    {"n": n, "R": R, "ratio": 1000.0, "seed": seed})
 
 
-def rt_params(width=512, Re=3000.0, uref=0.04, dt=0.5):
+def rt_params(width=512, Re=3000.0, uref=0.08, dt=0.5):
     g = uref * uref / width
     nu = width * uref / Re
     tau = nu / (CS2 * dt)
     return g, nu, tau
 
 
-def c3_rayleigh_taylor(nx=512, ny=2048, steps=20000, Re=3000.0):
+def c3_rayleigh_taylor(nx=512, ny=2048, steps=20000, Re=3000.0, uref=0.08):
     """512x2048 structured split, walls top/bottom, periodic x, At = 0.5,
     amplitude 0.1 W, Re 3000, gravity body force, FP32."""
     xy, tri, box, tag = inputs.structured_mesh(nx, ny, periodic_y=False)
     rho_h, rho_lt = 1.0, 1.0 / 3.0
-    g, nu, tau = rt_params(nx, Re)
+    g, nu, tau = rt_params(nx, Re, uref)
     rho0, u0, p0 = inputs.rayleigh_taylor_fields(xy, nx, ny, rho_h, rho_lt, 4.0, 0.1 * nx, g)
     return Problem("c3_rayleigh_taylor_%dx%d" % (nx, ny), xy, tri, box, tag, rho0, u0, p0,
                    params(rho_h, rho_lt, 1e-4, 4.0, tau, tau, 0.5, (0.0, -g)), steps, "fp32",
@@ -113,6 +125,6 @@ def c4_batched(count=64, seed=1609, lo=32, hi=512):
     density ratio U[10, 1000], radius U[0.2, 0.35] of the side, FP32."""
     out = []
     for k, (side, ratio, rfrac) in enumerate(batched_sides(count, lo, hi, seed)):
-        out.append(droplet_structured(side, rfrac * side, ratio, 4.0, 0.01, 0.1, 0.1, 0.5, 0,
+        out.append(droplet_structured(side, rfrac * side, ratio, 16.0, 0.01, 0.1, 0.1, 0.5, 0,
                                       "fp32", "batch_%02d_%d" % (k, side)))
     return out

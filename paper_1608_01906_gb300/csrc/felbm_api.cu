@@ -7,6 +7,7 @@
 
 #include "felbm_internal.h"
 #include "felbm_kernels.cuh"
+#include "felbm_lattice.cuh"
 
 using namespace felbm;
 
@@ -190,12 +191,62 @@ static void init_topo(felbm_state *s, const Topo &d) {
                                               reinterpret_cast<const T *>(s->mom));
 }
 
+// Constant coefficient tables of a structured mesh for the state's dt.
+template <typename T>
+static LatCoef<T> lat_coef(const felbm_mesh *m, double dt) {
+    LatCoef<T> c;
+    for (int k = 0; k < 3; ++k)
+        for (int o = 0; o < 6; ++o) {
+            const double ax = m->sinfo.a[k][o][0], ay = m->sinfo.a[k][o][1];
+            const double bxx = m->sinfo.b[k][o][0], bxy = m->sinfo.b[k][o][1],
+                         byy = m->sinfo.b[k][o][2];
+            c.r[k][o][0] = (T)ax;
+            c.r[k][o][1] = (T)ay;
+            c.s[k][o][0] = T(0);
+            for (int a = 1; a < 9; ++a) {
+                const double ex = kEx(a), ey = kEy(a);
+                c.s[k][o][a] = (T)(ex * ax + ey * ay +
+                                   0.5 * dt * (ex * ex * bxx + 2.0 * ex * ey * bxy + ey * ey * byy));
+            }
+        }
+    return c;
+}
+
+template <typename T>
+static void step_lattice(felbm_state *s, LatArgs<T> &A, bool write_mom) {
+    const felbm_mesh *m = s->mesh;
+    A.fin = reinterpret_cast<const T *>(s->f[s->cur]);
+    A.fout = reinterpret_cast<T *>(s->f[s->cur ^ 1]);
+    A.mom = write_mom ? reinterpret_cast<T *>(s->mom) : nullptr;
+    const dim3 blk(kLTX, kLTY), grd((A.nx + kLTX - 1) / kLTX, (A.ny + kLTY - 1) / kLTY);
+    int sl = prof_begin(s, 5);
+    k_lat_rho<T><<<grd, blk, 0, m->stream>>>(A);
+    prof_end(s, sl);
+    sl = prof_begin(s, 4);
+    k_lat_step<T><<<grd, blk, lat_step_smem<T>(), m->stream>>>(A);
+    prof_end(s, sl);
+    s->cur ^= 1;
+}
+
 template <typename T>
 static void do_steps(felbm_state *s, int64_t n) {
     const felbm_mesh *m = s->mesh;
     if (m->kind == 1) {
-        const DevLattice<T> d = dev_lattice<T>(m);
-        for (int64_t k = 0; k < n; ++k) step_topo<T>(s, d, k == n - 1);
+        static bool attr_set = false;  // once per instantiation (per process)
+        if (!attr_set) {
+            cudaFuncSetAttribute(k_lat_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)lat_step_smem<T>());
+            attr_set = true;
+        }
+        LatArgs<T> A;
+        A.nx = m->sinfo.nx;
+        A.ny = m->sinfo.ny;
+        A.walls = m->sinfo.walls ? 1 : 0;
+        A.c = lat_coef<T>(m, s->params.dt);
+        A.P = phys_of<T>(s->params);
+        A.rho = fields_of<T>(s).rho;
+        A.flag = s->d_flag;
+        for (int64_t k = 0; k < n; ++k) step_lattice<T>(s, A, k == n - 1);
     } else {
         const DevCSR<T> d = dev_csr<T>(m);
         for (int64_t k = 0; k < n; ++k) step_topo<T>(s, d, k == n - 1);

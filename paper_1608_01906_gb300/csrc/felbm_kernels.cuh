@@ -137,6 +137,12 @@ __global__ void __launch_bounds__(256) k_grad(Topo m, Fields<T> F) {
     F.dry[i] = gy;
 }
 
+// mu_phi = 4 beta (rho - rho_v)(rho - rho_l)(rho - (rho_v + rho_l)/2).
+template <typename T>
+__device__ __forceinline__ T mu_bulk(const Phys<T> &P, T r) {
+    return T(4) * P.beta * (r - P.rho_v) * (r - P.rho_l) * (r - T(0.5) * (P.rho_v + P.rho_l));
+}
+
 // lap rho = R_x(d_x rho) + R_y(d_y rho);
 // K_x = kappa [R_x((d_y rho)^2) - R_y(d_x rho d_y rho)],
 // K_y = kappa [R_y((d_x rho)^2) - R_x(d_x rho d_y rho)]
@@ -148,34 +154,113 @@ __global__ void __launch_bounds__(256) k_mu(Topo m, Fields<T> F, Phys<T> P) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m.n) return;
     const T gxi = F.drx[i], gyi = F.dry[i];
-    const T xxi = gxi * gxi, xyi = gxi * gyi, yyi = gyi * gyi;
     T lap = T(0), kx = T(0), ky = T(0);
     m.for_each(i, [&](int32_t j, T ax, T ay, T, T, T) {
         const T gxj = __ldg(F.drx + j), gyj = __ldg(F.dry + j);
         lap += ax * (gxj - gxi) + ay * (gyj - gyi);
-        const T dxx = gxj * gxj - xxi, dxy = gxj * gyj - xyi, dyy = gyj * gyj - yyi;
+        // differences of the gradient products in product form (no
+        // cancellation between two squares of nearly equal size)
+        const T ddx = gxj - gxi, ddy = gyj - gyi;
+        const T dxx = ddx * (gxj + gxi), dxy = gxj * ddy + gyi * ddx, dyy = ddy * (gyj + gyi);
         kx += ax * dyy - ay * dxy;
         ky += ay * dxx - ax * dxy;
     });
-    const T r = F.rho[i];
-    const T mub = T(4) * P.beta * (r - P.rho_v) * (r - P.rho_l) * (r - T(0.5) * (P.rho_v + P.rho_l));
-    F.mu[i] = mub - P.kappa * lap;
+    F.mu[i] = mu_bulk<T>(P, F.rho[i]) - P.kappa * lap;
     F.kx[i] = P.kappa * kx;
     F.ky[i] = P.kappa * ky;
 }
 
-// Local collision of one node (Sec. 2.2).  In: streamed h*, g* (9 each),
-// rho, grad rho, grad mu, K.  Out: next stored pre-collided values, moments.
+// Local collision of one node (Sec. 2.2), split in two so that callers can
+// keep the streamed populations outside registers:
+//   collide_prep  moments (Eqs. velocity, pressure), tau, and the per-node
+//                 scalars of the equilibria and sources;
+//   collide_pop   the update of population a.
 // With eq and source S of the node, the post-streaming collision
 //   psi = psi* + 2tau/(2tau+1) (-(psi* - eq)/(2tau) + S)
-// followed by the pre-streaming collision
+// followed by the pre-streaming collision of the next step
 //   psibar = psi + (-(psi - eq)/(2tau) + S)
 // equals psibar = eq + S + w (psi* - eq + S), w = (2tau - 1)/(2tau + 1).
+template <typename T>
+struct CollidePrep {
+    T r, ux, uy, p, w, hdt, Xx, Xy, uX, uD, uK, uu, dux, duy, udu, drx, dry, kx, ky;
+};
+
+// sg = sum_a g*_a, mx, my = sum_a e_a g*_a of the streamed (and bounced) g.
+template <typename T>
+__device__ __forceinline__ CollidePrep<T> collide_prep(const Phys<T> &P, T sg, T mx, T my, T r,
+                                                       T drx, T dry, T dmx, T dmy, T kx, T ky) {
+    constexpr T cs2 = T(1) / T(3);
+    CollidePrep<T> c;
+    c.hdt = T(0.5) * P.dt;
+    const T inv_r = T(1) / r;
+    c.r = r;
+    c.ux = (mx + c.hdt * kx + c.hdt * r * P.gx) * inv_r;
+    c.uy = (my + c.hdt * ky + c.hdt * r * P.gy) * inv_r;
+    c.p = cs2 * (sg + c.hdt * (c.ux * drx + c.uy * dry));
+    T C = (r - P.rho_v) / (P.rho_l - P.rho_v);
+    C = C < T(0) ? T(0) : (C > T(1) ? T(1) : C);
+    const T tau = T(1) / (C * P.inv_tau_l + (T(1) - C) * P.inv_tau_v);
+    c.w = (T(2) * tau - T(1)) / (T(2) * tau + T(1));
+    c.Xx = cs2 * drx - r * dmx;  // F: c_s^2 grad rho - rho grad mu
+    c.Xy = cs2 * dry - r * dmy;
+    c.uX = c.ux * c.Xx + c.uy * c.Xy;
+    c.uD = c.ux * drx + c.uy * dry;
+    c.uK = c.ux * kx + c.uy * ky;
+    c.uu = c.ux * c.ux + c.uy * c.uy;
+    c.dux = P.gx * P.dt;  // exact-difference du = g dt
+    c.duy = P.gy * P.dt;
+    c.udu = c.dux * (T(2) * c.ux + c.dux) + c.duy * (T(2) * c.uy + c.duy);
+    c.drx = drx;
+    c.dry = dry;
+    c.kx = kx;
+    c.ky = ky;
+    return c;
+}
+
+template <typename T, int A>
+__device__ __forceinline__ void collide_pop(const CollidePrep<T> &c, T hs, T gs, T &hout, T &gout) {
+    constexpr int ex = kEx(A), ey = kEy(A);
+    constexpr T wa = kW<T>(A);
+    const T eu = T(ex) * c.ux + T(ey) * c.uy;
+    // Gamma - w formed directly: forming Gamma ~ w first and subtracting w
+    // would cancel away the momentum part rho w 3 e.u in FP32.
+    const T gmw = wa * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * c.uu);
+    const T gam = wa + gmw;
+    const T eX = T(ex) * c.Xx + T(ey) * c.Xy;
+    const T eD = T(ex) * c.drx + T(ey) * c.dry;
+    const T eK = T(ex) * c.kx + T(ey) * c.ky;
+    const T edu = T(ex) * c.dux + T(ey) * c.duy;
+    const T heq = c.r * gam;
+    const T geq = wa * T(3) * c.p + c.r * gmw;
+    const T Fa = c.hdt * T(3) * (eX - c.uX) * gam;
+    const T Ga = c.hdt * (eD - c.uD) * gmw + c.hdt * T(3) * (eK - c.uK) * gam;
+    // 1/2 [g_eq(u + du) - g_eq(u)] = rho/2 [Gamma(u + du) - Gamma(u)]
+    const T Ba = T(0.5) * c.r * wa * (T(3) * edu + T(4.5) * edu * (T(2) * eu + edu) - T(1.5) * c.udu);
+    const T Sg = Ga + Ba;
+    hout = heq + Fa + c.w * (hs - heq + Fa);
+    gout = geq + Sg + c.w * (gs - geq + Sg);
+}
+
+template <typename T>
+__device__ __forceinline__ void collide_pop_rt(const CollidePrep<T> &c, int a, T hs, T gs, T &ho,
+                                               T &go) {
+    switch (a) {
+        case 0: collide_pop<T, 0>(c, hs, gs, ho, go); break;
+        case 1: collide_pop<T, 1>(c, hs, gs, ho, go); break;
+        case 2: collide_pop<T, 2>(c, hs, gs, ho, go); break;
+        case 3: collide_pop<T, 3>(c, hs, gs, ho, go); break;
+        case 4: collide_pop<T, 4>(c, hs, gs, ho, go); break;
+        case 5: collide_pop<T, 5>(c, hs, gs, ho, go); break;
+        case 6: collide_pop<T, 6>(c, hs, gs, ho, go); break;
+        case 7: collide_pop<T, 7>(c, hs, gs, ho, go); break;
+        default: collide_pop<T, 8>(c, hs, gs, ho, go); break;
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void collide_node(const Phys<T> &P, const T *hs, const T *gs, T r,
                                              T drx, T dry, T dmx, T dmy, T kx, T ky, T *hout,
                                              T *gout, T &ux, T &uy, T &p) {
-    constexpr T cs2 = T(1) / T(3);
     T mx = T(0), my = T(0), sg = T(0);
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
@@ -183,46 +268,12 @@ __device__ __forceinline__ void collide_node(const Phys<T> &P, const T *hs, cons
         if (kEx(a)) mx += T(kEx(a)) * gs[a];
         if (kEy(a)) my += T(kEy(a)) * gs[a];
     }
-    const T hdt = T(0.5) * P.dt;
-    const T inv_r = T(1) / r;
-    ux = (mx + hdt * kx + hdt * r * P.gx) * inv_r;
-    uy = (my + hdt * ky + hdt * r * P.gy) * inv_r;
-    p = cs2 * (sg + hdt * (ux * drx + uy * dry));
-    T C = (r - P.rho_v) / (P.rho_l - P.rho_v);
-    C = C < T(0) ? T(0) : (C > T(1) ? T(1) : C);
-    const T tau = T(1) / (C * P.inv_tau_l + (T(1) - C) * P.inv_tau_v);
-    const T w = (T(2) * tau - T(1)) / (T(2) * tau + T(1));
-    // force vectors
-    const T Xx = cs2 * drx - r * dmx, Xy = cs2 * dry - r * dmy;  // F: c_s^2 grad rho - rho grad mu
-    const T uX = ux * Xx + uy * Xy, uD = ux * drx + uy * dry, uK = ux * kx + uy * ky;
-    const T uu = ux * ux + uy * uy;
-    const T dux = P.gx * P.dt, duy = P.gy * P.dt;  // exact-difference du = g dt
-    const T udu = dux * (T(2) * ux + dux) + duy * (T(2) * uy + duy);
-    const T p3 = T(3) * p;
+    const CollidePrep<T> c = collide_prep<T>(P, sg, mx, my, r, drx, dry, dmx, dmy, kx, ky);
 #pragma unroll
-    for (int a = 0; a < 9; ++a) {
-        const int ex = kEx(a), ey = kEy(a);
-        const T wa = kW<T>(a);
-        const T eu = T(ex) * ux + T(ey) * uy;
-        // Gamma - w computed directly: forming Gamma ~ w first and subtracting
-        // w would cancel away the momentum part rho w 3 e.u in FP32.
-        const T gmw = wa * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * uu);
-        const T gam = wa + gmw;
-        const T eX = T(ex) * Xx + T(ey) * Xy;
-        const T eD = T(ex) * drx + T(ey) * dry;
-        const T eK = T(ex) * kx + T(ey) * ky;
-        const T edu = T(ex) * dux + T(ey) * duy;
-        const T heq = r * gam;
-        const T geq = wa * p3 + r * gmw;
-        const T Fa = hdt * T(3) * (eX - uX) * gam;
-        const T Ga = hdt * (eD - uD) * gmw + hdt * T(3) * (eK - uK) * gam;
-        // 1/2 [g_eq(u + du) - g_eq(u)] = rho/2 [Gamma(u + du) - Gamma(u)]
-        const T Ba = T(0.5) * r * wa *
-                     (T(3) * edu + T(4.5) * edu * (T(2) * eu + edu) - T(1.5) * udu);
-        const T Sh = Fa, Sg = Ga + Ba;
-        hout[a] = heq + Sh + w * (hs[a] - heq + Sh);
-        gout[a] = geq + Sg + w * (gs[a] - geq + Sg);
-    }
+    for (int a = 0; a < 9; ++a) collide_pop_rt<T>(c, a, hs[a], gs[a], hout[a], gout[a]);
+    ux = c.ux;
+    uy = c.uy;
+    p = c.p;
 }
 
 template <typename T, typename Topo>
