@@ -185,6 +185,36 @@ int felbm_profile_read(felbm_state *state, double *ms, int64_t *timed, int64_t *
 /* Static name of kernel kind k (NULL when out of range). */
 const char *felbm_profile_kind_name(int k);
 
+/* ---- allocation-free reduction (no counterpart in the paper) ------------
+ * The same FP64 totals as felbm_moments_get -- sum_i w_i rho_i,
+ * sum_i w_i rho_i ux_i, sum_i w_i rho_i uy_i -- over device arrays the
+ * caller owns, for callers whose device memory belongs to another allocator
+ * (a framework's caching allocator, an arena sized once at start-up) and who
+ * therefore cannot let this library call cudaMalloc.  This entry point
+ * allocates nothing: its scratch, 1024 x 3 partial sums (24 KiB), is a
+ * fixed array in the library's device image that every GPU which loads the
+ * library holds until the process exits.
+ *   rho, ux, uy  device arrays of n values, double (FELBM_FP64) or float
+ *                (FELBM_FP32) as precision says.
+ *   weight       device array of n doubles (e.g. the lumped nodal mass), or
+ *                NULL for unit weights.
+ *   n            1 .. FELBM_NALLOC_MAX_NODES; larger n returns
+ *                FELBM_ERR_INVALID_ARG.
+ *   totals       device array of 3 doubles, written by the call.
+ *   stream       cudaStream_t (as void*) the work is issued on; NULL = the
+ *                legacy default stream.  The call returns after enqueueing.
+ * The first call on a device, with that device current, looks up the device
+ * address of the scratch array; make that first call before any stream
+ * capture.  All calls on a device share the one scratch array and leave
+ * their partial sums in it (each call writes every slot it reads, so nothing
+ * needs clearing); calls whose work overlaps on the GPU -- on different
+ * streams, or from different host threads without ordering -- race on it.
+ * Errors: INVALID_ARG (NULL pointer, n out of range, bad precision),
+ * UNSUPPORTED (device ordinal >= 64), CUDA. */
+#define FELBM_NALLOC_MAX_NODES (1LL << 30)
+int felbm_totals_nalloc(const void *rho, const void *ux, const void *uy, const double *weight,
+                        int64_t n, int32_t precision, double *totals, void *stream);
+
 /* Short static description of a status code. */
 const char *felbm_status_string(int status);
 
