@@ -162,6 +162,33 @@ int felbm_state_import(felbm_state *state, const double *hbar, const double *gba
 
 void felbm_state_destroy(felbm_state *state);
 
+/* ---- batched launch (many runs per launch; the paper has a single run) ---
+ * A batch advances many states on structured meshes (felbm_mesh_info kind
+ * 1) of any sizes in one persistent, cooperative launch per time step: the
+ * density pass of every 32 x 8 tile of every mesh, a grid-wide barrier, then
+ * the step pass of every tile.  Each state's results are the same as from
+ * felbm_step alone (same per-node arithmetic).  Step pairs are replayed from
+ * a CUDA graph.  With FELBM_BATCH_AUTOTUNE the first felbm_batch_step long
+ * enough to afford it times real steps under each candidate (blocks per SM
+ * from 1 to the co-resident maximum, tile order mesh-major or interleaved)
+ * and keeps the fastest; those steps count toward n_steps.
+ *   states   n_states distinct states, same precision, meshes on the same
+ *            stream; the batch borrows them (they must outlive it).
+ * Stepping a member state on its own between batch steps is allowed; the
+ * next felbm_batch_step then waits for the stream and rebuilds its tables.
+ * Errors: INVALID_ARG, UNSUPPORTED (a general mesh), OOM, CUDA; TIMEOUT from
+ * felbm_batch_sync if the barrier's bounded wait ever gave up. */
+#define FELBM_BATCH_AUTOTUNE 0x1u
+int felbm_batch_create(felbm_state *const *states, int32_t n_states, uint32_t flags,
+                       felbm_batch **out);
+int felbm_batch_step(felbm_batch *batch, int64_t n_steps);
+int felbm_batch_sync(felbm_batch *batch);
+/* Chosen configuration and counters; any output pointer may be NULL.
+ * tile_order: 0 mesh-major, 1 interleaved across meshes. */
+int felbm_batch_info(const felbm_batch *batch, int32_t *blocks_per_sm, int32_t *tile_order,
+                     int32_t *n_tiles, int64_t *launches, double *tuned_ms_per_step);
+void felbm_batch_destroy(felbm_batch *batch);
+
 /* ---- profiling aid (no counterpart in the paper) ------------------------
  * Kernel kinds issued by felbm_step, reported by felbm_profile_read:
  *   0 stream h + rho, 1 grad rho, 2 lap rho / stress / mu,

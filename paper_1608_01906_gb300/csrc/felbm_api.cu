@@ -319,9 +319,25 @@ int felbm_mesh_create(const double *xy, int64_t n_nodes, const int32_t *tri, int
     m->n_tri = n_tri;
     m->flags = flags;
     m->stream = reinterpret_cast<cudaStream_t>(stream);
-    int st;
+    // cheap checks every path relies on
+    if (((flags & FELBM_PERIODIC_X) && !(box[0] > 0.0)) ||
+        ((flags & FELBM_PERIODIC_Y) && !(box[1] > 0.0))) {
+        delete m;
+        return FELBM_ERR_INVALID_ARG;
+    }
+    for (int64_t t = 0; t < 3 * n_tri; ++t)
+        if (tri[t] < 0 || tri[t] >= n_nodes) {
+            delete m;
+            return FELBM_ERR_INVALID_MESH;
+        }
+    int st = FELBM_OK;
+    std::vector<double> lattice_mass;
     try {
-        st = build_csr(xy, n_nodes, tri, n_tri, box, flags, node_tag, m->host);
+        // a structured lattice needs no assembled CSR: its three row kinds'
+        // coefficients come from the triangles around representative nodes
+        if (!(flags & FELBM_MESH_GENERAL))
+            detect_structured(xy, n_nodes, tri, n_tri, box, flags, node_tag, m->sinfo, lattice_mass);
+        if (!m->sinfo.ok) st = build_csr(xy, n_nodes, tri, n_tri, box, flags, node_tag, m->host);
     } catch (const std::bad_alloc &) {
         st = FELBM_ERR_OOM;
     }
@@ -329,8 +345,6 @@ int felbm_mesh_create(const double *xy, int64_t n_nodes, const int32_t *tri, int
         delete m;
         return st;
     }
-    if (!(flags & FELBM_MESH_GENERAL))
-        detect_structured(xy, n_nodes, tri, n_tri, box, flags, node_tag, m->host, m->sinfo);
     m->kind = m->sinfo.ok ? 1 : 0;
     const HostCSR &H = m->host;
     const size_t N = (size_t)n_nodes, nnz = H.col.size();
@@ -356,12 +370,9 @@ int felbm_mesh_create(const double *xy, int64_t n_nodes, const int32_t *tri, int
         return rs;
     }
     // uploads (synchronous: host vectors are temporaries of this call)
-    std::vector<double> mass_caller;
     if (m->kind == 1) {
         // structured kernels use the caller's (lattice) order
-        mass_caller.resize(N);
-        for (size_t k = 0; k < N; ++k) mass_caller[H.perm[k]] = H.mass[k];
-        e = cudaMemcpy(m->d_mass, mass_caller.data(), N * sizeof(double), cudaMemcpyHostToDevice);
+        e = cudaMemcpy(m->d_mass, lattice_mass.data(), N * sizeof(double), cudaMemcpyHostToDevice);
     } else {
         e = cudaMemcpy(m->d_mass, H.mass.data(), N * sizeof(double), cudaMemcpyHostToDevice);
         if (e == cudaSuccess)

@@ -1,0 +1,531 @@
+// Batched time step: many structured-lattice states of uneven size advance
+// in one persistent, cooperative launch per time step.
+//
+// The launch walks a global list of 32 x 8 tiles of all meshes twice: the
+// density pass for every tile, a grid-wide barrier, then the step pass for
+// every tile (the per-tile code is the one of the single-mesh kernels, so a
+// state's results do not depend on which other states share the launch).
+// The grid is sized to the co-resident block count (cooperative launch), the
+// barrier is a counter with a bounded spin: a wait that gives up sets an
+// error word the host reports as FELBM_ERR_TIMEOUT.  Launches of whole step
+// pairs are captured in a CUDA graph.  An autotuner picks the blocks per SM
+// and the tile order by timing real steps (all candidates compute identical
+// values, so tuning steps are ordinary steps of the runs).
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "felbm_internal.h"
+#include "felbm_kernels.cuh"
+#include "felbm_lattice.cuh"
+
+namespace felbm {
+
+struct TileRef {
+    uint16_t mesh, bx, by, pad;
+};
+
+template <typename T>
+struct BatchMesh {
+    LatArgs<T> a;  // fin / fout / mom are set per launch from f[], c0
+    T *f[2];
+    T *mom;
+    int32_t c0;
+};
+
+template <typename T>
+struct BatchArgs {
+    const BatchMesh<T> *meshes;
+    const TileRef *tiles;
+    int32_t ntiles;
+    unsigned *bar;  // [0] arrival count, [1] generation
+    int *err;
+    int parity;
+    int write_mom;
+};
+
+// Grid-wide barrier for a cooperative launch.  The spin is bounded
+// (2^26 polls of ~64 ns); on giving up it records bit 2 in *err and returns.
+__device__ __forceinline__ void grid_barrier(unsigned *bar, int *err) {
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        volatile unsigned *gen = bar + 1;
+        const unsigned g = *gen;
+        __threadfence();
+        const unsigned nb = gridDim.x * gridDim.y;
+        if (atomicAdd(bar, 1u) == nb - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            unsigned spins = 0;
+            while (*gen == g) {
+                if (++spins > (1u << 26)) {
+                    atomicOr(err, 2);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ void load_mesh(const BatchArgs<T> &B, int m, LatArgs<T> &sA, int &cur) {
+    if (m == cur) return;
+    const BatchMesh<T> &bm = B.meshes[m];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    static_assert(sizeof(LatArgs<T>) % 4 == 0, "word copy");
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(&bm.a);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(&sA);
+    for (int w = tid; w < (int)(sizeof(LatArgs<T>) / 4); w += blockDim.x * blockDim.y) dst[w] = src[w];
+    __syncthreads();
+    if (tid == 0) {
+        const int c = bm.c0 ^ B.parity;
+        sA.fin = bm.f[c];
+        sA.fout = bm.f[c ^ 1];
+        sA.mom = B.write_mom ? bm.mom : nullptr;
+    }
+    __syncthreads();
+    cur = m;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kLTX *kLTY, 3) k_batch_step(BatchArgs<T> B) {
+    __shared__ StepSmem<T> S;
+    __shared__ __align__(16) LatArgs<T> sA;
+    extern __shared__ __align__(16) unsigned char bdsm[];
+    int cur = -1;
+    for (int t = blockIdx.x; t < B.ntiles; t += gridDim.x) {
+        const TileRef r = B.tiles[t];
+        load_mesh<T>(B, r.mesh, sA, cur);
+        lat_rho_tile<T>(sA, r.bx, r.by, reinterpret_cast<T (*)[kPN]>(bdsm));
+    }
+    grid_barrier(B.bar, B.err);
+    for (int t = blockIdx.x; t < B.ntiles; t += gridDim.x) {
+        const TileRef r = B.tiles[t];
+        load_mesh<T>(B, r.mesh, sA, cur);
+        lat_step_tile<T>(sA, r.bx, r.by, S, bdsm);
+    }
+}
+
+template <typename T>
+static LatCoef<T> lat_coef_b(const felbm_mesh *m, double dt) {
+    LatCoef<T> c;
+    for (int k = 0; k < 3; ++k)
+        for (int o = 0; o < 6; ++o) {
+            const double ax = m->sinfo.a[k][o][0], ay = m->sinfo.a[k][o][1];
+            const double bxx = m->sinfo.b[k][o][0], bxy = m->sinfo.b[k][o][1],
+                         byy = m->sinfo.b[k][o][2];
+            c.r[k][o][0] = (T)ax;
+            c.r[k][o][1] = (T)ay;
+            c.s[k][o][0] = T(0);
+            for (int a = 1; a < 9; ++a) {
+                const double ex = kEx(a), ey = kEy(a);
+                c.s[k][o][a] = (T)(ex * ax + ey * ay +
+                                   0.5 * dt * (ex * ex * bxx + 2.0 * ex * ey * bxy + ey * ey * byy));
+            }
+        }
+    return c;
+}
+
+template <typename T>
+static Phys<T> phys_b(const felbm_params &p) {
+    const double d = p.rho_l - p.rho_v;
+    Phys<T> P;
+    P.rho_l = (T)p.rho_l;
+    P.rho_v = (T)p.rho_v;
+    P.beta = (T)(12.0 * p.sigma / (p.xi * d * d * d * d));
+    P.kappa = (T)(1.5 * p.xi * p.sigma / (d * d));
+    P.inv_tau_l = (T)(1.0 / p.tau_l);
+    P.inv_tau_v = (T)(1.0 / p.tau_v);
+    P.dt = (T)p.dt;
+    P.gx = (T)p.gravity[0];
+    P.gy = (T)p.gravity[1];
+    return P;
+}
+
+}  // namespace felbm
+
+using namespace felbm;
+
+struct felbm_batch {
+    std::vector<felbm_state *> states;
+    int esize = 4;
+    cudaStream_t stream = nullptr;
+    void *d_meshes = nullptr;
+    TileRef *d_tiles = nullptr;
+    int32_t ntiles = 0;
+    unsigned *d_bar = nullptr;
+    int *d_err = nullptr;
+    int parity = 0;
+    int sm_count = 0, max_bps = 1;
+    int bps = 1, order = 0;  // chosen configuration
+    bool autotune = false, tuned = false;
+    double tuned_ms = 0.0;
+    cudaGraphExec_t graph = nullptr;
+    bool graph_failed = false;
+    int64_t launches = 0;
+    std::vector<TileRef> tiles_mesh_major, tiles_interleaved;
+    std::vector<int> c0;  // each state's current buffer when descriptors were built
+};
+
+static int b_status(cudaError_t e) {
+    if (e == cudaSuccess) return FELBM_OK;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return FELBM_ERR_OOM;
+    }
+    return FELBM_ERR_CUDA;
+}
+
+static size_t batch_smem(int esize) {
+    return esize == 8 ? lat_step_smem<double>() : lat_step_smem<float>();
+}
+
+template <typename T>
+static cudaError_t batch_launch(felbm_batch *b, int parity, int write_mom) {
+    BatchArgs<T> B;
+    B.meshes = reinterpret_cast<const BatchMesh<T> *>(b->d_meshes);
+    B.tiles = b->d_tiles;
+    B.ntiles = b->ntiles;
+    B.bar = b->d_bar;
+    B.err = b->d_err;
+    B.parity = parity;
+    B.write_mom = write_mom;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(b->bps * b->sm_count));
+    cfg.blockDim = dim3(kLTX, kLTY);
+    cfg.dynamicSmemBytes = batch_smem(sizeof(T));
+    cfg.stream = b->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    b->launches++;
+    return cudaLaunchKernelEx(&cfg, k_batch_step<T>, B);
+}
+
+static cudaError_t launch_any(felbm_batch *b, int parity, int write_mom) {
+    return b->esize == 8 ? batch_launch<double>(b, parity, write_mom)
+                         : batch_launch<float>(b, parity, write_mom);
+}
+
+static cudaError_t upload_tiles(felbm_batch *b) {
+    const std::vector<TileRef> &src = b->order ? b->tiles_interleaved : b->tiles_mesh_major;
+    return cudaMemcpy(b->d_tiles, src.data(), src.size() * sizeof(TileRef), cudaMemcpyHostToDevice);
+}
+
+static void drop_graph(felbm_batch *b) {
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+}
+
+// Graph of two steps starting at parity 0, without moments.
+static void build_graph(felbm_batch *b) {
+    drop_graph(b);
+    if (b->graph_failed) return;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        b->graph_failed = true;
+        return;
+    }
+    const int64_t l0 = b->launches;
+    cudaError_t e1 = launch_any(b, 0, 0);
+    cudaError_t e2 = launch_any(b, 1, 0);
+    b->launches = l0;
+    cudaError_t e3 = cudaStreamEndCapture(b->stream, &g);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess ||
+        cudaGraphInstantiate(&b->graph, g, 0) != cudaSuccess) {
+        cudaGetLastError();
+        b->graph = nullptr;
+        b->graph_failed = true;
+    }
+    if (g) cudaGraphDestroy(g);
+}
+
+template <typename T>
+static int setup_meshes(felbm_batch *b) {
+    const size_t n = b->states.size();
+    std::vector<BatchMesh<T>> hm(n);
+    for (size_t k = 0; k < n; ++k) {
+        felbm_state *s = b->states[k];
+        const felbm_mesh *m = s->mesh;
+        BatchMesh<T> &bm = hm[k];
+        std::memset(&bm, 0, sizeof(bm));
+        bm.a.nx = m->sinfo.nx;
+        bm.a.ny = m->sinfo.ny;
+        bm.a.walls = m->sinfo.walls ? 1 : 0;
+        bm.a.c = lat_coef_b<T>(m, s->params.dt);
+        bm.a.P = phys_b<T>(s->params);
+        bm.a.rho = reinterpret_cast<T *>(s->scratch);  // first scratch field
+        bm.a.flag = s->d_flag;
+        bm.f[0] = reinterpret_cast<T *>(s->f[0]);
+        bm.f[1] = reinterpret_cast<T *>(s->f[1]);
+        bm.mom = reinterpret_cast<T *>(s->mom);
+        bm.c0 = s->cur;
+        b->c0[k] = s->cur;
+    }
+    return b_status(cudaMemcpy(b->d_meshes, hm.data(), n * sizeof(BatchMesh<T>), cudaMemcpyHostToDevice));
+}
+
+template <typename T>
+static int occupancy(felbm_batch *b) {
+    int bps = 0;
+    cudaError_t e = cudaFuncSetAttribute(k_batch_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)batch_smem(sizeof(T)));
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_batch_step<T>, kLTX * kLTY,
+                                                          batch_smem(sizeof(T)));
+    if (e != cudaSuccess) return b_status(e);
+    b->max_bps = std::max(1, bps);
+    return FELBM_OK;
+}
+
+// A state stepped on its own since the descriptors were built no longer
+// matches them: wait for the stream (no launch may still read the
+// descriptors) and rebuild them from the states' current buffers.
+static int sync_descriptors(felbm_batch *b) {
+    bool stale = false;
+    for (size_t k = 0; k < b->states.size(); ++k)
+        stale |= b->states[k]->cur != (b->c0[k] ^ b->parity);
+    if (!stale) return FELBM_OK;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return b_status(e);
+    b->parity = 0;
+    return b->esize == 8 ? setup_meshes<double>(b) : setup_meshes<float>(b);
+}
+
+extern "C" {
+
+int felbm_batch_create(felbm_state *const *states, int32_t n_states, uint32_t flags,
+                       felbm_batch **out) {
+    if (!states || n_states < 1 || n_states > 65535 || !out) return FELBM_ERR_INVALID_ARG;
+    if (flags & ~FELBM_BATCH_AUTOTUNE) return FELBM_ERR_INVALID_ARG;
+    felbm_batch *b = new (std::nothrow) felbm_batch();
+    if (!b) return FELBM_ERR_OOM;
+    try {
+        b->states.assign(states, states + n_states);
+    } catch (const std::bad_alloc &) {
+        delete b;
+        return FELBM_ERR_OOM;
+    }
+    for (int32_t k = 0; k < n_states; ++k) {
+        felbm_state *s = states[k];
+        if (!s || s->mesh->kind != 1 || (int)s->esize != (int)states[0]->esize ||
+            s->mesh->stream != states[0]->mesh->stream || s->mesh->sinfo.nx > 65535 * kLTX ||
+            s->mesh->sinfo.ny > 65535 * kLTY) {
+            delete b;
+            return (s && s->mesh->kind != 1) ? FELBM_ERR_UNSUPPORTED : FELBM_ERR_INVALID_ARG;
+        }
+        for (int32_t q = 0; q < k; ++q)
+            if (states[q] == s) {
+                delete b;
+                return FELBM_ERR_INVALID_ARG;
+            }
+    }
+    b->esize = (int)states[0]->esize;
+    b->c0.assign(n_states, 0);
+    b->stream = states[0]->mesh->stream;
+    b->autotune = (flags & FELBM_BATCH_AUTOTUNE) != 0;
+    // tile lists: mesh-major and round-robin over meshes (largest first)
+    std::vector<std::vector<TileRef>> per(n_states);
+    for (int32_t k = 0; k < n_states; ++k) {
+        const int tx = (states[k]->mesh->sinfo.nx + kLTX - 1) / kLTX;
+        const int ty = (states[k]->mesh->sinfo.ny + kLTY - 1) / kLTY;
+        for (int by = 0; by < ty; ++by)
+            for (int bx = 0; bx < tx; ++bx)
+                per[k].push_back(TileRef{(uint16_t)k, (uint16_t)bx, (uint16_t)by, 0});
+        b->tiles_mesh_major.insert(b->tiles_mesh_major.end(), per[k].begin(), per[k].end());
+    }
+    {
+        std::vector<size_t> pos(n_states, 0);
+        bool any = true;
+        while (any) {
+            any = false;
+            for (int32_t k = 0; k < n_states; ++k)
+                if (pos[k] < per[k].size()) {
+                    b->tiles_interleaved.push_back(per[k][pos[k]++]);
+                    any = true;
+                }
+        }
+    }
+    b->ntiles = (int32_t)b->tiles_mesh_major.size();
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
+    const size_t mesh_bytes = (size_t)n_states * (b->esize == 8 ? sizeof(BatchMesh<double>)
+                                                                : sizeof(BatchMesh<float>));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_meshes, mesh_bytes);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_tiles, (size_t)b->ntiles * sizeof(TileRef));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_bar, 2 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(b->d_bar, 0, 2 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, sizeof(int));
+    int st = b_status(e);
+    if (st == FELBM_OK) st = b->esize == 8 ? occupancy<double>(b) : occupancy<float>(b);
+    if (st == FELBM_OK) {
+        b->bps = b->max_bps;
+        b->order = 0;
+        st = b_status(upload_tiles(b));
+    }
+    if (st == FELBM_OK) st = b->esize == 8 ? setup_meshes<double>(b) : setup_meshes<float>(b);
+    if (st != FELBM_OK) {
+        felbm_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return FELBM_OK;
+}
+
+// Time `trial` direct steps under each candidate (blocks per SM x tile
+// order) and keep the fastest.  Steps taken here are ordinary steps.
+static int autotune(felbm_batch *b, int trial, int64_t *used) {
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return FELBM_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return FELBM_ERR_CUDA;
+    }
+    double best = 1e30;
+    int best_bps = b->bps, best_order = b->order;
+    int st = FELBM_OK;
+    for (int order = 0; order < 2 && st == FELBM_OK; ++order) {
+        b->order = order;
+        st = b_status(upload_tiles(b));
+        for (int bps = 1; bps <= b->max_bps && st == FELBM_OK; ++bps) {
+            b->bps = bps;
+            // one untimed step, then `trial` timed steps
+            cudaError_t e = launch_any(b, b->parity, 0);
+            b->parity ^= 1;
+            *used += 1;
+            if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+            for (int k = 0; k < trial && e == cudaSuccess; ++k) {
+                e = launch_any(b, b->parity, 0);
+                b->parity ^= 1;
+                *used += 1;
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            st = b_status(e);
+            if (st == FELBM_OK && ms / trial < best) {
+                best = ms / trial;
+                best_bps = bps;
+                best_order = order;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != FELBM_OK) return st;
+    b->bps = best_bps;
+    b->order = best_order;
+    b->tuned = true;
+    b->tuned_ms = best;
+    return b_status(upload_tiles(b));
+}
+
+int felbm_batch_step(felbm_batch *b, int64_t n_steps) {
+    if (!b || n_steps < 0) return FELBM_ERR_INVALID_ARG;
+    if (n_steps == 0) return FELBM_OK;
+    int st0 = sync_descriptors(b);
+    if (st0 != FELBM_OK) return st0;
+    int64_t left = n_steps;
+    cudaError_t e = cudaSuccess;
+    if (b->autotune && !b->tuned) {
+        const int trial = 3;
+        const int64_t need = 2LL * b->max_bps * (trial + 1) + 1;
+        if (left > need) {
+            int64_t used = 0;
+            int st = autotune(b, trial, &used);
+            left -= used;
+            if (st != FELBM_OK) return st;
+            drop_graph(b);
+        }
+    }
+    // steps before an even parity, then graph pairs, then the last step
+    // with the moments written
+    while (left > 1 && b->parity != 0 && e == cudaSuccess) {
+        e = launch_any(b, b->parity, 0);
+        b->parity ^= 1;
+        --left;
+    }
+    if (e == cudaSuccess && left > 2) {
+        if (!b->graph && !b->graph_failed) build_graph(b);
+        const int64_t pairs = (left - 1) / 2;
+        for (int64_t p = 0; p < pairs && e == cudaSuccess; ++p) {
+            if (b->graph) {
+                e = cudaGraphLaunch(b->graph, b->stream);
+                b->launches += 2;
+            } else {
+                e = launch_any(b, 0, 0);
+                if (e == cudaSuccess) e = launch_any(b, 1, 0);
+            }
+        }
+        left -= 2 * pairs;
+    }
+    while (left > 1 && e == cudaSuccess) {
+        e = launch_any(b, b->parity, 0);
+        b->parity ^= 1;
+        --left;
+    }
+    if (e == cudaSuccess) {
+        e = launch_any(b, b->parity, 1);
+        b->parity ^= 1;
+    }
+    if (e != cudaSuccess) return b_status(e);
+    // each state's current buffer follows the batch parity (host bookkeeping
+    // only; the descriptors stay valid)
+    for (size_t k = 0; k < b->states.size(); ++k) {
+        felbm_state *s = b->states[k];
+        s->cur = b->c0[k] ^ b->parity;
+        s->have_moments = true;
+        s->steps_done += n_steps;
+    }
+    return FELBM_OK;
+}
+
+int felbm_batch_sync(felbm_batch *b) {
+    if (!b) return FELBM_ERR_INVALID_ARG;
+    int herr = 0;
+    cudaError_t e = cudaMemcpyAsync(&herr, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return b_status(e);
+    if (herr & 2) return FELBM_ERR_TIMEOUT;
+    for (felbm_state *s : b->states) {
+        const int st = felbm_state_sync(s);
+        if (st != FELBM_OK) return st;
+    }
+    return FELBM_OK;
+}
+
+int felbm_batch_info(const felbm_batch *b, int32_t *blocks_per_sm, int32_t *tile_order,
+                     int32_t *n_tiles, int64_t *launches, double *tuned_ms_per_step) {
+    if (!b) return FELBM_ERR_INVALID_ARG;
+    if (blocks_per_sm) *blocks_per_sm = b->bps;
+    if (tile_order) *tile_order = b->order;
+    if (n_tiles) *n_tiles = b->ntiles;
+    if (launches) *launches = b->launches;
+    if (tuned_ms_per_step) *tuned_ms_per_step = b->tuned ? b->tuned_ms : 0.0;
+    return FELBM_OK;
+}
+
+void felbm_batch_destroy(felbm_batch *b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    drop_graph(b);
+    cudaFree(b->d_meshes);
+    cudaFree(b->d_tiles);
+    cudaFree(b->d_bar);
+    cudaFree(b->d_err);
+    delete b;
+}
+
+}  // extern "C"

@@ -42,9 +42,11 @@ struct StructuredInfo {
 
 int build_csr(const double *xy, int64_t n_nodes, const int32_t *tri, int64_t n_tri,
               const double box[2], uint32_t flags, const uint8_t *tag, HostCSR &out);
+// Recognise the structured lattice split; on success fills info (sizes and
+// the coefficients of the three row kinds) and the lumped mass (lattice order).
 void detect_structured(const double *xy, int64_t n_nodes, const int32_t *tri, int64_t n_tri,
                        const double box[2], uint32_t flags, const uint8_t *tag,
-                       const HostCSR &csr, StructuredInfo &info);
+                       StructuredInfo &info, std::vector<double> &mass);
 
 // ---- device-side views --------------------------------------------------
 

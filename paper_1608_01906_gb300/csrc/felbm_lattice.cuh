@@ -172,10 +172,10 @@ __device__ __forceinline__ int bb_mult(int k, int a) {
     return in_a ? 0 : (in_opp ? 2 : 1);
 }
 
+// Density pass of tile (bx, by); tiles: shared memory for 8 halo tiles.
 template <typename T>
-__global__ void __launch_bounds__(kLTX *kLTY, 4) k_lat_rho(LatArgs<T> A) {
-    __shared__ T tiles[8][kPN];
-    const int x0 = blockIdx.x * kLTX, y0 = blockIdx.y * kLTY;
+__device__ __forceinline__ void lat_rho_tile(const LatArgs<T> &A, int bx, int by, T (*tiles)[kPN]) {
+    const int x0 = bx * kLTX, y0 = by * kLTY;
     const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * kLTX + lx;
     const int x = x0 + lx, y = y0 + ly;
     const bool valid = x < A.nx && y < A.ny;
@@ -189,13 +189,21 @@ __global__ void __launch_bounds__(kLTX *kLTY, 4) k_lat_rho(LatArgs<T> A) {
     T r = valid ? __ldg(A.fin + i) : T(0);  // rest population is not moved
     cp_async_wait_all();
     __syncthreads();
-    if (!valid) return;
+    if (valid) {
 #pragma unroll
-    for (int d = 1; d < 9; ++d) {
-        const T v = streamed<T>(A.c, k, interior, d, tiles[d - 1], lx, ly, A.P.dt);
-        r += k ? T(bb_mult(k, d)) * v : v;
+        for (int d = 1; d < 9; ++d) {
+            const T v = streamed<T>(A.c, k, interior, d, tiles[d - 1], lx, ly, A.P.dt);
+            r += k ? T(bb_mult(k, d)) * v : v;
+        }
+        A.rho[i] = r;
     }
-    A.rho[i] = r;
+    __syncthreads();  // the caller may reuse the tiles for the next tile
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kLTX *kLTY, 4) k_lat_rho(LatArgs<T> A) {
+    __shared__ T tiles[8][kPN];
+    lat_rho_tile<T>(A, blockIdx.x, blockIdx.y, tiles);
 }
 
 template <typename T>
@@ -203,20 +211,85 @@ constexpr size_t lat_step_smem() {
     return (16 * (size_t)kPN + 18 * (size_t)kLTX * kLTY) * sizeof(T);
 }
 
+// Streaming from the halo tiles, bounce-back, collision and the write of one
+// node of a step tile.
 template <typename T>
-__global__ void __launch_bounds__(kLTX *kLTY, 3) k_lat_step(LatArgs<T> A) {
-    constexpr int RW = kLTX + 6, RH = kLTY + 6;  // rho: halo 3
-    constexpr int GW = kLTX + 4, GH = kLTY + 4;  // grad rho: halo 2
-    constexpr int MW = kLTX + 2, MH = kLTY + 2;  // mu: halo 1
-    __shared__ T s_rho[RH][RW];
-    __shared__ T s_gx[GH][GW], s_gy[GH][GW];
-    __shared__ T s_mu[MH][MW];
-    // dynamic: 16 halo tiles then 18 rows of streamed values (lat_step_smem)
-    extern __shared__ __align__(16) unsigned char lat_dsm[];
+__device__ __forceinline__ void lat_step_node(const LatArgs<T> &A, int k, bool interior, int lx, int ly,
+                                              int tid, int32_t i, size_t n, T r0, T drx, T dry,
+                                              T dmx, T dmy, T kx, T ky, T (*tiles)[kPN],
+                                              T (*s_psi)[kLTX * kLTY]) {
+    const Phys<T> &P = A.P;
+    // streamed populations of this node go to shared memory (slot tid of
+    // row a): keeps the 18 values out of registers
+    const T dt = P.dt;
+    s_psi[0][tid] = __ldg(A.fin + i);
+    s_psi[9][tid] = __ldg(A.fin + 9 * n + i);
+#pragma unroll
+    for (int d = 1; d < 9; ++d) {
+        s_psi[d][tid] = streamed<T>(A.c, k, interior, d, tiles[d - 1], lx, ly, dt);
+        s_psi[9 + d][tid] = streamed<T>(A.c, k, interior, d, tiles[7 + d], lx, ly, dt);
+    }
+    if (k) {  // wall row: bounce-back of the populations entering the fluid
+        const int nk = k == 1 ? 2 : 4;
+#pragma unroll
+        for (int a = 1; a < 9; ++a)
+            if (kEx(a) * kEx(nk) + kEy(a) * kEy(nk) > 0) {
+                s_psi[a][tid] = s_psi[kOpp(a)][tid];
+                s_psi[9 + a][tid] = s_psi[9 + kOpp(a)][tid];
+            }
+    }
+    T sg = T(0), mx = T(0), my = T(0);
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        const T g = s_psi[9 + a][tid];
+        sg += g;
+        if (kEx(a)) mx += T(kEx(a)) * g;
+        if (kEy(a)) my += T(kEy(a)) * g;
+    }
+    const CollidePrep<T> cp = collide_prep<T>(P, sg, mx, my, r0, drx, dry, dmx, dmy, kx, ky);
+    const T r = cp.r, ux = cp.ux, uy = cp.uy, p = cp.p;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        T ho, go;
+        collide_pop_rt<T>(cp, a, s_psi[a][tid], s_psi[9 + a][tid], ho, go);
+        A.fout[(size_t)a * n + i] = ho;
+        A.fout[(size_t)(9 + a) * n + i] = go;
+    }
+    if (!(finite_val(r) && finite_val(ux) && finite_val(uy) && finite_val(p))) atomicOr(A.flag, 1);
+    if (A.mom) {
+        A.mom[i] = r;
+        A.mom[n + i] = ux;
+        A.mom[2 * n + i] = uy;
+        A.mom[3 * n + i] = p;
+    }
+}
+
+constexpr int kRW = kLTX + 6, kRH = kLTY + 6;  // rho: halo 3
+constexpr int kGW = kLTX + 4, kGH = kLTY + 4;  // grad rho: halo 2
+constexpr int kMW = kLTX + 2, kMH = kLTY + 2;  // mu: halo 1
+
+// Shared memory of one step tile: the scalar chain and, in lat_dsm (dynamic,
+// lat_step_smem bytes), 16 halo tiles then 18 rows of streamed values.
+template <typename T>
+struct StepSmem {
+    T s_rho[kRH][kRW];
+    T s_gx[kGH][kGW], s_gy[kGH][kGW];
+    T s_mu[kMH][kMW];
+};
+
+// Step pass of tile (bx, by).
+template <typename T>
+__device__ __forceinline__ void lat_step_tile(const LatArgs<T> &A, int bx, int by, StepSmem<T> &S,
+                                              unsigned char *lat_dsm) {
+    constexpr int RW = kRW, RH = kRH, GW = kGW, GH = kGH, MW = kMW, MH = kMH;
+    auto &s_rho = S.s_rho;
+    auto &s_gx = S.s_gx;
+    auto &s_gy = S.s_gy;
+    auto &s_mu = S.s_mu;
     T (*tiles)[kPN] = reinterpret_cast<T (*)[kPN]>(lat_dsm);
     T (*s_psi)[kLTX * kLTY] = reinterpret_cast<T (*)[kLTX * kLTY]>(lat_dsm + 16 * kPN * sizeof(T));
     const int nx = A.nx, ny = A.ny, walls = A.walls;
-    const int x0 = blockIdx.x * kLTX, y0 = blockIdx.y * kLTY;
+    const int x0 = bx * kLTX, y0 = by * kLTY;
     const int tid = threadIdx.y * kLTX + threadIdx.x;
     constexpr int NT = kLTX * kLTY;
     const size_t n = (size_t)nx * ny;
@@ -313,50 +386,16 @@ __global__ void __launch_bounds__(kLTX *kLTY, 3) k_lat_step(LatArgs<T> A) {
     const int32_t i = valid ? x + nx * y : 0;
     cp_async_wait_all();
     __syncthreads();
-    if (!valid) return;  // no barrier below
-    // streamed populations of this node go to shared memory (slot tid of
-    // row a): keeps the 18 values out of registers
-    const T dt = P.dt;
-    s_psi[0][tid] = __ldg(A.fin + i);
-    s_psi[9][tid] = __ldg(A.fin + 9 * n + i);
-#pragma unroll
-    for (int d = 1; d < 9; ++d) {
-        s_psi[d][tid] = streamed<T>(A.c, k, interior, d, tiles[d - 1], lx, ly, dt);
-        s_psi[9 + d][tid] = streamed<T>(A.c, k, interior, d, tiles[7 + d], lx, ly, dt);
-    }
-    if (k) {  // wall row: bounce-back of the populations entering the fluid
-        const int nk = k == 1 ? 2 : 4;
-#pragma unroll
-        for (int a = 1; a < 9; ++a)
-            if (kEx(a) * kEx(nk) + kEy(a) * kEy(nk) > 0) {
-                s_psi[a][tid] = s_psi[kOpp(a)][tid];
-                s_psi[9 + a][tid] = s_psi[9 + kOpp(a)][tid];
-            }
-    }
-    T sg = T(0), mx = T(0), my = T(0);
-#pragma unroll
-    for (int a = 0; a < 9; ++a) {
-        const T g = s_psi[9 + a][tid];
-        sg += g;
-        if (kEx(a)) mx += T(kEx(a)) * g;
-        if (kEy(a)) my += T(kEy(a)) * g;
-    }
-    const CollidePrep<T> cp = collide_prep<T>(P, sg, mx, my, r0, drx, dry, dmx, dmy, kx, ky);
-    const T r = cp.r, ux = cp.ux, uy = cp.uy, p = cp.p;
-#pragma unroll
-    for (int a = 0; a < 9; ++a) {
-        T ho, go;
-        collide_pop_rt<T>(cp, a, s_psi[a][tid], s_psi[9 + a][tid], ho, go);
-        A.fout[(size_t)a * n + i] = ho;
-        A.fout[(size_t)(9 + a) * n + i] = go;
-    }
-    if (!(finite_val(r) && finite_val(ux) && finite_val(uy) && finite_val(p))) atomicOr(A.flag, 1);
-    if (A.mom) {
-        A.mom[i] = r;
-        A.mom[n + i] = ux;
-        A.mom[2 * n + i] = uy;
-        A.mom[3 * n + i] = p;
-    }
+    if (valid) lat_step_node<T>(A, k, interior, lx, ly, tid, i, n, r0, drx, dry, dmx, dmy, kx, ky,
+                                tiles, s_psi);
+    __syncthreads();  // the caller may reuse shared memory for the next tile
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kLTX *kLTY, 3) k_lat_step(LatArgs<T> A) {
+    __shared__ StepSmem<T> S;
+    extern __shared__ __align__(16) unsigned char lat_dsm[];
+    lat_step_tile<T>(A, blockIdx.x, blockIdx.y, S, lat_dsm);
 }
 
 }  // namespace felbm

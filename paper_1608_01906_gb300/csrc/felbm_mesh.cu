@@ -223,7 +223,7 @@ int build_csr(const double *xy, int64_t n_nodes, const int32_t *tri, int64_t n_t
 // node of row 0 tagged 2 and of row ny-1 tagged 4 and no other tag.
 void detect_structured(const double *xy, int64_t n_nodes, const int32_t *tri, int64_t n_tri,
                        const double box[2], uint32_t flags, const uint8_t *tag,
-                       const HostCSR &csr, StructuredInfo &info) {
+                       StructuredInfo &info, std::vector<double> &mass) {
     info.ok = false;
     if (n_nodes < 16 || !(flags & FELBM_PERIODIC_X)) return;
     // nx from the first row: nodes with y == y0 in increasing x
@@ -276,29 +276,56 @@ void detect_structured(const double *xy, int64_t n_nodes, const int32_t *tri, in
         }
         if (!matched) return;
     }
-    // coefficients of the three row kinds (interior, bottom wall row, top wall
-    // row) read off the assembled CSR at a representative node of each kind
+    // Lumped mass of every node and, for a representative node of each row
+    // kind (interior, bottom wall row, top wall row), the assembled a_ij,
+    // b_ij of its six neighbours, from the triangles incident to it (the same
+    // element formulas as the general assembly; every node of a kind has
+    // the same coefficients by translation invariance).
+    const double Lp[2] = {box[0], py ? box[1] : 0.0};
     static const int OFF[6][2] = {{1, 0}, {1, 1}, {0, 1}, {-1, 0}, {-1, -1}, {0, -1}};
     const int64_t rows[3] = {ny / 2, 0, ny - 1};
+    int32_t rep[3];
+    for (int kind = 0; kind < 3; ++kind) rep[kind] = (int32_t)(nx / 2 + nx * rows[kind]);
+    mass.assign((size_t)n_nodes, 0.0);
+    std::vector<ElemGeom> rep_geo[3];
+    std::vector<int32_t> rep_tri[3];
+    for (int64_t t = 0; t < n_tri; ++t) {
+        ElemGeom g;
+        if (!elem_geom(xy, tri + 3 * t, Lp, g)) return;
+        for (int k = 0; k < 3; ++k) mass[tri[3 * t + k]] += g.area / 3.0;
+        for (int kind = 0; kind < 3; ++kind)
+            for (int k = 0; k < 3; ++k)
+                if (tri[3 * t + k] == rep[kind]) {
+                    rep_geo[kind].push_back(g);
+                    rep_tri[kind].push_back((int32_t)t);
+                }
+    }
     for (int kind = 0; kind < 3; ++kind) {
         const int64_t j = rows[kind];
         const int64_t i = nx / 2;
-        const int32_t node = (int32_t)(i + nx * j);
-        const int32_t k = csr.iperm[node];
+        const int32_t node = rep[kind];
+        const double mi = mass[node];
         for (int o = 0; o < 6; ++o) {
             info.a[kind][o][0] = info.a[kind][o][1] = 0.0;
             info.b[kind][o][0] = info.b[kind][o][1] = info.b[kind][o][2] = 0.0;
             const int64_t jj = j + OFF[o][1];
             if (!py && (jj < 0 || jj >= ny)) continue;
             const int32_t nb = (int32_t)(((i + OFF[o][0] + nx) % nx) + nx * ((jj + ny) % ny));
-            const int32_t kn = csr.iperm[nb];
-            for (int32_t p = csr.rowptr[k]; p < csr.rowptr[k + 1]; ++p) {
-                if (csr.col[p] != kn) continue;
-                info.a[kind][o][0] = csr.ax[p];
-                info.a[kind][o][1] = csr.ay[p];
-                info.b[kind][o][0] = csr.bxx[p];
-                info.b[kind][o][1] = csr.bxy[p];
-                info.b[kind][o][2] = csr.byy[p];
+            for (size_t q = 0; q < rep_tri[kind].size(); ++q) {
+                const int32_t *v = tri + 3 * rep_tri[kind][q];
+                const ElemGeom &g = rep_geo[kind][q];
+                int a = -1, b = -1;
+                for (int k = 0; k < 3; ++k) {
+                    if (v[k] == node) a = k;
+                    if (v[k] == nb) b = k;
+                }
+                if (a < 0 || b < 0) continue;
+                info.a[kind][o][0] += g.area * g.gx[b] / (3.0 * mi);
+                info.a[kind][o][1] += g.area * g.gy[b] / (3.0 * mi);
+                const double sc = g.area / mi;
+                info.b[kind][o][0] += sc * g.gx[a] * g.gx[b];
+                info.b[kind][o][1] += sc * 0.5 * (g.gx[a] * g.gy[b] + g.gy[a] * g.gx[b]);
+                info.b[kind][o][2] += sc * g.gy[a] * g.gy[b];
             }
         }
     }

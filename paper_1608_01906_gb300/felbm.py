@@ -35,7 +35,10 @@ EXPORTED = [
     "felbm_step", "felbm_state_sync", "felbm_moments_get", "felbm_state_export",
     "felbm_state_import", "felbm_state_destroy", "felbm_status_string",
     "felbm_profile_enable", "felbm_profile_read", "felbm_profile_kind_name",
+    "felbm_batch_create", "felbm_batch_step", "felbm_batch_sync", "felbm_batch_info",
+    "felbm_batch_destroy", "felbm_totals_nalloc",
 ]
+FELBM_BATCH_AUTOTUNE = 0x1
 FELBM_PROFILE_KINDS = 8
 
 
@@ -112,8 +115,15 @@ def _declare_extra(lib):
         lib.felbm_batch_create.argtypes = [C.POINTER(C.c_void_p), i32, C.c_uint32, pp]
         lib.felbm_batch_step.restype = C.c_int
         lib.felbm_batch_step.argtypes = [vp, i64]
+        lib.felbm_batch_sync.restype = C.c_int
+        lib.felbm_batch_sync.argtypes = [vp]
+        lib.felbm_batch_info.restype = C.c_int
+        lib.felbm_batch_info.argtypes = [vp, vp, vp, vp, vp, vp]
         lib.felbm_batch_destroy.restype = None
         lib.felbm_batch_destroy.argtypes = [vp]
+    if hasattr(lib, "felbm_totals_nalloc"):
+        lib.felbm_totals_nalloc.restype = C.c_int
+        lib.felbm_totals_nalloc.argtypes = [vp, vp, vp, vp, i64, i32, vp, vp]
 
 
 def _p(a):
@@ -274,6 +284,46 @@ class State:
     def close(self):
         if getattr(self, "handle", None):
             load().felbm_state_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many structured-mesh states advanced by one launch per time step."""
+
+    def __init__(self, states, autotune=True):
+        lib = load()
+        self.states = list(states)
+        arr = (C.c_void_p * len(self.states))(*[st.handle.value if isinstance(st.handle, C.c_void_p)
+                                                 else st.handle for st in self.states])
+        out = C.c_void_p()
+        flags = FELBM_BATCH_AUTOTUNE if autotune else 0
+        _check(lib.felbm_batch_create(arr, len(self.states), flags, C.byref(out)),
+               "felbm_batch_create")
+        self.handle = out
+
+    def step(self, n):
+        _check(load().felbm_batch_step(self.handle, int(n)), "felbm_batch_step")
+
+    def sync(self):
+        _check(load().felbm_batch_sync(self.handle), "felbm_batch_sync")
+
+    def info(self):
+        bps, order, nt = C.c_int32(), C.c_int32(), C.c_int32()
+        launches, ms = C.c_int64(), C.c_double()
+        _check(load().felbm_batch_info(self.handle, C.byref(bps), C.byref(order), C.byref(nt),
+                                       C.byref(launches), C.byref(ms)), "felbm_batch_info")
+        return {"blocks_per_sm": bps.value, "tile_order": order.value, "n_tiles": nt.value,
+                "launches": launches.value, "tuned_ms_per_step": ms.value}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().felbm_batch_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

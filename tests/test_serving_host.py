@@ -1,0 +1,71 @@
+"""Host-side logic of the serving loop (no GPU): the request stream and the
+scheduler's admission, chunking and retirement, with the device calls faked."""
+import numpy as np
+
+from paper_1608_01906_gb300 import serving
+
+
+def test_poisson_stream_is_seeded_and_in_range():
+    a = serving.poisson_stream(2000, rate=5.0, seed=1610)
+    b = serving.poisson_stream(2000, rate=5.0, seed=1610)
+    assert [(r.arrival, r.side, r.steps) for r in a] == [(r.arrival, r.side, r.steps) for r in b]
+    sides = np.array([r.side for r in a])
+    assert sides.min() >= 64 and sides.max() <= 1024
+    steps = np.array([r.steps for r in a])
+    assert steps.min() >= 1000 and steps.max() <= 20000
+    gaps = np.diff([0.0] + [r.arrival for r in a])
+    assert abs(gaps.mean() - 0.2) < 0.02  # mean inter-arrival 1 / rate
+
+
+class FakeState:
+    def __init__(self, *a, **k):
+        self.closed = False
+
+    def moments(self):
+        return {"rho": np.zeros(1)}
+
+    def close(self):
+        self.closed = True
+
+
+class FakeMesh(FakeState):
+    pass
+
+
+class FakeBatch:
+    log = []
+
+    def __init__(self, states, autotune=True):
+        self.n = len(states)
+
+    def step(self, n):
+        FakeBatch.log.append((self.n, n))
+
+    def sync(self):
+        pass
+
+    def close(self):
+        pass
+
+
+def test_scheduler_budget_chunks_and_retirement(monkeypatch):
+    monkeypatch.setattr(serving.felbm, "Mesh", FakeMesh)
+    monkeypatch.setattr(serving.felbm, "State", FakeState)
+    monkeypatch.setattr(serving.felbm, "Batch", FakeBatch)
+    monkeypatch.setattr(serving, "problem_for", lambda req: type(
+        "P", (), {"xy": None, "tri": None, "box": None, "tag": None, "rho0": None, "u0": None,
+                  "p0": None, "params": {"rho_l": 1.0, "rho_v": 0.1, "sigma": 0.01, "xi": 4.0,
+                                         "tau_l": 0.1, "tau_v": 0.1, "dt": 0.5,
+                                         "gravity": (0.0, 0.0)}})())
+    FakeBatch.log = []
+    reqs = [serving.Request(k, 0.0, 64, 10.0, 0.3, s) for k, s in enumerate([100, 250, 60, 300])]
+    budget = 2 * serving.state_bytes(64)  # two runs at a time
+    results, stats = serving.serve(reqs, budget, chunk=80, autotune=False)
+    assert stats["completed"] == 4
+    # never more than two runs in a launch, chunk never above 80 nor past a finish
+    assert max(n for n, _ in FakeBatch.log) == 2
+    assert all(c <= 80 for _, c in FakeBatch.log)
+    done = {r.rid: r.steps for r in results}
+    assert done == {0: 100, 1: 250, 2: 60, 3: 300}
+    # total node-steps equal the requested work
+    assert sum(n * c for n, c in FakeBatch.log) == 100 + 250 + 60 + 300
