@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--skip-batched", action="store_true")
+    ap.add_argument("--skip-serving", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=40)
     return ap.parse_args()
 
 
@@ -195,6 +198,74 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------- batched and served
+def run_batched(torch, felbm, steps=200):
+    """64 uneven droplet meshes: one batched launch per step vs one
+    felbm_step per mesh per step (same states, same steps)."""
+    from paper_1608_01906_gb300 import configs
+
+    probs = configs.c4_batched()
+    nodes = sum(p.n_nodes for p in probs)
+    stream = torch.cuda.Stream()
+    meshes = [felbm.Mesh(p.xy, p.tri, p.box, p.tag, stream=stream.cuda_stream) for p in probs]
+    states = [felbm.State(m, felbm.make_params(precision="fp32", **p.params), p.rho0, p.u0, p.p0)
+              for m, p in zip(meshes, probs)]
+    for st in states:
+        st.step(3)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for st in states:
+        st.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    seq_ms = e0.elapsed_time(e1)
+    b = felbm.Batch(states, autotune=True)
+    b.step(100)  # autotuning steps
+    b.sync()
+    e0.record(stream)
+    b.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    b.sync()
+    bat_ms = e0.elapsed_time(e1)
+    info = b.info()
+    b.close()
+    for st in states:
+        st.close()
+    for m in meshes:
+        m.close()
+    return {"workload": "64 periodic droplet meshes, sides log-uniform [32,512] (seed 1609), "
+                        "ratio U[10,1000], FP32",
+            "nodes": nodes, "steps": steps,
+            "value": nodes * steps / (bat_ms * 1e-3) / 1e6, "unit": UNIT,
+            "sequential": nodes * steps / (seq_ms * 1e-3) / 1e6,
+            "speedup": seq_ms / bat_ms, "launches_per_step": 1,
+            "blocks_per_sm": info["blocks_per_sm"], "tile_order": info["tile_order"]}
+
+
+def run_serving(torch, felbm, capacity_mnups, n_requests):
+    """Poisson stream at 80% of the measured batched capacity."""
+    import math
+
+    from paper_1608_01906_gb300 import serving
+
+    lo, hi = 64, 1024
+    mean_nodes = (hi * hi - lo * lo) / (2.0 * math.log(hi / lo))  # E[side^2], log-uniform
+    mean_work = mean_nodes * (1000 + 20000) / 2.0
+    rate = 0.8 * capacity_mnups * 1e6 / mean_work
+    reqs = serving.poisson_stream(n_requests, rate, seed=1610)
+    stream = torch.cuda.Stream()
+    budget = 64 * 1024 ** 3
+    results, stats = serving.serve(reqs, budget, chunk=500, stream=stream.cuda_stream)
+    stats.update({"requests": n_requests, "rate_per_s": rate, "budget_gb": 64,
+                  "load": "80% of batched capacity %.0f MNUPS" % capacity_mnups,
+                  "workload": "droplet runs, sides log-uniform [64,1024], ratio U[10,1000], "
+                              "steps U[1000,20000], Poisson arrivals (seed 1610), FP32"})
+    return stats
+
+
 # --------------------------------------------------------------------- GPU arm
 def main():
     args = parse()
@@ -296,6 +367,11 @@ def main():
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "FP64 C oracle (1 thread), full 512x2048 mesh, %d time steps, %.1f s"
                          % (nsteps, el)}
+    batched = serving = None
+    if rank == 0 and world == 1 and not args.skip_batched:
+        batched = run_batched(torch, felbm)
+        if not args.skip_serving:
+            serving = run_serving(torch, felbm, batched["value"], args.serve_requests)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,
@@ -309,7 +385,7 @@ def main():
                 "gpu_launches": launches * world, "clocks": clocks,
                 "kernels": {k: {"ms": v[0], "timed": v[1], "launches": v[2]}
                             for k, v in prof.items() if v[2]},
-                "mass": float(mom["totals"][0])}
+                "mass": float(mom["totals"][0]), "batched": batched, "serving": serving}
         print(json.dumps(line), flush=True)
     st.close()
     mesh.close()

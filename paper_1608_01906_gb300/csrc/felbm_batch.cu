@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kLTX *kLTY, 3) k_batch_step(BatchArgs<T> B) {
     for (int t = blockIdx.x; t < B.ntiles; t += gridDim.x) {
         const TileRef r = B.tiles[t];
         load_mesh<T>(B, r.mesh, sA, cur);
-        lat_rho_tile<T>(sA, r.bx, r.by, reinterpret_cast<T (*)[kPN]>(bdsm));
+        lat_rho_tile<T>(sA, r.bx, r.by, reinterpret_cast<T *>(bdsm));
     }
     grid_barrier(B.bar, B.err);
     for (int t = blockIdx.x; t < B.ntiles; t += gridDim.x) {

@@ -179,10 +179,14 @@ __global__ void __launch_bounds__(256) k_mu(Topo m, Fields<T> F, Phys<T> P) {
 //   psi = psi* + 2tau/(2tau+1) (-(psi* - eq)/(2tau) + S)
 // followed by the pre-streaming collision of the next step
 //   psibar = psi + (-(psi - eq)/(2tau) + S)
-// equals psibar = eq + S + w (psi* - eq + S), w = (2tau - 1)/(2tau + 1).
+// equals psibar = eq + S + w (psi* - eq + S), w = (2tau - 1)/(2tau + 1),
+// evaluated as psibar = psi* + (1 - w)(eq - psi*) + (1 + w) S with
+// eq - psi* = fma(rho, w_a, -psi*) + rho (Gamma - w_a): every rounding then
+// falls on the small collision increment instead of on O(w_a rho) terms
+// (in FP32 the other order repeats the same O(ulp(rho)) error every step).
 template <typename T>
 struct CollidePrep {
-    T r, ux, uy, p, w, hdt, Xx, Xy, uX, uD, uK, uu, dux, duy, udu, drx, dry, kx, ky;
+    T r, ux, uy, p, w, omw, opw, hdt, Xx, Xy, uX, uD, uK, uu, dux, duy, udu, drx, dry, kx, ky;
 };
 
 // sg = sum_a g*_a, mx, my = sum_a e_a g*_a of the streamed (and bounced) g.
@@ -201,6 +205,8 @@ __device__ __forceinline__ CollidePrep<T> collide_prep(const Phys<T> &P, T sg, T
     C = C < T(0) ? T(0) : (C > T(1) ? T(1) : C);
     const T tau = T(1) / (C * P.inv_tau_l + (T(1) - C) * P.inv_tau_v);
     c.w = (T(2) * tau - T(1)) / (T(2) * tau + T(1));
+    c.omw = T(2) / (T(2) * tau + T(1));        // 1 - w
+    c.opw = T(4) * tau / (T(2) * tau + T(1));  // 1 + w
     c.Xx = cs2 * drx - r * dmx;  // F: c_s^2 grad rho - rho grad mu
     c.Xy = cs2 * dry - r * dmy;
     c.uX = c.ux * c.Xx + c.uy * c.Xy;
@@ -230,15 +236,15 @@ __device__ __forceinline__ void collide_pop(const CollidePrep<T> &c, T hs, T gs,
     const T eD = T(ex) * c.drx + T(ey) * c.dry;
     const T eK = T(ex) * c.kx + T(ey) * c.ky;
     const T edu = T(ex) * c.dux + T(ey) * c.duy;
-    const T heq = c.r * gam;
-    const T geq = wa * T(3) * c.p + c.r * gmw;
     const T Fa = c.hdt * T(3) * (eX - c.uX) * gam;
     const T Ga = c.hdt * (eD - c.uD) * gmw + c.hdt * T(3) * (eK - c.uK) * gam;
     // 1/2 [g_eq(u + du) - g_eq(u)] = rho/2 [Gamma(u + du) - Gamma(u)]
     const T Ba = T(0.5) * c.r * wa * (T(3) * edu + T(4.5) * edu * (T(2) * eu + edu) - T(1.5) * c.udu);
     const T Sg = Ga + Ba;
-    hout = heq + Fa + c.w * (hs - heq + Fa);
-    gout = geq + Sg + c.w * (gs - geq + Sg);
+    const T dh = fma(c.r, wa, -hs) + c.r * gmw;           // h_eq - h*
+    const T dg = fma(wa * T(3), c.p, -gs) + c.r * gmw;    // g_eq - g*
+    hout = hs + (c.omw * dh + c.opw * Fa);
+    gout = gs + (c.omw * dg + c.opw * Sg);
 }
 
 template <typename T>
@@ -257,20 +263,35 @@ __device__ __forceinline__ void collide_pop_rt(const CollidePrep<T> &c, int a, T
     }
 }
 
+// Zeroth and first moments of the streamed g.  The first moments are summed
+// as differences of opposite populations: each difference is exact in
+// floating point when the two are close (they share the pressure part
+// w_a 3p), so only the small momentum-carrying parts are rounded.
+template <typename T>
+__device__ __forceinline__ void g_moments(T g0, T g1, T g2, T g3, T g4, T g5, T g6, T g7, T g8,
+                                          T &sg, T &mx, T &my) {
+    const T d13 = g1 - g3, d24 = g2 - g4, d57 = g5 - g7, d68 = g6 - g8;
+    mx = d13 + (d57 - d68);  // e_x: +1, 3: -1, 5: +1, 6: -1, 7: -1, 8: +1
+    my = d24 + (d57 + d68);  // e_y: +2, 4: -1, 5: +1, 6: +1, 7: -1, 8: -1
+    sg = ((g0 + (g1 + g3)) + (g2 + g4)) + ((g5 + g7) + (g6 + g8));
+}
+
 template <typename T>
 __device__ __forceinline__ void collide_node(const Phys<T> &P, const T *hs, const T *gs, T r,
                                              T drx, T dry, T dmx, T dmy, T kx, T ky, T *hout,
                                              T *gout, T &ux, T &uy, T &p) {
-    T mx = T(0), my = T(0), sg = T(0);
-#pragma unroll
-    for (int a = 0; a < 9; ++a) {
-        sg += gs[a];
-        if (kEx(a)) mx += T(kEx(a)) * gs[a];
-        if (kEy(a)) my += T(kEy(a)) * gs[a];
-    }
+    T sg, mx, my;
+    g_moments<T>(gs[0], gs[1], gs[2], gs[3], gs[4], gs[5], gs[6], gs[7], gs[8], sg, mx, my);
     const CollidePrep<T> c = collide_prep<T>(P, sg, mx, my, r, drx, dry, dmx, dmy, kx, ky);
+    T dsum = T(0);  // sum of the h increments: zero in exact arithmetic
 #pragma unroll
-    for (int a = 0; a < 9; ++a) collide_pop_rt<T>(c, a, hs[a], gs[a], hout[a], gout[a]);
+    for (int a = 1; a < 9; ++a) {
+        collide_pop_rt<T>(c, a, hs[a], gs[a], hout[a], gout[a]);
+        dsum += hout[a] - hs[a];
+    }
+    collide_pop_rt<T>(c, 0, hs[0], gs[0], hout[0], gout[0]);
+    dsum += hout[0] - hs[0];
+    hout[0] -= dsum;  // local mass: sum_a hbar_a = sum_a h*_a up to one rounding
     ux = c.ux;
     uy = c.uy;
     p = c.p;

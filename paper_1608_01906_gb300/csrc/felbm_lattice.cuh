@@ -68,74 +68,135 @@ __device__ __forceinline__ void lat_neighbours(int x, int y, int nx, int ny, int
     }
 }
 
-// Halo tile of one population: (kLTY + 2) x (kLTX + 2) values around the
-// block's tile, filled by the block's threads (each fills at most 2 slots;
-// the global offsets of those slots are the same for every population).
-constexpr int kPW = kLTX + 2, kPH = kLTY + 2, kPN = kPW * kPH;
-static_assert(kPN <= 2 * kLTX * kLTY, "two fill slots per thread");
+// Halo tile of one population: kPH = kLTY + 2 rows of kPW<T> values around
+// the block's tile.  Rows start CE = 16 / sizeof(T) columns left of the tile
+// so that a tile away from the x wrap is filled with 16-byte copies (the
+// stencil reads the kLTX + 2 central columns).  Tiles at the x wrap, and
+// meshes whose row length is not a multiple of CE, are filled element by
+// element with the periodic wrap applied per element.
+template <typename T>
+struct PopTile {
+    static constexpr int CE = 16 / (int)sizeof(T);
+    static constexpr int W = kLTX + 2 * CE;
+    static constexpr int H = kLTY + 2;
+    static constexpr int N = W * H;
+    static constexpr int CHUNKS = N / CE;  // 16-byte chunks of a tile
+};
+constexpr int kPH = kLTY + 2;
+template <typename T>
+constexpr int kPN = PopTile<T>::N;
 
-struct FillSlots {
-    int32_t off[2];  // global node id of the slot, -1 = outside a walled domain
-    int n;           // number of slots this thread fills
+// Fill plan of one thread for one halo window (the same for every
+// population): up to kMaxSlots slots, each a global element offset and a
+// shared-memory element offset; a slot outside a walled domain copies zero
+// bytes (cp.async zero-fills it).  VEC: the slots are 16-byte chunks.
+constexpr int kMaxSlots = 3;
+struct FillPlan {
+    int32_t src[kMaxSlots];
+    int32_t dst[kMaxSlots];
+    int8_t ok[kMaxSlots];  // inside the domain
+    int n;
 };
 
-__device__ __forceinline__ FillSlots fill_slots(int tid, int x0, int y0, int nx, int ny, int walls) {
-    FillSlots f;
+// Plan for a window of H rows x W columns whose top-left element is global
+// (gx0, gy0).  VEC requires a window without x wrap and 16-byte aligned rows
+// (the caller checks).
+template <typename T, int W, int H, bool VEC>
+__device__ __forceinline__ FillPlan fill_plan(int tid, int nthreads, int gx0, int gy0, int nx, int ny,
+                                              int walls) {
+    constexpr int CE = 16 / (int)sizeof(T);
+    constexpr int PER_ROW = VEC ? W / CE : W;
+    constexpr int TOTAL = PER_ROW * H;
+    FillPlan f;
     f.n = 0;
 #pragma unroll
-    for (int t = 0; t < 2; ++t) {
-        const int q = tid + t * kLTX * kLTY;
-        f.off[t] = -1;
-        if (q < kPN) {
-            const int ly = q / kPW, lx = q - ly * kPW;
-            int gx = x0 + lx - 1, gy = y0 + ly - 1;
+    for (int t = 0; t < kMaxSlots; ++t) {
+        const int q = tid + t * nthreads;
+        f.src[t] = 0;
+        f.dst[t] = 0;
+        f.ok[t] = 0;
+        if (q < TOTAL) {
+            const int r = q / PER_ROW, c = q - r * PER_ROW;
+            const int col = VEC ? c * CE : c;
+            int gx = gx0 + col, gy = gy0 + r;
             while (gx < 0) gx += nx;
             while (gx >= nx) gx -= nx;
+            bool inside = true;
             if (walls) {
-                if (gy >= 0 && gy < ny) f.off[t] = gx + nx * gy;
+                inside = gy >= 0 && gy < ny;
             } else {
                 while (gy < 0) gy += ny;
                 while (gy >= ny) gy -= ny;
-                f.off[t] = gx + nx * gy;
             }
+            f.src[t] = inside ? gx + nx * gy : 0;
+            f.ok[t] = inside;
+            f.dst[t] = r * W + col;
             f.n = t + 1;
         }
     }
     return f;
 }
 
-// Asynchronous global -> shared copies (cp.async, one element each): the
-// halo tiles of all moving populations are requested at once so that their
-// latency overlaps the other work of the block.
-template <typename T>
-__device__ __forceinline__ void cp_async_elem(T *smem, const T *gmem) {
+// Asynchronous global -> shared copies (cp.async) with a source size: a
+// zero source size fills the destination with zeros.  The halo tiles of all
+// moving populations are requested at once so that their latency overlaps
+// the other work of the block.
+template <typename T, bool VEC>
+__device__ __forceinline__ void cp_async_zfill(T *smem, const T *gmem, bool ok) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    if (sizeof(T) == 4)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+    if (VEC) {
+        const int ssz = ok ? 16 : 0;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gmem), "r"(ssz)
+                     : "memory");
+    } else if (sizeof(T) == 4) {
+        const int ssz = ok ? 4 : 0;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(sa), "l"(gmem), "r"(ssz)
+                     : "memory");
+    } else {
+        const int ssz = ok ? 8 : 0;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(ssz)
+                     : "memory");
+    }
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// wait until at most N committed groups of this thread are still pending
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
-// Request the halo tiles of populations A0 + 1 .. A0 + 8 into tiles[0..8).
-// Slots outside a walled domain are set to zero.
-template <typename T, int A0>
-__device__ __forceinline__ void issue_tiles(const LatArgs<T> &A, const FillSlots &f, T (*tiles)[kPN],
-                                            int tid, size_t n) {
+// Request NF fields (src + f_i * src_stride -> dst + f_i * dst_stride) of
+// one window following plan f.
+template <typename T, bool VEC, int NF>
+__device__ __forceinline__ void fill_issue(const FillPlan &f, const T *__restrict__ src, size_t src_stride,
+                                           T *dst, int dst_stride) {
 #pragma unroll
-    for (int d = 1; d < 9; ++d) {
-        const T *src = A.fin + (size_t)(A0 + d) * n;
+    for (int t = 0; t < kMaxSlots; ++t) {
+        if (t < f.n) {
+            const T *s = src + f.src[t];
+            T *d = dst + f.dst[t];
+            const bool ok = f.ok[t];
 #pragma unroll
-        for (int t = 0; t < 2; ++t) {
-            if (t < f.n) {
-                T *dst = &tiles[d - 1][tid + t * kLTX * kLTY];
-                if (f.off[t] >= 0)
-                    cp_async_elem<T>(dst, src + f.off[t]);
-                else
-                    *dst = T(0);
-            }
+            for (int q = 0; q < NF; ++q) cp_async_zfill<T, VEC>(d + q * dst_stride, s + q * src_stride, ok);
         }
+    }
+}
+
+// Request the halo tiles of populations A0 + 1 .. A0 + 8 of block tile
+// (x0, y0) into tiles[0..8) (tile stride kPN).
+template <typename T, int A0>
+__device__ __forceinline__ void issue_pop_tiles(const LatArgs<T> &A, int tid, int x0, int y0, T *tiles,
+                                                size_t n) {
+    constexpr int CE = PopTile<T>::CE, W = PopTile<T>::W, H = PopTile<T>::H;
+    const int nx = A.nx, ny = A.ny, walls = A.walls;
+    const T *src = A.fin + (size_t)(A0 + 1) * n;
+    if ((nx % CE) == 0 && x0 - CE >= 0 && x0 + kLTX + CE <= nx) {
+        const FillPlan f = fill_plan<T, W, H, true>(tid, kLTX * kLTY, x0 - CE, y0 - 1, nx, ny, walls);
+        fill_issue<T, true, 8>(f, src, n, tiles, kPN<T>);
+    } else {
+        const FillPlan f = fill_plan<T, W, H, false>(tid, kLTX * kLTY, x0 - CE, y0 - 1, nx, ny, walls);
+        fill_issue<T, false, 8>(f, src, n, tiles, kPN<T>);
     }
 }
 
@@ -143,11 +204,12 @@ __device__ __forceinline__ void issue_tiles(const LatArgs<T> &A, const FillSlots
 // (lx, ly) of the block's tile.
 template <typename T>
 __device__ __forceinline__ T stencil(const LatCoef<T> &c, int k, int d, const T *buf, int lx, int ly) {
-    const T self = buf[(ly + 1) * kPW + lx + 1];
+    constexpr int W = PopTile<T>::W, CE = PopTile<T>::CE;
+    const T self = buf[(ly + 1) * W + lx + CE];
     T acc = T(0);
 #pragma unroll
     for (int o = 0; o < 6; ++o)
-        acc += c.s[k][o][d] * (buf[(ly + 1 + lat_dy(o)) * kPW + lx + 1 + lat_dx(o)] - self);
+        acc += c.s[k][o][d] * (buf[(ly + 1 + lat_dy(o)) * W + lx + CE + lat_dx(o)] - self);
     return acc;
 }
 
@@ -156,7 +218,8 @@ __device__ __forceinline__ T stencil(const LatCoef<T> &c, int k, int d, const T 
 template <typename T>
 __device__ __forceinline__ T streamed(const LatCoef<T> &c, int k, bool interior, int d, const T *buf,
                                       int lx, int ly, T dt) {
-    const T self = buf[(ly + 1) * kPW + lx + 1];
+    constexpr int W = PopTile<T>::W, CE = PopTile<T>::CE;
+    const T self = buf[(ly + 1) * W + lx + CE];
     const T acc = interior ? stencil<T>(c, 0, d, buf, lx, ly) : stencil<T>(c, k, d, buf, lx, ly);
     return self - dt * acc;
 }
@@ -174,14 +237,13 @@ __device__ __forceinline__ int bb_mult(int k, int a) {
 
 // Density pass of tile (bx, by); tiles: shared memory for 8 halo tiles.
 template <typename T>
-__device__ __forceinline__ void lat_rho_tile(const LatArgs<T> &A, int bx, int by, T (*tiles)[kPN]) {
+__device__ __forceinline__ void lat_rho_tile(const LatArgs<T> &A, int bx, int by, T *tiles) {
     const int x0 = bx * kLTX, y0 = by * kLTY;
     const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * kLTX + lx;
     const int x = x0 + lx, y = y0 + ly;
     const bool valid = x < A.nx && y < A.ny;
     const size_t n = (size_t)A.nx * A.ny;
-    const FillSlots f = fill_slots(tid, x0, y0, A.nx, A.ny, A.walls);
-    issue_tiles<T, 0>(A, f, tiles, tid, n);
+    issue_pop_tiles<T, 0>(A, tid, x0, y0, tiles, n);
     cp_async_commit();
     const int k = valid ? lat_kind(A.walls, y, A.ny) : 0;
     const bool interior = !A.walls || (y0 > 0 && y0 + kLTY < A.ny);
@@ -192,7 +254,7 @@ __device__ __forceinline__ void lat_rho_tile(const LatArgs<T> &A, int bx, int by
     if (valid) {
 #pragma unroll
         for (int d = 1; d < 9; ++d) {
-            const T v = streamed<T>(A.c, k, interior, d, tiles[d - 1], lx, ly, A.P.dt);
+            const T v = streamed<T>(A.c, k, interior, d, tiles + (d - 1) * kPN<T>, lx, ly, A.P.dt);
             r += k ? T(bb_mult(k, d)) * v : v;
         }
         A.rho[i] = r;
@@ -202,13 +264,13 @@ __device__ __forceinline__ void lat_rho_tile(const LatArgs<T> &A, int bx, int by
 
 template <typename T>
 __global__ void __launch_bounds__(kLTX *kLTY, 4) k_lat_rho(LatArgs<T> A) {
-    __shared__ T tiles[8][kPN];
+    __shared__ __align__(16) T tiles[8 * kPN<T>];
     lat_rho_tile<T>(A, blockIdx.x, blockIdx.y, tiles);
 }
 
 template <typename T>
 constexpr size_t lat_step_smem() {
-    return (16 * (size_t)kPN + 18 * (size_t)kLTX * kLTY) * sizeof(T);
+    return (16 * (size_t)kPN<T> + 18 * (size_t)kLTX * kLTY) * sizeof(T);
 }
 
 // Streaming from the halo tiles, bounce-back, collision and the write of one
@@ -216,7 +278,7 @@ constexpr size_t lat_step_smem() {
 template <typename T>
 __device__ __forceinline__ void lat_step_node(const LatArgs<T> &A, int k, bool interior, int lx, int ly,
                                               int tid, int32_t i, size_t n, T r0, T drx, T dry,
-                                              T dmx, T dmy, T kx, T ky, T (*tiles)[kPN],
+                                              T dmx, T dmy, T kx, T ky, const T *tiles,
                                               T (*s_psi)[kLTX * kLTY]) {
     const Phys<T> &P = A.P;
     // streamed populations of this node go to shared memory (slot tid of
@@ -226,8 +288,8 @@ __device__ __forceinline__ void lat_step_node(const LatArgs<T> &A, int k, bool i
     s_psi[9][tid] = __ldg(A.fin + 9 * n + i);
 #pragma unroll
     for (int d = 1; d < 9; ++d) {
-        s_psi[d][tid] = streamed<T>(A.c, k, interior, d, tiles[d - 1], lx, ly, dt);
-        s_psi[9 + d][tid] = streamed<T>(A.c, k, interior, d, tiles[7 + d], lx, ly, dt);
+        s_psi[d][tid] = streamed<T>(A.c, k, interior, d, tiles + (d - 1) * kPN<T>, lx, ly, dt);
+        s_psi[9 + d][tid] = streamed<T>(A.c, k, interior, d, tiles + (7 + d) * kPN<T>, lx, ly, dt);
     }
     if (k) {  // wall row: bounce-back of the populations entering the fluid
         const int nk = k == 1 ? 2 : 4;
@@ -238,22 +300,32 @@ __device__ __forceinline__ void lat_step_node(const LatArgs<T> &A, int k, bool i
                 s_psi[9 + a][tid] = s_psi[9 + kOpp(a)][tid];
             }
     }
-    T sg = T(0), mx = T(0), my = T(0);
-#pragma unroll
-    for (int a = 0; a < 9; ++a) {
-        const T g = s_psi[9 + a][tid];
-        sg += g;
-        if (kEx(a)) mx += T(kEx(a)) * g;
-        if (kEy(a)) my += T(kEy(a)) * g;
-    }
+    T sg, mx, my;
+    g_moments<T>(s_psi[9][tid], s_psi[10][tid], s_psi[11][tid], s_psi[12][tid], s_psi[13][tid],
+                 s_psi[14][tid], s_psi[15][tid], s_psi[16][tid], s_psi[17][tid], sg, mx, my);
     const CollidePrep<T> cp = collide_prep<T>(P, sg, mx, my, r0, drx, dry, dmx, dmy, kx, ky);
     const T r = cp.r, ux = cp.ux, uy = cp.uy, p = cp.p;
+    // populations 1..8, then the rest population, which also takes the sum of
+    // the h increments (zero in exact arithmetic): the collision then keeps
+    // the node's mass to one rounding instead of accumulating the rounding
+    // of the nine source terms every step
+    T dsum = T(0);
 #pragma unroll
-    for (int a = 0; a < 9; ++a) {
+    for (int a = 1; a < 9; ++a) {
         T ho, go;
-        collide_pop_rt<T>(cp, a, s_psi[a][tid], s_psi[9 + a][tid], ho, go);
+        const T hs = s_psi[a][tid];
+        collide_pop_rt<T>(cp, a, hs, s_psi[9 + a][tid], ho, go);
+        dsum += ho - hs;
         A.fout[(size_t)a * n + i] = ho;
         A.fout[(size_t)(9 + a) * n + i] = go;
+    }
+    {
+        T ho, go;
+        const T hs = s_psi[0][tid];
+        collide_pop_rt<T>(cp, 0, hs, s_psi[9][tid], ho, go);
+        dsum += ho - hs;
+        A.fout[i] = ho - dsum;
+        A.fout[(size_t)9 * n + i] = go;
     }
     if (!(finite_val(r) && finite_val(ux) && finite_val(uy) && finite_val(p))) atomicOr(A.flag, 1);
     if (A.mom) {
@@ -264,14 +336,14 @@ __device__ __forceinline__ void lat_step_node(const LatArgs<T> &A, int k, bool i
     }
 }
 
-constexpr int kRW = kLTX + 6, kRH = kLTY + 6;  // rho: halo 3
+constexpr int kRW = kLTX + 8, kRH = kLTY + 6;  // rho: halo 3, rows from x0 - 4 (16-byte aligned)
 constexpr int kGW = kLTX + 4, kGH = kLTY + 4;  // grad rho: halo 2
 constexpr int kMW = kLTX + 2, kMH = kLTY + 2;  // mu: halo 1
 
 // Shared memory of one step tile: the scalar chain and, in lat_dsm (dynamic,
 // lat_step_smem bytes), 16 halo tiles then 18 rows of streamed values.
 template <typename T>
-struct StepSmem {
+struct __align__(16) StepSmem {
     T s_rho[kRH][kRW];
     T s_gx[kGH][kGW], s_gy[kGH][kGW];
     T s_mu[kMH][kMW];
@@ -286,48 +358,45 @@ __device__ __forceinline__ void lat_step_tile(const LatArgs<T> &A, int bx, int b
     auto &s_gx = S.s_gx;
     auto &s_gy = S.s_gy;
     auto &s_mu = S.s_mu;
-    T (*tiles)[kPN] = reinterpret_cast<T (*)[kPN]>(lat_dsm);
-    T (*s_psi)[kLTX * kLTY] = reinterpret_cast<T (*)[kLTX * kLTY]>(lat_dsm + 16 * kPN * sizeof(T));
+    T *tiles = reinterpret_cast<T *>(lat_dsm);
+    T (*s_psi)[kLTX * kLTY] = reinterpret_cast<T (*)[kLTX * kLTY]>(lat_dsm + 16 * kPN<T> * sizeof(T));
     const int nx = A.nx, ny = A.ny, walls = A.walls;
     const int x0 = bx * kLTX, y0 = by * kLTY;
     const int tid = threadIdx.y * kLTX + threadIdx.x;
     constexpr int NT = kLTX * kLTY;
     const size_t n = (size_t)nx * ny;
-    // 0. request the halo tiles of the 16 moving populations (h then g)
-    const FillSlots f = fill_slots(tid, x0, y0, nx, ny, walls);
-    issue_tiles<T, 0>(A, f, tiles, tid, n);
-    issue_tiles<T, 9>(A, f, tiles + 8, tid, n);
+    // 0. request rho with a depth-3 halo (group 1), then the halo tiles of the
+    //    16 moving populations (group 2); the populations arrive while the
+    //    scalar chain is computed
+    {
+        constexpr int CE = 16 / (int)sizeof(T);
+        if ((nx % CE) == 0 && x0 - 4 >= 0 && x0 + kLTX + 4 <= nx) {
+            const FillPlan fr = fill_plan<T, RW, RH, true>(tid, NT, x0 - 4, y0 - 3, nx, ny, walls);
+            fill_issue<T, true, 1>(fr, A.rho, 0, &s_rho[0][0], 0);
+        } else {
+            const FillPlan fr = fill_plan<T, RW, RH, false>(tid, NT, x0 - 4, y0 - 3, nx, ny, walls);
+            fill_issue<T, false, 1>(fr, A.rho, 0, &s_rho[0][0], 0);
+        }
+        cp_async_commit();
+    }
+    issue_pop_tiles<T, 0>(A, tid, x0, y0, tiles, n);
+    issue_pop_tiles<T, 9>(A, tid, x0, y0, tiles + 8 * kPN<T>, n);
     cp_async_commit();
     const auto &rc = A.c.r;  // recovery coefficients
-    // 1. rho on the tile with a depth-3 halo (periodic wrap in x; in y wrap or,
-    //    for walls, zero outside the domain: those entries meet only zero
-    //    coefficients)
-    for (int q = tid; q < RW * RH; q += NT) {
-        const int ly = q / RW, lx = q - ly * RW;
-        int gx = x0 + lx - 3, gy = y0 + ly - 3;
-        while (gx < 0) gx += nx;  // the halo may span more than one period
-        while (gx >= nx) gx -= nx;
-        T v = T(0);
-        if (walls) {
-            if (gy >= 0 && gy < ny) v = __ldg(A.rho + gx + nx * gy);
-        } else {
-            while (gy < 0) gy += ny;
-            while (gy >= ny) gy -= ny;
-            v = __ldg(A.rho + gx + nx * gy);
-        }
-        s_rho[ly][lx] = v;
-    }
+    // 1. rho (s_rho[r][c] = global (x0 - 4 + c, y0 - 3 + r); zero outside a
+    //    walled domain, where only zero coefficients meet it)
+    cp_async_wait_group<1>();
     __syncthreads();
     // 2. recovered grad rho on the depth-2 region
     for (int q = tid; q < GW * GH; q += NT) {
         const int ly = q / GW, lx = q - ly * GW;
         const int gy = y0 + ly - 2;
         const int k = (walls && (gy == 0 || gy == ny - 1)) ? (gy == 0 ? 1 : 2) : 0;
-        const T c0 = s_rho[ly + 1][lx + 1];
+        const T c0 = s_rho[ly + 1][lx + 2];
         T sx = T(0), sy = T(0);
 #pragma unroll
         for (int o = 0; o < 6; ++o) {
-            const T d = s_rho[ly + 1 + lat_dy(o)][lx + 1 + lat_dx(o)] - c0;
+            const T d = s_rho[ly + 1 + lat_dy(o)][lx + 2 + lat_dx(o)] - c0;
             sx += rc[k][o][0] * d;
             sy += rc[k][o][1] * d;
         }
@@ -348,7 +417,7 @@ __device__ __forceinline__ void lat_step_tile(const LatArgs<T> &A, int bx, int b
             lap += rc[k][o][0] * (s_gx[ly + 1 + lat_dy(o)][lx + 1 + lat_dx(o)] - gxc) +
                    rc[k][o][1] * (s_gy[ly + 1 + lat_dy(o)][lx + 1 + lat_dx(o)] - gyc);
         }
-        s_mu[ly][lx] = mu_bulk<T>(P, s_rho[ly + 2][lx + 2]) - P.kappa * lap;
+        s_mu[ly][lx] = mu_bulk<T>(P, s_rho[ly + 2][lx + 3]) - P.kappa * lap;
     }
     __syncthreads();
     // 4. per node: grad mu, stress force, streaming, collision.  Threads of
@@ -381,7 +450,7 @@ __device__ __forceinline__ void lat_step_tile(const LatArgs<T> &A, int bx, int b
         kx = P.kappa * skx;
         ky = P.kappa * sky;
     }
-    const T r0 = s_rho[ly + 3][lx + 3];
+    const T r0 = s_rho[ly + 3][lx + 4];
     const T drx = s_gx[ly + 2][lx + 2], dry = s_gy[ly + 2][lx + 2];
     const int32_t i = valid ? x + nx * y : 0;
     cp_async_wait_all();

@@ -2,11 +2,11 @@
 
 Tolerances (relative L2 over all nodes, per field):
 * FP64 GPU run: <= 1e-12 (reordered sums only).
-* FP32 GPU run after 1000 steps: the target is 1e-5 in velocity and C.  The
-  FP32 populations hold it for C at density ratio 10 (8.6e-6) but not for u
-  (1.4e-5), nor at ratio 1000 (C 1.6e-5, u 6.7e-5): in the vapour the
-  momentum part of g (rho u ~ 1e-6) is rounded against its pressure part
-  (w 3p ~ 1e-4).  These tests hold the measured levels as regression bounds.
+* FP32 GPU run after 1000 steps: the target is 1e-5 in velocity and C.  C
+  holds it with a wide margin (1.3e-7 at density ratio 10, 1.6e-7 at ratio
+  1000: the collision is formed as an increment and keeps each node's mass
+  to one rounding).  Velocity does not: 1.3e-5 at ratio 10 and 6.3e-5 at
+  ratio 1000.  These tests hold the measured levels as regression bounds.
 """
 import numpy as np
 import pytest
@@ -111,7 +111,7 @@ def test_fp32_droplet_1000_steps(general):
     o = run_oracle(prob, 1000)
     e = errors(m, o)
     print("fp32 1000-step errors", e)
-    assert e["C"] <= 1e-5 and e["u"] <= 2e-5, e
+    assert e["C"] <= 1e-6 and e["u"] <= 2e-5, e
 
 
 def test_checkpoint_restart_bitwise():
@@ -180,4 +180,4 @@ def test_fullsize_unstructured_fp32_1000_steps():
     o = run_oracle(prob, 1000)
     e = errors(m, o)
     print("c2 1000-step fp32 errors", e)
-    assert e["C"] <= 3e-5 and e["u"] <= 1.5e-4, e
+    assert e["C"] <= 1e-6 and e["u"] <= 1e-4, e
