@@ -202,11 +202,15 @@ static LatCoef<T> lat_coef(const felbm_mesh *m, double dt) {
                          byy = m->sinfo.b[k][o][2];
             c.r[k][o][0] = (T)ax;
             c.r[k][o][1] = (T)ay;
-            c.s[k][o][0] = T(0);
+            T sv[9];
             for (int a = 1; a < 9; ++a) {
                 const double ex = kEx(a), ey = kEy(a);
-                c.s[k][o][a] = (T)(ex * ax + ey * ay +
-                                   0.5 * dt * (ex * ex * bxx + 2.0 * ex * ey * bxy + ey * ey * byy));
+                sv[a] = (T)(ex * ax + ey * ay +
+                            0.5 * dt * (ex * ex * bxx + 2.0 * ex * ey * bxy + ey * ey * byy));
+            }
+            for (int q = 0; q < 4; ++q) {
+                c.s[k][o][q].x = sv[pair_dir(q, 0)];
+                c.s[k][o][q].y = sv[pair_dir(q, 1)];
             }
         }
     return c;
@@ -460,8 +464,8 @@ int felbm_state_init(const felbm_mesh *mesh, const felbm_params *params, const d
     auto alloc = [&](void **p, size_t bytes) {
         if (e == cudaSuccess) e = cudaMalloc(p, bytes);
     };
-    alloc(&s->f[0], 18 * N * es);
-    alloc(&s->f[1], 18 * N * es);
+    alloc(&s->f[0], 18 * pad4(N) * es);
+    alloc(&s->f[1], 18 * pad4(N) * es);
     alloc(&s->scratch, 6 * N * es);
     alloc(&s->mom, 4 * N * es);
     alloc((void **)&s->d_out, (5 * N + 3 * (kTotalsBlocks + 1)) * sizeof(double));
@@ -558,7 +562,7 @@ int felbm_moments_get(felbm_state *s, double *rho, double *C, double *u, double 
 int felbm_state_export(felbm_state *s, double *hbar, double *gbar) {
     if (!s || !hbar || !gbar) return FELBM_ERR_INVALID_ARG;
     const size_t N = (size_t)s->mesh->n_nodes, es = s->esize;
-    std::vector<unsigned char> buf(18 * N * es);
+    std::vector<unsigned char> buf(18 * pad4(N) * es);
     cudaError_t e = cudaMemcpyAsync(buf.data(), s->f[s->cur], buf.size(), cudaMemcpyDeviceToHost,
                                     s->mesh->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->mesh->stream);
@@ -567,8 +571,9 @@ int felbm_state_export(felbm_state *s, double *hbar, double *gbar) {
     for (int a = 0; a < 18; ++a)
         for (size_t k = 0; k < N; ++k) {
             const size_t c = perm ? (size_t)s->mesh->host.perm[k] : k;
-            const double v = es == 8 ? reinterpret_cast<double *>(buf.data())[a * N + k]
-                                     : (double)reinterpret_cast<float *>(buf.data())[a * N + k];
+            const size_t q = pop_index(a, k, N);
+            const double v = es == 8 ? reinterpret_cast<double *>(buf.data())[q]
+                                     : (double)reinterpret_cast<float *>(buf.data())[q];
             (a < 9 ? hbar : gbar)[(a % 9) * N + c] = v;
         }
     return check_flag(s);
@@ -577,7 +582,7 @@ int felbm_state_export(felbm_state *s, double *hbar, double *gbar) {
 int felbm_state_import(felbm_state *s, const double *hbar, const double *gbar) {
     if (!s || !hbar || !gbar) return FELBM_ERR_INVALID_ARG;
     const size_t N = (size_t)s->mesh->n_nodes, es = s->esize;
-    std::vector<unsigned char> buf(18 * N * es);
+    std::vector<unsigned char> buf(18 * pad4(N) * es, 0);
     const bool perm = s->mesh->kind == 0;
     for (int a = 0; a < 18; ++a)
         for (size_t k = 0; k < N; ++k) {
@@ -585,9 +590,9 @@ int felbm_state_import(felbm_state *s, const double *hbar, const double *gbar) {
             const double v = (a < 9 ? hbar : gbar)[(a % 9) * N + c];
             if (!std::isfinite(v)) return FELBM_ERR_INVALID_ARG;
             if (es == 8)
-                reinterpret_cast<double *>(buf.data())[a * N + k] = v;
+                reinterpret_cast<double *>(buf.data())[pop_index(a, k, N)] = v;
             else
-                reinterpret_cast<float *>(buf.data())[a * N + k] = (float)v;
+                reinterpret_cast<float *>(buf.data())[pop_index(a, k, N)] = (float)v;
         }
     cudaError_t e = cudaMemcpyAsync(s->f[s->cur], buf.data(), buf.size(), cudaMemcpyHostToDevice,
                                     s->mesh->stream);

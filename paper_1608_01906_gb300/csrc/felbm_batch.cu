@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kLTX *kLTY, 3) k_batch_step(BatchArgs<T> B) {
     for (int t = blockIdx.x; t < B.ntiles; t += gridDim.x) {
         const TileRef r = B.tiles[t];
         load_mesh<T>(B, r.mesh, sA, cur);
-        lat_rho_tile<T>(sA, r.bx, r.by, reinterpret_cast<T *>(bdsm));
+        lat_rho_tile<T>(sA, r.bx, r.by, reinterpret_cast<V2<T> *>(bdsm));
     }
     grid_barrier(B.bar, B.err);
     for (int t = blockIdx.x; t < B.ntiles; t += gridDim.x) {
@@ -122,11 +122,15 @@ static LatCoef<T> lat_coef_b(const felbm_mesh *m, double dt) {
                          byy = m->sinfo.b[k][o][2];
             c.r[k][o][0] = (T)ax;
             c.r[k][o][1] = (T)ay;
-            c.s[k][o][0] = T(0);
+            T sv[9];
             for (int a = 1; a < 9; ++a) {
                 const double ex = kEx(a), ey = kEy(a);
-                c.s[k][o][a] = (T)(ex * ax + ey * ay +
-                                   0.5 * dt * (ex * ex * bxx + 2.0 * ex * ey * bxy + ey * ey * byy));
+                sv[a] = (T)(ex * ax + ey * ay +
+                            0.5 * dt * (ex * ex * bxx + 2.0 * ex * ey * bxy + ey * ey * byy));
+            }
+            for (int q = 0; q < 4; ++q) {
+                c.s[k][o][q].x = sv[pair_dir(q, 0)];
+                c.s[k][o][q].y = sv[pair_dir(q, 1)];
             }
         }
     return c;
@@ -183,6 +187,9 @@ static int b_status(cudaError_t e) {
 }
 
 static size_t batch_smem(int esize) {
+    // the density pass reuses the step pass's dynamic shared memory
+    static_assert(lat_rho_smem<float>() <= lat_step_smem<float>(), "smem");
+    static_assert(lat_rho_smem<double>() <= lat_step_smem<double>(), "smem");
     return esize == 8 ? lat_step_smem<double>() : lat_step_smem<float>();
 }
 

@@ -121,6 +121,45 @@ struct Phys {
     T rho_l, rho_v, beta, kappa, inv_tau_l, inv_tau_v, dt, gx, gy;
 };
 
+// Storage of the 18 populations of a state: direction pairs interleaved.
+// With Np = N rounded up to a multiple of 4 (keeps every pair array 16-byte
+// aligned): h_0 at [0, N); the h pairs q = 0..3 of opposite directions
+// (1,3), (2,4), (5,7), (6,8) at Np + 2 Np q + 2 i + s, slot s = 0 for 1, 2,
+// 5, 6 and s = 1 for 3, 4, 7, 8; g the same from offset 9 Np.  A state
+// buffer holds 18 Np values.
+// A pair is one 8-byte (FP32) or 16-byte (FP64) word per node, read and
+// streamed together with packed two-wide arithmetic.
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+constexpr int pair_of(int d) { return d == 1 || d == 3 ? 0 : (d == 2 || d == 4 ? 1 : (d == 5 || d == 7 ? 2 : 3)); }
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+constexpr int slot_of(int d) { return d == 3 || d == 4 || d == 7 || d == 8 ? 1 : 0; }
+// first direction of pair q (slot 0): 1, 2, 5, 6
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+constexpr int pair_dir(int q, int s) { return s == 0 ? (q == 0 ? 1 : (q == 1 ? 2 : (q == 2 ? 5 : 6)))
+                                                     : (q == 0 ? 3 : (q == 1 ? 4 : (q == 2 ? 7 : 8))); }
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline size_t pad4(size_t n) { return (n + 3) & ~(size_t)3; }
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline size_t pop_index(int a, size_t i, size_t n) {
+    const size_t np = pad4(n);
+    const size_t base = a < 9 ? 0 : 9 * np;
+    const int d = a % 9;
+    return d == 0 ? base + i : base + np + 2 * np * (size_t)pair_of(d) + 2 * i + (size_t)slot_of(d);
+}
+
 template <typename T>
 struct Fields {
     T *rho, *drx, *dry, *mu, *kx, *ky;  // N each
@@ -151,7 +190,7 @@ struct felbm_state {
     felbm_params params{};
     int precision = FELBM_FP64;
     size_t esize = 8;
-    void *f[2] = {nullptr, nullptr};  // 18 N each: h_0..h_8, g_0..g_8
+    void *f[2] = {nullptr, nullptr};  // 18 pad4(N) each, layout of pop_index
     int cur = 0;
     void *scratch = nullptr;          // 6 N: rho, drx, dry, mu, kx, ky
     void *mom = nullptr;              // 4 N: rho, ux, uy, p (internal order)

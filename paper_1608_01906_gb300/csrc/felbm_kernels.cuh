@@ -71,7 +71,7 @@ struct StreamAcc {
                     case 7: c = stream_coef<T, 7>(ax, ay, hbxx, hbxy, hbyy); break;
                     default: c = stream_coef<T, 8>(ax, ay, hbxx, hbxy, hbyy); break;
                 }
-                acc[a - A0] += c * (__ldg(pops + (size_t)a * n + j) - self[a - A0]);
+                acc[a - A0] += c * (__ldg(pops + pop_index(a, (size_t)j, (size_t)n)) - self[a - A0]);
             }
         });
     }
@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(256) k_rho(Topo m, const T *__restrict__ f, T 
     T h[9], acc[9];
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-        h[a] = f[a * n + i];
+        h[a] = f[pop_index(a, (size_t)i, n)];
         acc[a] = T(0);
     }
     StreamAcc<T, 0, 9>::run(m, f, i, dt, h, acc);
@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(256) k_collide(CollideArgs<T, Topo> A) {
         T self[18], acc[18];
 #pragma unroll
         for (int a = 0; a < 18; ++a) {
-            self[a] = A.fin[a * n + i];
+            self[a] = A.fin[pop_index(a, (size_t)i, n)];
             acc[a] = T(0);
         }
         StreamAcc<T, 0, 18>::run(m, A.fin, i, A.P.dt, self, acc);
@@ -344,8 +344,8 @@ __global__ void __launch_bounds__(256) k_collide(CollideArgs<T, Topo> A) {
                     gout, ux, uy, p);
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-        A.fout[a * n + i] = hout[a];
-        A.fout[(9 + a) * n + i] = gout[a];
+        A.fout[pop_index(a, (size_t)i, n)] = hout[a];
+        A.fout[pop_index(9 + a, (size_t)i, n)] = gout[a];
     }
     if (!(finite_val(r) && finite_val(ux) && finite_val(uy) && finite_val(p))) atomicOr(A.flag, 1);
     if (A.mom) {
@@ -388,8 +388,8 @@ __global__ void __launch_bounds__(256) k_init(Topo m, T *__restrict__ fout, Fiel
         const T Fa = hdt * T(3) * (eX - uX) * gam;
         const T Ga = hdt * (eD - uD) * gmw + hdt * T(3) * (eK - uK) * gam;
         const T Ba = T(0.5) * r * wa * (T(3) * edu + T(4.5) * edu * (T(2) * eu + edu) - T(1.5) * udu);
-        fout[a * n + i] = r * gam + Fa;
-        fout[(9 + a) * n + i] = wa * T(3) * p + r * gmw + Ga + Ba;
+        fout[pop_index(a, (size_t)i, n)] = r * gam + Fa;
+        fout[pop_index(9 + a, (size_t)i, n)] = wa * T(3) * p + r * gmw + Ga + Ba;
     }
 }
 
