@@ -33,6 +33,11 @@ namespace felbm {
 
 constexpr int kLTX = 32, kLTY = 8;  // tile of nodes per block
 
+template <int V>
+struct IntC {
+    static constexpr int value = V;
+};
+
 template <typename T>
 struct V2T;
 template <>
@@ -53,6 +58,10 @@ __device__ __forceinline__ double2 vfma(double2 a, double2 b, double2 c) {
 }
 __device__ __forceinline__ float2 vset(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ double2 vset(double a, double b) { return make_double2(a, b); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ double2 vadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ double2 vmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
 
 template <typename T>
 struct LatCoef {
@@ -215,6 +224,42 @@ __device__ __forceinline__ V2<T> streamed2(const LatCoef<T> &c, int k, bool inte
     return vfma(vset(-dt, -dt), acc, self);
 }
 
+// Collision of the opposite pair q = (a, abar) of one node (see
+// collide_pop): e_abar = -e_a and w_abar = w_a, so the odd parts (e.u, e.X,
+// e.grad rho, e.K, e.du) flip sign between the two lanes and the even parts
+// are shared; the two lanes run in packed two-wide arithmetic.
+template <typename T, int Q>
+__device__ __forceinline__ void collide_pair(const CollidePrep<T> &c, V2<T> hs, V2<T> gs, V2<T> &ho,
+                                             V2<T> &go) {
+    constexpr int A = pair_dir(Q, 0);
+    constexpr int ex = kEx(A), ey = kEy(A);
+    constexpr T wa = kW<T>(A);
+    const T eu = T(ex) * c.ux + T(ey) * c.uy;
+    const T eX = T(ex) * c.Xx + T(ey) * c.Xy;
+    const T eD = T(ex) * c.drx + T(ey) * c.dry;
+    const T eK = T(ex) * c.kx + T(ey) * c.ky;
+    const T edu = T(ex) * c.dux + T(ey) * c.duy;
+    // Gamma - w = w (3 e.u + 4.5 (e.u)^2 - 1.5 u.u), formed without the w
+    // offset (FP32: keeps the momentum part)
+    const T even = T(4.5) * eu * eu - T(1.5) * c.uu;
+    const V2<T> gmw = vfma(vset(T(3) * wa, T(3) * wa), vset(eu, -eu), vset(wa * even, wa * even));
+    const V2<T> gam = vadd(gmw, vset(wa, wa));
+    const T h3 = c.hdt * T(3);
+    const V2<T> Fa = vmul(vset(h3 * (eX - c.uX), h3 * (-eX - c.uX)), gam);
+    const V2<T> Ga = vfma(vset(c.hdt * (eD - c.uD), c.hdt * (-eD - c.uD)), gmw,
+                          vmul(vset(h3 * (eK - c.uK), h3 * (-eK - c.uK)), gam));
+    // 1/2 [g_eq(u + du) - g_eq(u)] = rho/2 [Gamma(u + du) - Gamma(u)]
+    const T bev = T(4.5) * edu * (T(2) * eu + edu) - T(1.5) * c.udu;
+    const T hrw = T(0.5) * c.r * wa;
+    const V2<T> Sg = vfma(vset(hrw, hrw), vset(T(3) * edu + bev, bev - T(3) * edu), Ga);
+    const V2<T> rg = vmul(vset(c.r, c.r), gmw);
+    const V2<T> dh = vadd(vfma(vset(c.r, c.r), vset(wa, wa), vset(-hs.x, -hs.y)), rg);  // h_eq - h*
+    const T p3 = wa * T(3) * c.p;
+    const V2<T> dg = vadd(vset(p3 - gs.x, p3 - gs.y), rg);  // g_eq - g*
+    ho = vadd(hs, vfma(vset(c.omw, c.omw), dh, vmul(vset(c.opw, c.opw), Fa)));
+    go = vadd(gs, vfma(vset(c.omw, c.omw), dg, vmul(vset(c.opw, c.opw), Sg)));
+}
+
 // Weight of streamed h_a in rho at a wall row of kind k (bounce-back replaces
 // each population entering the fluid by its opposite).
 __device__ __forceinline__ int bb_mult(int k, int a) {
@@ -350,16 +395,19 @@ __device__ __forceinline__ void lat_step_node(const LatArgs<T> &A, int k, bool i
     T dsum = T(0);
     V2<T> *hout = reinterpret_cast<V2<T> *>(A.fout + np);
     V2<T> *gout = reinterpret_cast<V2<T> *>(A.fout + 10 * np);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    auto pair_update = [&](auto qc) {
+        constexpr int q = decltype(qc)::value;
         const V2<T> hs = s_psi[q][tid], gs = s_psi[4 + q][tid];
-        T ha, ga, hb, gb;
-        collide_pop_rt<T>(cp, pair_dir(q, 0), hs.x, gs.x, ha, ga);
-        collide_pop_rt<T>(cp, pair_dir(q, 1), hs.y, gs.y, hb, gb);
-        dsum += (ha - hs.x) + (hb - hs.y);
-        hout[(size_t)q * np + i] = vset(ha, hb);
-        gout[(size_t)q * np + i] = vset(ga, gb);
-    }
+        V2<T> ho, go;
+        collide_pair<T, q>(cp, hs, gs, ho, go);
+        dsum += (ho.x - hs.x) + (ho.y - hs.y);
+        hout[(size_t)q * np + i] = ho;
+        gout[(size_t)q * np + i] = go;
+    };
+    pair_update(IntC<0>{});
+    pair_update(IntC<1>{});
+    pair_update(IntC<2>{});
+    pair_update(IntC<3>{});
     {
         T ho, go;
         collide_pop_rt<T>(cp, 0, h0, g0, ho, go);
@@ -498,7 +546,7 @@ __device__ __forceinline__ void lat_step_tile(const LatArgs<T> &A, int bx, int b
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kLTX *kLTY, 3) k_lat_step(LatArgs<T> A) {
+__global__ void __launch_bounds__(kLTX *kLTY, 4) k_lat_step(LatArgs<T> A) {
     __shared__ StepSmem<T> S;
     extern __shared__ __align__(16) unsigned char lat_dsm[];
     lat_step_tile<T>(A, blockIdx.x, blockIdx.y, S, lat_dsm);
