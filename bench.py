@@ -260,7 +260,7 @@ def run_serving(torch, felbm, capacity_mnups, n_requests):
     budget = 64 * 1024 ** 3
     results, stats = serving.serve(reqs, budget, chunk=500, stream=stream.cuda_stream)
     stats.update({"requests": n_requests, "rate_per_s": rate, "budget_gb": 64,
-                  "load": "80% of batched capacity %.0f MNUPS" % capacity_mnups,
+                  "load": "80%% of batched capacity %.0f MNUPS" % capacity_mnups,
                   "workload": "droplet runs, sides log-uniform [64,1024], ratio U[10,1000], "
                               "steps U[1000,20000], Poisson arrivals (seed 1610), FP32"})
     return stats
@@ -369,9 +369,16 @@ def main():
                          % (nsteps, el)}
     batched = serving = None
     if rank == 0 and world == 1 and not args.skip_batched:
-        batched = run_batched(torch, felbm)
-        if not args.skip_serving:
-            serving = run_serving(torch, felbm, batched["value"], args.serve_requests)
+        # the headline line prints even if a secondary measurement fails
+        try:
+            batched = run_batched(torch, felbm)
+        except Exception as e:  # noqa: BLE001
+            batched = {"error": "%s: %s" % (type(e).__name__, e)}
+        if not args.skip_serving and "value" in batched:
+            try:
+                serving = run_serving(torch, felbm, batched["value"], args.serve_requests)
+            except Exception as e:  # noqa: BLE001
+                serving = {"error": "%s: %s" % (type(e).__name__, e)}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup,

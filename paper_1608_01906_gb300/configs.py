@@ -27,7 +27,10 @@ restated in 2-D.  Readings fixed here (documented in the design notes):
   sigma = 1e-4 (the model needs sigma > 0).  With sqrt(lambda g) = 0.04 or
   0.06 (tau 0.041, 0.061) a mode at the bounce-back walls grows about 4.6x
   per 1000 steps and the run diverges.
-* Batched / served droplets: tau_l = tau_v = 0.1, dt = 0.5, xi = 16.
+* Batched / served droplets: tau_l = tau_v = 0.1, dt = 0.5, xi = 24.  At xi = 16
+  ratio 1000 diverges after 10000-18000 steps on sides 128-1024 (ratios 10 and
+  100 hold for 20000); xi = 24 and 32 hold ratio 1000 for 20000 steps on
+  sides 64-1024 (measured).
 """
 from __future__ import annotations
 
@@ -111,6 +114,9 @@ def c3_rayleigh_taylor(nx=512, ny=2048, steps=20000, Re=3000.0, uref=0.08):
                    {"nx": nx, "ny": ny, "Re": Re, "At": 0.5, "g": g, "nu": nu})
 
 
+DROPLET_XI = 24.0
+
+
 def batched_sides(count=64, lo=32, hi=512, seed=1609):
     """Mesh sides log-uniform in [lo, hi] (integers, multiples of 1)."""
     rng = np.random.default_rng(seed)
@@ -125,6 +131,6 @@ def c4_batched(count=64, seed=1609, lo=32, hi=512):
     density ratio U[10, 1000], radius U[0.2, 0.35] of the side, FP32."""
     out = []
     for k, (side, ratio, rfrac) in enumerate(batched_sides(count, lo, hi, seed)):
-        out.append(droplet_structured(side, rfrac * side, ratio, 16.0, 0.01, 0.1, 0.1, 0.5, 0,
+        out.append(droplet_structured(side, rfrac * side, ratio, DROPLET_XI, 0.01, 0.1, 0.1, 0.5, 0,
                                       "fp32", "batch_%02d_%d" % (k, side)))
     return out

@@ -9,7 +9,9 @@ per time step (``felbm_batch_*``).  Between chunks of steps it
   and the state is freed),
 * admits arrived requests while the HBM budget allows (the mesh of a side is
   shared by every run on it),
-* rebuilds the batch when its membership changed.
+* rebuilds the batch when its membership changed,
+* retires a run whose fields went non-finite as ``diverged`` (its state's
+  own flag says which run it was) while the others carry on.
 
 A run's result does not depend on which other runs shared its launches (the
 batched kernel runs the same per-node arithmetic as a stand-alone step), so
@@ -53,6 +55,7 @@ class Result:
     steps: int
     nodes: int
     moments: dict
+    status: str = "ok"      # "ok" or "diverged"
 
     @property
     def latency(self):
@@ -83,7 +86,8 @@ def state_bytes(side, precision="fp32"):
 
 
 def problem_for(req: Request):
-    return configs.droplet_structured(req.side, req.radius_frac * req.side, req.ratio, 16.0, 0.01,
+    return configs.droplet_structured(req.side, req.radius_frac * req.side, req.ratio,
+                                      configs.DROPLET_XI, 0.01,
                                       0.1, 0.1, 0.5, req.steps, "fp32", "req%d" % req.rid)
 
 
@@ -103,6 +107,7 @@ class Server:
         self.dirty = True
         self.results = []
         self.node_steps = 0
+        self.t0 = time.perf_counter()
 
     # ---- resources ----------------------------------------------------
     def _mesh(self, req):
@@ -134,11 +139,11 @@ class Server:
         self.active.append({"req": req, "state": st, "done": 0, "admitted": now})
         self.dirty = True
 
-    def _retire(self, slot, now):
+    def _retire(self, slot, now, status="ok"):
         req = slot["req"]
-        m = slot["state"].moments()
-        self.results.append(Result(req.rid, req.arrival, slot["admitted"], now, req.steps,
-                                   req.nodes, m))
+        m = slot["state"].moments() if status == "ok" else {}
+        self.results.append(Result(req.rid, req.arrival, slot["admitted"], now, slot["done"],
+                                   req.nodes, m, status))
         slot["state"].close()
         self._release_mesh(req.side)
         self.used -= state_bytes(req.side, self.precision)
@@ -156,10 +161,24 @@ class Server:
             self.dirty = False
         n = min(self.chunk, min(s["req"].steps - s["done"] for s in self.active))
         self.batch.step(n)
-        self.batch.sync()
+        diverged = []
+        try:
+            self.batch.sync()
+        except felbm.FelbmError as e:
+            if e.status != felbm.FELBM_ERR_NONFINITE:
+                raise
+            diverged = [s for s in self.active
+                        if felbm.felbm_state_sync(s["state"].handle) == felbm.FELBM_ERR_NONFINITE]
+            if not diverged:
+                raise
         for s in self.active:
             s["done"] += n
             self.node_steps += n * s["req"].nodes
+        if diverged:
+            now = time.perf_counter() - self.t0
+            for s in diverged:
+                self._retire(s, now, "diverged")
+            self.active = [s for s in self.active if all(s is not d for d in diverged)]
         return n
 
     def retire_finished(self, now):
@@ -188,7 +207,7 @@ def serve(requests, budget_bytes, chunk=200, stream=None, time_scale=1.0, autotu
     srv = Server(budget_bytes, chunk=chunk, stream=stream, autotune=autotune)
     pending = sorted(requests, key=lambda r: r.arrival)
     queue = []  # arrived, not yet admitted (FIFO by arrival)
-    t0 = time.perf_counter()
+    t0 = srv.t0 = time.perf_counter()
     i = 0
     try:
         while i < len(pending) or queue or srv.active:
@@ -214,10 +233,12 @@ def serve(requests, budget_bytes, chunk=200, stream=None, time_scale=1.0, autotu
         results = list(srv.results)
         node_steps = srv.node_steps
         srv.close()
-    # latencies measured from the (scaled) arrival time
-    lat = np.array([r.finished - r.arrival * time_scale for r in results]) if results else np.zeros(0)
+    # latencies measured from the (scaled) arrival time, over completed runs
+    done = [r for r in results if r.status == "ok"]
+    lat = np.array([r.finished - r.arrival * time_scale for r in done]) if done else np.zeros(0)
     stats = {
-        "completed": len(results),
+        "completed": len(done),
+        "diverged": len(results) - len(done),
         "wall_s": wall,
         "aggregate_mnups": node_steps / wall / 1e6 if wall > 0 else 0.0,
         "p50_s": float(np.percentile(lat, 50)) if len(lat) else None,

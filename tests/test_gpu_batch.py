@@ -20,8 +20,8 @@ def _lib():
 
 def mixed_problems():
     probs = [configs.droplet_structured(40, 10.0, 10.0, xi=4.0),
-             configs.droplet_structured(64, 20.0, 300.0, xi=16.0, tau_l=0.1, tau_v=0.1),
-             configs.droplet_structured(33, 9.0, 1000.0, xi=16.0, tau_l=0.1, tau_v=0.1)]
+             configs.droplet_structured(64, 20.0, 300.0, xi=configs.DROPLET_XI, tau_l=0.1, tau_v=0.1),
+             configs.droplet_structured(33, 9.0, 1000.0, xi=configs.DROPLET_XI, tau_l=0.1, tau_v=0.1)]
     rt = configs.c3_rayleigh_taylor(nx=48, ny=100)
     probs.append(rt)
     xy, tri, box, tag = inputs.structured_mesh(70, 45)

@@ -69,3 +69,52 @@ def test_scheduler_budget_chunks_and_retirement(monkeypatch):
     assert done == {0: 100, 1: 250, 2: 60, 3: 300}
     # total node-steps equal the requested work
     assert sum(n * c for n, c in FakeBatch.log) == 100 + 250 + 60 + 300
+
+
+def test_diverged_run_is_retired_and_the_rest_finish(monkeypatch):
+    """A run whose fields go non-finite is retired as diverged at the chunk
+    where the batch reports it; the other runs carry on to their step count."""
+    class DState(FakeState):
+        count = 0
+
+        def __init__(self, *a, **k):
+            super().__init__()
+            self.handle = DState.count
+            DState.count += 1
+
+    class DBatch(FakeBatch):
+        def __init__(self, states, autotune=True):
+            super().__init__(states, autotune)
+            self.handles = [s.handle for s in states]
+            self.steps = 0
+
+        def step(self, n):
+            super().step(n)
+            self.steps += n
+
+        def sync(self):
+            if 1 in self.handles and DBatch.total + self.steps >= 120:
+                raise serving.felbm.FelbmError(serving.felbm.FELBM_ERR_NONFINITE, "sync")
+
+        def close(self):
+            DBatch.total += self.steps
+
+    DBatch.total = 0
+    monkeypatch.setattr(serving.felbm, "Mesh", FakeMesh)
+    monkeypatch.setattr(serving.felbm, "State", DState)
+    monkeypatch.setattr(serving.felbm, "Batch", DBatch)
+    monkeypatch.setattr(serving.felbm, "felbm_state_sync",
+                        lambda h: serving.felbm.FELBM_ERR_NONFINITE if h == 1 else 0)
+    monkeypatch.setattr(serving, "problem_for", lambda req: type(
+        "P", (), {"xy": None, "tri": None, "box": None, "tag": None, "rho0": None, "u0": None,
+                  "p0": None, "params": {"rho_l": 1.0, "rho_v": 0.1, "sigma": 0.01, "xi": 4.0,
+                                         "tau_l": 0.1, "tau_v": 0.1, "dt": 0.5,
+                                         "gravity": (0.0, 0.0)}})())
+    FakeBatch.log = []
+    reqs = [serving.Request(k, 0.0, 64, 10.0, 0.3, s) for k, s in enumerate([300, 400, 200])]
+    results, stats = serving.serve(reqs, 3 * serving.state_bytes(64), chunk=40, autotune=False)
+    by = {r.rid: r for r in results}
+    assert stats["completed"] == 2 and stats["diverged"] == 1
+    assert by[1].status == "diverged" and by[1].steps == 120 and by[1].moments == {}
+    assert by[0].status == "ok" and by[0].steps == 300
+    assert by[2].status == "ok" and by[2].steps == 200
