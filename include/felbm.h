@@ -128,7 +128,8 @@ void felbm_mesh_destroy(felbm_mesh *mesh);
  *   rho0  host, n_nodes doubles, > 0.
  *   u0    host, n_nodes x 2 doubles (ux, uy) or NULL for rest.
  *   p0    host, n_nodes doubles or NULL for zero pressure.
- * Device memory: 2 x 18 n_nodes values of the chosen precision plus scratch.
+ * Device memory: 2 x 18 n_nodes values of the chosen precision plus scratch
+ * (structured meshes with nx % 4 == 0: also 768 bytes of TMA tensor maps).
  * Errors: INVALID_ARG, OOM, CUDA. */
 int felbm_state_init(const felbm_mesh *mesh, const felbm_params *params, const double *rho0,
                      const double *u0, const double *p0, felbm_state **out);
@@ -138,7 +139,9 @@ int felbm_state_init(const felbm_mesh *mesh, const felbm_params *params, const d
 int felbm_step(felbm_state *state, int64_t n_steps);
 
 /* Wait for the state's work and report FELBM_ERR_NONFINITE if any step
- * produced a non-finite density, velocity or pressure. */
+ * produced a non-finite density, velocity or pressure, else
+ * FELBM_ERR_TIMEOUT if a bounded device wait for a tile's TMA halo load gave
+ * up (that step's tile was not updated). */
 int felbm_state_sync(felbm_state *state);
 
 /* Moments of the latest step (or of the initial fields before any step):
@@ -164,20 +167,21 @@ void felbm_state_destroy(felbm_state *state);
 
 /* ---- batched launch (many runs per launch; the paper has a single run) ---
  * A batch advances many states on structured meshes (felbm_mesh_info kind
- * 1) of any sizes in one persistent, cooperative launch per time step: the
- * density pass of every 32 x 8 tile of every mesh, a grid-wide barrier, then
- * the step pass of every tile.  Each state's results are the same as from
- * felbm_step alone (same per-node arithmetic).  Step pairs are replayed from
- * a CUDA graph.  With FELBM_BATCH_AUTOTUNE the first felbm_batch_step long
- * enough to afford it times real steps under each candidate (blocks per SM
- * from 1 to the co-resident maximum, tile order mesh-major or interleaved)
- * and keeps the fastest; those steps count toward n_steps.
+ * 1) of any sizes in one launch per time step over every 32 x 8 tile of every
+ * mesh.  Each state's results are the same as from felbm_step alone (same
+ * per-tile code).  Step pairs are replayed from a CUDA graph.  With
+ * FELBM_BATCH_AUTOTUNE the first felbm_batch_step long enough to afford it
+ * times real steps under each candidate (a persistent grid of 1 to the
+ * co-resident maximum blocks per SM, or one block per tile, reported as 0;
+ * tile order mesh-major or interleaved) and keeps the fastest; those steps
+ * count toward n_steps.
  *   states   n_states distinct states, same precision, meshes on the same
  *            stream; the batch borrows them (they must outlive it).
  * Stepping a member state on its own between batch steps is allowed; the
  * next felbm_batch_step then waits for the stream and rebuilds its tables.
- * Errors: INVALID_ARG, UNSUPPORTED (a general mesh), OOM, CUDA; TIMEOUT from
- * felbm_batch_sync if the barrier's bounded wait ever gave up. */
+ * Errors: INVALID_ARG, UNSUPPORTED (a general mesh), OOM, CUDA; NONFINITE
+ * (or TIMEOUT) from felbm_batch_sync as a member's felbm_state_sync reports
+ * it. */
 #define FELBM_BATCH_AUTOTUNE 0x1u
 int felbm_batch_create(felbm_state *const *states, int32_t n_states, uint32_t flags,
                        felbm_batch **out);
@@ -193,8 +197,8 @@ void felbm_batch_destroy(felbm_batch *batch);
  * Kernel kinds issued by felbm_step, reported by felbm_profile_read:
  *   0 stream h + rho, 1 grad rho, 2 lap rho / stress / mu,
  *   3 grad mu + stream + collide (the general four-pass step),
- *   4 fused lattice step (one launch per step on structured meshes),
- *   5 lattice density pre-pass. */
+ *   4 lattice step (one launch per step on structured meshes),
+ *   5-7 unused. */
 #define FELBM_PROFILE_KINDS 8
 
 /* on != 0: every kernel launched by later felbm_step calls is bracketed by a

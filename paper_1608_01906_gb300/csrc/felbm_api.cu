@@ -1,4 +1,5 @@
 // C ABI of the FE-LBM library: handle management, uploads, launches.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -222,12 +223,10 @@ static void step_lattice(felbm_state *s, LatArgs<T> &A, bool write_mom) {
     A.fin = reinterpret_cast<const T *>(s->f[s->cur]);
     A.fout = reinterpret_cast<T *>(s->f[s->cur ^ 1]);
     A.mom = write_mom ? reinterpret_cast<T *>(s->mom) : nullptr;
-    const dim3 blk(kLTX, kLTY), grd((A.nx + kLTX - 1) / kLTX, (A.ny + kLTY - 1) / kLTY);
-    int sl = prof_begin(s, 5);
-    k_lat_rho<T><<<grd, blk, 0, m->stream>>>(A);
-    prof_end(s, sl);
-    sl = prof_begin(s, 4);
-    k_lat_step<T><<<grd, blk, lat_step_smem<T>(), m->stream>>>(A);
+    A.tmap = s->d_tmap ? s->d_tmap + 3 * s->cur : nullptr;
+    const dim3 grd((A.nx + kLTX - 1) / kLTX, (A.ny + kLTY - 1) / kLTY);
+    const int sl = prof_begin(s, 4);
+    k_lat_step<T><<<grd, dim3(kLTX, kLTY), lat_smem<T>(), m->stream>>>(A);
     prof_end(s, sl);
     s->cur ^= 1;
 }
@@ -239,7 +238,7 @@ static void do_steps(felbm_state *s, int64_t n) {
         static bool attr_set = false;  // once per instantiation (per process)
         if (!attr_set) {
             cudaFuncSetAttribute(k_lat_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)lat_step_smem<T>());
+                                 (int)lat_smem<T>());
             attr_set = true;
         }
         LatArgs<T> A;
@@ -433,6 +432,7 @@ static void state_free(felbm_state *s) {
     cudaFree(s->mom);
     cudaFree(s->d_out);
     cudaFree(s->d_flag);
+    cudaFree(s->d_tmap);
     delete s;
 }
 
@@ -508,6 +508,7 @@ int felbm_state_init(const felbm_mesh *mesh, const felbm_params *params, const d
         state_free(s);
         return rs;
     }
+    lattice_tmaps(s);  // optional: tiles fall back to cp.async fills without maps
     s->have_moments = true;
     *out = s;
     return FELBM_OK;
@@ -530,7 +531,7 @@ static int check_flag(felbm_state *s) {
     cudaError_t e = cudaMemcpyAsync(&h, s->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s->mesh->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->mesh->stream);
     if (e != cudaSuccess) return cuda_status(e);
-    return h ? FELBM_ERR_NONFINITE : FELBM_OK;
+    return (h & 1) ? FELBM_ERR_NONFINITE : (h & 4) ? FELBM_ERR_TIMEOUT : FELBM_OK;
 }
 
 int felbm_state_sync(felbm_state *s) {
@@ -654,7 +655,7 @@ int felbm_profile_read(felbm_state *s, double *ms, int64_t *timed, int64_t *laun
 
 const char *felbm_profile_kind_name(int k) {
     static const char *names[FELBM_PROFILE_KINDS] = {
-        "k_rho", "k_grad", "k_mu", "k_collide", "k_lattice_step", "k_lattice_rho", "unused6",
+        "k_rho", "k_grad", "k_mu", "k_collide", "k_lattice_step", "unused5", "unused6",
         "unused7"};
     return (k >= 0 && k < FELBM_PROFILE_KINDS) ? names[k] : nullptr;
 }

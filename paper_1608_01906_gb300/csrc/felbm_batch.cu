@@ -1,16 +1,18 @@
 // Batched time step: many structured-lattice states of uneven size advance
-// in one persistent, cooperative launch per time step.
+// in one launch per time step.
 //
-// The launch walks a global list of 32 x 8 tiles of all meshes twice: the
-// density pass for every tile, a grid-wide barrier, then the step pass for
-// every tile (the per-tile code is the one of the single-mesh kernels, so a
-// state's results do not depend on which other states share the launch).
-// The grid is sized to the co-resident block count (cooperative launch), the
-// barrier is a counter with a bounded spin: a wait that gives up sets an
-// error word the host reports as FELBM_ERR_TIMEOUT.  Launches of whole step
-// pairs are captured in a CUDA graph.  An autotuner picks the blocks per SM
-// and the tile order by timing real steps (all candidates compute identical
-// values, so tuning steps are ordinary steps of the runs).
+// The launch walks a global list of the 32 x 8 tiles of all meshes and runs
+// the single-mesh tile step on each (so a state's results do not depend on
+// which other states share the launch).  A tile step reads only the previous
+// step's populations, so no tile waits for another within a launch.  The
+// grid is either persistent (blocks per SM x SMs) or one block per tile.
+// Block b starts with tile b and claims each further tile from the launch's
+// counter at the start of its current tile; when the claimed tile is on the
+// same mesh and loads by TMA, its h halo is requested as soon as the current
+// tile has formed rho.  Launches of whole step pairs are captured in a CUDA
+// graph.  An autotuner picks the grid and the tile order by timing real
+// steps (all candidates compute identical values, so tuning steps are
+// ordinary steps of the runs).
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -28,9 +30,10 @@ struct TileRef {
 
 template <typename T>
 struct BatchMesh {
-    LatArgs<T> a;  // fin / fout / mom are set per launch from f[], c0
+    LatArgs<T> a;  // fin / fout / mom / tmap are set per launch from f[], c0
     T *f[2];
     T *mom;
+    const TMap *tmap;  // the state's 2 x 3 tensor maps, or nullptr
     int32_t c0;
 };
 
@@ -39,39 +42,10 @@ struct BatchArgs {
     const BatchMesh<T> *meshes;
     const TileRef *tiles;
     int32_t ntiles;
-    unsigned *bar;  // [0] arrival count, [1] generation
-    int *err;
+    unsigned *ctr;  // 2 tile counters, by parity
     int parity;
     int write_mom;
 };
-
-// Grid-wide barrier for a cooperative launch.  The spin is bounded
-// (2^26 polls of ~64 ns); on giving up it records bit 2 in *err and returns.
-__device__ __forceinline__ void grid_barrier(unsigned *bar, int *err) {
-    __syncthreads();
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-        volatile unsigned *gen = bar + 1;
-        const unsigned g = *gen;
-        __threadfence();
-        const unsigned nb = gridDim.x * gridDim.y;
-        if (atomicAdd(bar, 1u) == nb - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            unsigned spins = 0;
-            while (*gen == g) {
-                if (++spins > (1u << 26)) {
-                    atomicOr(err, 2);
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-}
 
 template <typename T>
 __device__ __forceinline__ void load_mesh(const BatchArgs<T> &B, int m, LatArgs<T> &sA, int &cur) {
@@ -88,27 +62,44 @@ __device__ __forceinline__ void load_mesh(const BatchArgs<T> &B, int m, LatArgs<
         sA.fin = bm.f[c];
         sA.fout = bm.f[c ^ 1];
         sA.mom = B.write_mom ? bm.mom : nullptr;
+        sA.tmap = bm.tmap ? bm.tmap + 3 * c : nullptr;
     }
     __syncthreads();
     cur = m;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kLTX *kLTY, 3) k_batch_step(BatchArgs<T> B) {
+__global__ void __launch_bounds__(kNT, (sizeof(T) == 4 ? 768 : 512) / kNT) k_batch_step(BatchArgs<T> B) {
     __shared__ StepSmem<T> S;
     __shared__ __align__(16) LatArgs<T> sA;
-    extern __shared__ __align__(16) unsigned char bdsm[];
+    extern __shared__ __align__(128) unsigned char bdsm[];
+    const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
+    if (lead && blockIdx.x == 0) B.ctr[B.parity ^ 1] = 0u;
+    if ((int)blockIdx.x >= B.ntiles) return;
+    lat_block_init<T>(S);
+    TilePipe pp;
     int cur = -1;
-    for (int t = blockIdx.x; t < B.ntiles; t += gridDim.x) {
+    // block b starts with tile b and claims the following ones from
+    // ctr[parity]; a claimed tile's h group is requested early only when it
+    // is on the same mesh
+    int t = blockIdx.x;
+    for (;;) {
         const TileRef r = B.tiles[t];
         load_mesh<T>(B, r.mesh, sA, cur);
-        lat_rho_tile<T>(sA, r.bx, r.by, reinterpret_cast<V2<T> *>(bdsm));
-    }
-    grid_barrier(B.bar, B.err);
-    for (int t = blockIdx.x; t < B.ntiles; t += gridDim.x) {
-        const TileRef r = B.tiles[t];
-        load_mesh<T>(B, r.mesh, sA, cur);
-        lat_step_tile<T>(sA, r.bx, r.by, S, bdsm);
+        NextTile next{0, 0, 0, false, false};
+        if (lead) {
+            next.t = (int)gridDim.x + (int)atomicAdd(&B.ctr[B.parity], 1u);
+            next.valid = next.t < B.ntiles;
+            if (next.valid) {
+                const TileRef rn = B.tiles[next.t];
+                next.bx = rn.bx;
+                next.by = rn.by;
+                next.tma = rn.mesh == r.mesh && tile_tma(sA, rn.bx, rn.by, bdsm);
+            }
+        }
+        if (!lat_tile<T>(sA, r.bx, r.by, S, bdsm, pp, next)) return;
+        if (!take_next(S, pp)) return;
+        t = S.nt[0];
     }
 }
 
@@ -162,12 +153,11 @@ struct felbm_batch {
     cudaStream_t stream = nullptr;
     void *d_meshes = nullptr;
     TileRef *d_tiles = nullptr;
+    unsigned *d_ctr = nullptr;  // tile counters of the launches, by parity
     int32_t ntiles = 0;
-    unsigned *d_bar = nullptr;
-    int *d_err = nullptr;
     int parity = 0;
     int sm_count = 0, max_bps = 1;
-    int bps = 1, order = 0;  // chosen configuration
+    int bps = 1, order = 0;  // chosen configuration (bps 0: one block per tile)
     bool autotune = false, tuned = false;
     double tuned_ms = 0.0;
     cudaGraphExec_t graph = nullptr;
@@ -187,10 +177,7 @@ static int b_status(cudaError_t e) {
 }
 
 static size_t batch_smem(int esize) {
-    // the density pass reuses the step pass's dynamic shared memory
-    static_assert(lat_rho_smem<float>() <= lat_step_smem<float>(), "smem");
-    static_assert(lat_rho_smem<double>() <= lat_step_smem<double>(), "smem");
-    return esize == 8 ? lat_step_smem<double>() : lat_step_smem<float>();
+    return esize == 8 ? lat_smem<double>() : lat_smem<float>();
 }
 
 template <typename T>
@@ -199,22 +186,13 @@ static cudaError_t batch_launch(felbm_batch *b, int parity, int write_mom) {
     B.meshes = reinterpret_cast<const BatchMesh<T> *>(b->d_meshes);
     B.tiles = b->d_tiles;
     B.ntiles = b->ntiles;
-    B.bar = b->d_bar;
-    B.err = b->d_err;
+    B.ctr = b->d_ctr;
     B.parity = parity;
     B.write_mom = write_mom;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(b->bps * b->sm_count));
-    cfg.blockDim = dim3(kLTX, kLTY);
-    cfg.dynamicSmemBytes = batch_smem(sizeof(T));
-    cfg.stream = b->stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    const unsigned grid = b->bps > 0 ? (unsigned)(b->bps * b->sm_count) : (unsigned)b->ntiles;
     b->launches++;
-    return cudaLaunchKernelEx(&cfg, k_batch_step<T>, B);
+    k_batch_step<T><<<grid, dim3(kLTX, kLTY), batch_smem(sizeof(T)), b->stream>>>(B);
+    return cudaGetLastError();
 }
 
 static cudaError_t launch_any(felbm_batch *b, int parity, int write_mom) {
@@ -275,6 +253,7 @@ static int setup_meshes(felbm_batch *b) {
         bm.f[0] = reinterpret_cast<T *>(s->f[0]);
         bm.f[1] = reinterpret_cast<T *>(s->f[1]);
         bm.mom = reinterpret_cast<T *>(s->mom);
+        bm.tmap = s->d_tmap;
         bm.c0 = s->cur;
         b->c0[k] = s->cur;
     }
@@ -370,10 +349,8 @@ int felbm_batch_create(felbm_state *const *states, int32_t n_states, uint32_t fl
                                                                 : sizeof(BatchMesh<float>));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_meshes, mesh_bytes);
     if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_tiles, (size_t)b->ntiles * sizeof(TileRef));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_bar, 2 * sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_err, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(b->d_bar, 0, 2 * sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMemset(b->d_err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_ctr, 2 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(b->d_ctr, 0, 2 * sizeof(unsigned));
     int st = b_status(e);
     if (st == FELBM_OK) st = b->esize == 8 ? occupancy<double>(b) : occupancy<float>(b);
     if (st == FELBM_OK) {
@@ -390,8 +367,8 @@ int felbm_batch_create(felbm_state *const *states, int32_t n_states, uint32_t fl
     return FELBM_OK;
 }
 
-// Time `trial` direct steps under each candidate (blocks per SM x tile
-// order) and keep the fastest.  Steps taken here are ordinary steps.
+// Time `trial` direct steps under each candidate (blocks per SM, or one
+// block per tile, x tile order) and keep the fastest.  Steps taken here are ordinary steps.
 static int autotune(felbm_batch *b, int trial, int64_t *used) {
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return FELBM_ERR_CUDA;
@@ -405,7 +382,7 @@ static int autotune(felbm_batch *b, int trial, int64_t *used) {
     for (int order = 0; order < 2 && st == FELBM_OK; ++order) {
         b->order = order;
         st = b_status(upload_tiles(b));
-        for (int bps = 1; bps <= b->max_bps && st == FELBM_OK; ++bps) {
+        for (int bps = 0; bps <= b->max_bps && st == FELBM_OK; ++bps) {
             b->bps = bps;
             // one untimed step, then `trial` timed steps
             cudaError_t e = launch_any(b, b->parity, 0);
@@ -448,7 +425,7 @@ int felbm_batch_step(felbm_batch *b, int64_t n_steps) {
     cudaError_t e = cudaSuccess;
     if (b->autotune && !b->tuned) {
         const int trial = 3;
-        const int64_t need = 2LL * b->max_bps * (trial + 1) + 1;
+        const int64_t need = 2LL * (b->max_bps + 1) * (trial + 1) + 1;
         if (left > need) {
             int64_t used = 0;
             int st = autotune(b, trial, &used);
@@ -501,11 +478,8 @@ int felbm_batch_step(felbm_batch *b, int64_t n_steps) {
 
 int felbm_batch_sync(felbm_batch *b) {
     if (!b) return FELBM_ERR_INVALID_ARG;
-    int herr = 0;
-    cudaError_t e = cudaMemcpyAsync(&herr, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    const cudaError_t e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return b_status(e);
-    if (herr & 2) return FELBM_ERR_TIMEOUT;
     for (felbm_state *s : b->states) {
         const int st = felbm_state_sync(s);
         if (st != FELBM_OK) return st;
@@ -530,8 +504,7 @@ void felbm_batch_destroy(felbm_batch *b) {
     drop_graph(b);
     cudaFree(b->d_meshes);
     cudaFree(b->d_tiles);
-    cudaFree(b->d_bar);
-    cudaFree(b->d_err);
+    cudaFree(b->d_ctr);
     delete b;
 }
 

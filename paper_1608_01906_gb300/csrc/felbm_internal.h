@@ -169,6 +169,13 @@ struct Fields {
 
 // ---- opaque handles ---------------------------------------------------------
 
+// Opaque storage of one TMA tensor map (CUtensorMap: 128 bytes, 64-byte
+// aligned), encoded on the host and read by cp.async.bulk.tensor from
+// global memory.
+struct alignas(64) TMap {
+    unsigned char bytes[128];
+};
+
 struct felbm_mesh {
     int64_t n_nodes = 0, n_tri = 0;
     uint32_t flags = 0;
@@ -195,7 +202,8 @@ struct felbm_state {
     void *scratch = nullptr;          // 6 N: rho, drx, dry, mu, kx, ky
     void *mom = nullptr;              // 4 N: rho, ux, uy, p (internal order)
     double *d_out = nullptr;          // 5 N staging in caller order + reduction partials
-    int *d_flag = nullptr;
+    int *d_flag = nullptr;            // bit 0: non-finite field, bit 2: bounded wait gave up
+    TMap *d_tmap = nullptr;           // structured meshes: 2 buffers x {h pairs, h rest, g pairs}
     bool have_moments = false;
     int64_t steps_done = 0;
     // profiling: event pairs around launches (felbm_profile_enable)
@@ -210,5 +218,8 @@ namespace felbm {
 // Record the launch of a kernel of the given kind; when profiling, the
 // returned event index brackets it (-1: not timed).
 int prof_begin(felbm_state *s, int kind);
+// Encode and upload the tensor maps of a state on a structured mesh
+// (felbm_tmap.cu); leaves d_tmap null where TMA is not usable.
+void lattice_tmaps(felbm_state *s);
 void prof_end(felbm_state *s, int slot);
 }  // namespace felbm

@@ -1,22 +1,24 @@
-// Structured-lattice step: two launches per time step.
+// Structured-lattice step: one launch per time step, one 32 x 8 tile of
+// nodes per block (k_lat_step).
 //
-//   k_lat_rho   Taylor-Galerkin streaming of the 9 h populations (Sec. 2.2.1)
-//               with per-state constant coefficient tables, wall bounce-back,
-//               rho = sum_a h_a.
-//   k_lat_step  one 32 x 8 tile per block: rho with a depth-3 halo is staged in
-//               shared memory; grad rho (depth 2), lap rho and mu (depth 1),
-//               then grad mu and the stress force at the tile's nodes are all
-//               recomputed there (Sec. 2.3 recovery, Sec. 2.1 mu, stress form);
-//               the populations are streamed from shared-memory halo tiles,
-//               bounced back at walls, and collided (Sec. 2.2); one write of
-//               the 18 populations.
+//   1. the 4 h pair tiles (halo depth 4) and the h rest tile are staged in
+//      shared memory; the h populations are streamed (Taylor-Galerkin,
+//      Sec. 2.2.1) and bounced back at walls on the tile's depth-3 halo, and
+//      rho = sum_a h_a there; the tile's own streamed h pairs are kept;
+//   2. grad rho (depth 2), lap rho and mu (depth 1), then grad mu and the
+//      stress force at the tile's nodes (Sec. 2.3 recovery, Sec. 2.1 mu,
+//      stress form);
+//   3. the g pairs are streamed from depth-1 tiles, the moments formed and
+//      all populations collided (Sec. 2.2); one write of the 18 populations.
 //
+// The density stage recomputes the streaming of h on the halo instead of a
+// separate density launch: neighbouring tiles share no data within a step.
 // Opposite directions (a, abar) are stored interleaved (pop_index): the
 // stencil of a pair reads one 8-byte (FP32) word per neighbour and runs in
 // packed two-wide arithmetic (FFMA2 on sm_103a), each lane with its own
-// coefficient.  The halo tiles of all pairs are requested with cp.async
-// (16-byte chunks away from the x wrap) when the block starts, so their
-// latency overlaps the scalar chain.
+// coefficient.  All tiles are requested with cp.async (16-byte chunks when
+// nx % 4 == 0) when the block starts; the g tiles arrive while rho and the
+// scalar chain are computed.
 //
 // Coefficient tables: for each row kind (interior, bottom wall row, top wall
 // row), offset o and pair q, the streaming coefficients of the pair's two
@@ -76,9 +78,10 @@ struct LatArgs {
     Phys<T> P;
     const T *fin;
     T *fout;
-    T *rho;
+    T *rho;  // unused by the lattice step (rho is formed per tile)
     T *mom;  // 4N or nullptr
     int *flag;
+    const TMap *tmap;  // {h pairs, h rest, g pairs} of fin, or nullptr
 };
 
 __device__ __forceinline__ int lat_kind(int walls, int y, int ny) {
@@ -159,6 +162,60 @@ __device__ __forceinline__ void cp_async_wait_group() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// ---- halo windows loaded by TMA -----------------------------------------
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// make barrier initialisation visible to the async proxy
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// Wait for the phase of the given parity to complete; each try_wait is
+// itself time-limited and the number of tries is bounded: false when the
+// bound ran out.
+constexpr unsigned kMbarTries = 1u << 20;
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+    const unsigned a = smem_u32(bar);
+    for (unsigned it = 0; it < kMbarTries; ++it) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+// order this thread's earlier generic-proxy shared accesses (as released to
+// it by a barrier) before later async-proxy writes
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const TMap *map, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];\n" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const TMap *map, int x, int y, int z, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // Request NF windows (src + f * src_stride -> dst + f * dst_stride).
 template <typename E, bool VEC, int NF>
 __device__ __forceinline__ void fill_issue(const FillPlan &f, const E *__restrict__ src, size_t src_stride,
@@ -175,51 +232,46 @@ __device__ __forceinline__ void fill_issue(const FillPlan &f, const E *__restric
     }
 }
 
-// Halo tile of one population pair: kLTY + 2 rows of W elements; rows start
-// CE = 16 / sizeof(pair) elements left of the tile (16-byte aligned chunks);
-// the stencil reads the kLTX + 2 central elements.
-template <typename T>
+// Halo tile of one population pair with D rows of halo above and below and
+// XH >= D columns left and right; XH is D rounded up to whole 16-byte chunks
+// of pairs, so rows start 16-byte aligned.
+template <typename T, int D>
 struct PairTile {
     static constexpr int CE = 16 / (int)sizeof(V2<T>);
-    static constexpr int W = kLTX + 2 * CE;
-    static constexpr int H = kLTY + 2;
+    static constexpr int XH = (D + CE - 1) / CE * CE;
+    static constexpr int W = kLTX + 2 * XH;
+    static constexpr int H = kLTY + 2 * D;
     static constexpr int N = W * H;
 };
 
-// Request the halo tiles of the 4 pairs of h (G = 0) or g (G = 1).
-template <typename T, int G, bool INTERIOR = false>
+// Request the depth-D halo tiles of the 4 pairs of h (G = 0) or g (G = 1).
+// VEC: 16-byte chunks (needs nx % 4 == 0, so no chunk straddles the x wrap).
+template <typename T, int G, int D, bool VEC>
 __device__ __forceinline__ void issue_pair_tiles(const LatArgs<T> &A, int tid, int x0, int y0,
-                                                 V2<T> *tiles, size_t n) {
+                                                 V2<T> *tiles, size_t np) {
     using E = V2<T>;
-    constexpr int CE = PairTile<T>::CE, W = PairTile<T>::W, H = PairTile<T>::H;
-    const int nx = A.nx, ny = A.ny, walls = A.walls;
-    const size_t np = pad4(n);
+    using PT = PairTile<T, D>;
     const E *src = reinterpret_cast<const E *>(A.fin + (G ? 10 : 1) * np);  // pair 0; pair q at + q np
-    if (INTERIOR || ((nx % CE) == 0 && x0 - CE >= 0 && x0 + kLTX + CE <= nx)) {
-        const FillPlan f = fill_plan<E, W, H, true>(tid, kLTX * kLTY, x0 - CE, y0 - 1, nx, ny, walls);
-        fill_issue<E, true, 4>(f, src, np, tiles, PairTile<T>::N);
-    } else {
-        const FillPlan f = fill_plan<E, W, H, false>(tid, kLTX * kLTY, x0 - CE, y0 - 1, nx, ny, walls);
-        fill_issue<E, false, 4>(f, src, np, tiles, PairTile<T>::N);
-    }
+    const FillPlan f =
+        fill_plan<E, PT::W, PT::H, VEC>(tid, kLTX * kLTY, x0 - PT::XH, y0 - D, A.nx, A.ny, A.walls);
+    fill_issue<E, VEC, 4>(f, src, np, tiles, PT::N);
 }
 
-// Streamed values of pair q of the node at (lx, ly) of the block's tile:
+// Streamed values of pair q of the node whose element in the halo tile buf
+// (rows of W elements) is c, at row kind k:
 // psi* = psi - dt sum_o s_o (psi(node + o) - psi(node)), both directions in
-// one packed operation per step; row kind 0 is compile-time on interior
-// tiles.
-template <typename T>
-__device__ __forceinline__ V2<T> streamed2(const LatCoef<T> &c, int k, bool interior, int q,
-                                           const V2<T> *buf, int lx, int ly, T dt) {
-    constexpr int W = PairTile<T>::W, CE = PairTile<T>::CE;
-    const V2<T> self = buf[(ly + 1) * W + lx + CE];
+// one packed operation per offset.
+template <typename T, int W>
+__device__ __forceinline__ V2<T> stream_pair(const LatCoef<T> &cf, int k, int q, const V2<T> *buf, int c,
+                                             T dt) {
+    const V2<T> self = buf[c];
     const V2<T> m1 = vset(T(-1), T(-1));
     V2<T> acc = vset(T(0), T(0));
 #pragma unroll
     for (int o = 0; o < 6; ++o) {
-        const V2<T> nb = buf[(ly + 1 + lat_dy(o)) * W + lx + CE + lat_dx(o)];
+        const V2<T> nb = buf[c + lat_dy(o) * W + lat_dx(o)];
         const V2<T> d = vfma(self, m1, nb);  // nb - self, exact negation
-        acc = vfma(interior ? c.s[0][o][q] : c.s[k][o][q], d, acc);
+        acc = vfma(cf.s[k][o][q], d, acc);
     }
     return vfma(vset(-dt, -dt), acc, self);
 }
@@ -260,17 +312,6 @@ __device__ __forceinline__ void collide_pair(const CollidePrep<T> &c, V2<T> hs, 
     go = vadd(gs, vfma(vset(c.omw, c.omw), dg, vmul(vset(c.opw, c.opw), Sg)));
 }
 
-// Weight of streamed h_a in rho at a wall row of kind k (bounce-back replaces
-// each population entering the fluid by its opposite).
-__device__ __forceinline__ int bb_mult(int k, int a) {
-    if (!k) return 1;
-    const int nk = k == 1 ? 2 : 4;
-    const int in_a = kEx(a) * kEx(nk) + kEy(a) * kEy(nk) > 0;
-    const int ao = kOpp(a);
-    const int in_opp = kEx(ao) * kEx(nk) + kEy(ao) * kEy(nk) > 0;
-    return in_a ? 0 : (in_opp ? 2 : 1);
-}
-
 // Bounce-back of a pair at a wall row of kind k (1: inward normal +y, the
 // slot-0 directions 2, 5, 6 of pairs 1..3 take their opposites; 2: normal
 // -y, the slot-1 directions 4, 7, 8 take theirs).
@@ -280,112 +321,84 @@ __device__ __forceinline__ V2<T> bounce_pair(int k, int q, V2<T> v) {
     return k == 1 ? vset(v.y, v.y) : vset(v.x, v.x);
 }
 
-// ---- density pass -------------------------------------------------------
+// ---- one step of a tile ---------------------------------------------------
 
-template <typename T>
-constexpr size_t lat_rho_smem() {
-    return 4 * (size_t)PairTile<T>::N * sizeof(V2<T>);
-}
+constexpr int kHD = 4;                            // depth of the h pair tiles
+constexpr int kH0W = kLTX + 8, kH0H = kLTY + 6;   // h rest tile: from (x0 - 4, y0 - 3)
+constexpr int kQW = kLTX + 6, kQH = kLTY + 6;     // rho region: halo 3
+constexpr int kRW = kLTX + 8, kRH = kLTY + 6;     // rho: rows from x0 - 4 (column 0, 39 unused)
+constexpr int kGW = kLTX + 4, kGH = kLTY + 4;     // grad rho: halo 2
+constexpr int kMW = kLTX + 2, kMH = kLTY + 2;     // mu: halo 1
+constexpr int kNT = kLTX * kLTY;
 
-// Whether every node and halo of tile (x0, y0) is an interior-row node away
-// from the x wrap, with 16-byte aligned rows: such tiles run with the row
-// kind fixed at compile time and vector fills only.
-template <typename T>
-__device__ __forceinline__ bool tile_interior(int x0, int y0, int nx, int ny, int walls) {
-    const bool yin = !walls || (y0 > 0 && y0 + kLTY < ny);
-    const bool xin = (nx % 4) == 0 && x0 - 4 >= 0 && x0 + kLTX + 4 <= nx;
-    return yin && xin;
-}
-
-// Density pass of tile (bx, by); tiles: shared memory of lat_rho_smem bytes.
-template <typename T, bool INTERIOR>
-__device__ __forceinline__ void lat_rho_tile_impl(const LatArgs<T> &A, int bx, int by, V2<T> *tiles) {
-    const int x0 = bx * kLTX, y0 = by * kLTY;
-    const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * kLTX + lx;
-    const int x = x0 + lx, y = y0 + ly;
-    const bool valid = x < A.nx && y < A.ny;
-    const size_t n = (size_t)A.nx * A.ny;
-    issue_pair_tiles<T, 0, INTERIOR>(A, tid, x0, y0, tiles, n);
-    cp_async_commit();
-    const int k = (INTERIOR || !valid) ? 0 : lat_kind(A.walls, y, A.ny);
-    const bool interior = INTERIOR || !A.walls || (y0 > 0 && y0 + kLTY < A.ny);
-    const int32_t i = x + A.nx * y;
-    T r = valid ? __ldg(A.fin + i) : T(0);  // rest population is not moved
-    cp_async_wait_group<0>();
-    __syncthreads();
-    if (valid) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const V2<T> v = streamed2<T>(A.c, k, interior, q, tiles + q * PairTile<T>::N, lx, ly, A.P.dt);
-            if (!INTERIOR && k)
-                r += T(bb_mult(k, pair_dir(q, 0))) * v.x + T(bb_mult(k, pair_dir(q, 1))) * v.y;
-            else
-                r += v.x + v.y;
-        }
-        A.rho[i] = r;
-    }
-    __syncthreads();  // the caller may reuse the tiles for the next tile
-}
-
-template <typename T>
-__device__ __forceinline__ void lat_rho_tile(const LatArgs<T> &A, int bx, int by, V2<T> *tiles) {
-    if (tile_interior<T>(bx * kLTX, by * kLTY, A.nx, A.ny, A.walls))
-        lat_rho_tile_impl<T, true>(A, bx, by, tiles);
-    else
-        lat_rho_tile_impl<T, false>(A, bx, by, tiles);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kLTX *kLTY, 6) k_lat_rho(LatArgs<T> A) {
-    __shared__ __align__(16) V2<T> tiles[4 * PairTile<T>::N];
-    lat_rho_tile<T>(A, blockIdx.x, blockIdx.y, tiles);
-}
-
-// ---- step pass ----------------------------------------------------------
-
-constexpr int kRW = kLTX + 8, kRH = kLTY + 6;  // rho: halo 3, rows from x0 - 4 (16-byte aligned)
-constexpr int kGW = kLTX + 4, kGH = kLTY + 4;  // grad rho: halo 2
-constexpr int kMW = kLTX + 2, kMH = kLTY + 2;  // mu: halo 1
-
-// Shared memory of one step tile: the scalar chain (static) and, in the
-// dynamic part (lat_step_smem bytes), the 8 pair halo tiles then the 8 rows
-// of streamed pairs.
+// Shared memory of one tile: the scalar chain (static) and the population
+// tiles (dynamic, lat_smem bytes).  The streamed g pairs stay in registers.
 template <typename T>
 struct __align__(16) StepSmem {
+    uint64_t bar[2];  // TMA completion: h tiles, g tiles
+    int nt[4];        // the block's next tile as claimed by thread 0: index, bx, by, flags
     T s_rho[kRH][kRW];
     T s_gx[kGH][kGW], s_gy[kGH][kGW];
     T s_mu[kMH][kMW];
 };
 
+constexpr size_t align128(size_t b) { return (b + 127) / 128 * 128; }
+
+// Regions of the dynamic shared memory, each 128-byte aligned (TMA
+// destinations).  The byte sizes of the h tiles (pairs + rest) and of the g
+// tiles are what one TMA load group delivers.
 template <typename T>
-constexpr size_t lat_step_smem() {
-    return (8 * (size_t)PairTile<T>::N + 8 * (size_t)kLTX * kLTY) * sizeof(V2<T>);
+struct LatSmem {
+    using PH = PairTile<T, kHD>;
+    using PG = PairTile<T, 1>;
+    static constexpr unsigned hT_bytes = 4 * PH::N * sizeof(V2<T>);
+    static constexpr unsigned h0_bytes = kH0W * kH0H * sizeof(T);
+    static constexpr unsigned gT_bytes = 4 * PG::N * sizeof(V2<T>);
+    static constexpr size_t hT = 0;                             // 4 h pair tiles
+    static constexpr size_t h0 = align128(hT + hT_bytes);      // h rest tile
+    static constexpr size_t gT = align128(h0 + h0_bytes);      // 4 g pair tiles
+    static constexpr size_t psi = align128(gT + gT_bytes);     // streamed h pairs
+    static constexpr size_t bytes = psi + 4 * (size_t)kNT * sizeof(V2<T>);
+};
+
+template <typename T>
+constexpr size_t lat_smem() {
+    return LatSmem<T>::bytes;
 }
 
-// Streaming from the pair tiles, bounce-back, collision and the write of one
-// node of a step tile.
+// Whether tile (x0, y0) is whole (no node outside the mesh), its rho region
+// and h tiles hold no wall row nor a row outside a walled domain, and rows
+// are 16-byte aligned: such tiles run with the row kind fixed at compile
+// time and vector fills only.
+__device__ __forceinline__ bool tile_interior(int x0, int y0, int nx, int ny, int walls) {
+    const bool yin = walls ? (y0 >= kHD && y0 + kLTY + kHD <= ny) : (y0 + kLTY <= ny);
+    return yin && (nx % 4) == 0 && x0 + kLTX <= nx;
+}
+
+// Whether the halo windows of tile (x0, y0) lie inside the mesh without a
+// periodic wrap: a TMA box then covers each of them.
+__device__ __forceinline__ bool tile_unwrapped(int x0, int y0, int nx, int ny) {
+    return x0 >= kHD && x0 + kLTX + kHD <= nx && y0 >= kHD && y0 + kLTY + kHD <= ny;
+}
+
+// Collision of one node: the g pairs are streamed here from their depth-1
+// tiles, the h pairs were streamed by the density stage.
 template <typename T>
-__device__ __forceinline__ void lat_step_node(const LatArgs<T> &A, int k, bool interior, int lx, int ly,
-                                              int tid, int32_t i, size_t n, T r0, T drx, T dry,
-                                              T dmx, T dmy, T kx, T ky, const V2<T> *tiles,
-                                              V2<T> (*s_psi)[kLTX * kLTY]) {
+__device__ __forceinline__ void lat_node(const LatArgs<T> &A, int k, int lx, int ly, int tid, int32_t i,
+                                         size_t n, T h0, T r0, T drx, T dry, T dmx, T dmy, T kx, T ky,
+                                         const V2<T> *gT, const V2<T> (*s_psi)[kNT]) {
+    using PG = PairTile<T, 1>;
     const Phys<T> &P = A.P;
     const size_t np = pad4(n);
-    const T dt = P.dt;
-    const T h0 = __ldg(A.fin + i), g0 = __ldg(A.fin + 9 * np + i);
-    // streamed pairs (bounced back at wall rows) go to shared memory: keeps
-    // them out of registers
+    const T g0 = __ldg(A.fin + 9 * np + i);
+    const int c = (ly + 1) * PG::W + lx + PG::XH;
+    V2<T> gq[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        s_psi[q][tid] = bounce_pair<T>(k, q, streamed2<T>(A.c, k, interior, q,
-                                                          tiles + q * PairTile<T>::N, lx, ly, dt));
-        s_psi[4 + q][tid] = bounce_pair<T>(k, q, streamed2<T>(A.c, k, interior, q,
-                                                              tiles + (4 + q) * PairTile<T>::N, lx, ly, dt));
-    }
-    const V2<T> gq0 = s_psi[4][tid], gq1 = s_psi[5][tid], gq2 = s_psi[6][tid], gq3 = s_psi[7][tid];
+    for (int q = 0; q < 4; ++q)
+        gq[q] = bounce_pair<T>(k, q, stream_pair<T, PG::W>(A.c, k, q, gT + q * PG::N, c, P.dt));
     T sg, mx, my;
     // g_1 = q0.x, g_3 = q0.y, g_2 = q1.x, g_4 = q1.y, g_5 = q2.x, g_7 = q2.y, g_6 = q3.x, g_8 = q3.y
-    g_moments<T>(g0, gq0.x, gq1.x, gq0.y, gq1.y, gq2.x, gq3.x, gq2.y, gq3.y, sg, mx, my);
+    g_moments<T>(g0, gq[0].x, gq[1].x, gq[0].y, gq[1].y, gq[2].x, gq[3].x, gq[2].y, gq[3].y, sg, mx, my);
     const CollidePrep<T> cp = collide_prep<T>(P, sg, mx, my, r0, drx, dry, dmx, dmy, kx, ky);
     const T r = cp.r, ux = cp.ux, uy = cp.uy, p = cp.p;
     // pairs, then the rest population, which also takes the sum of the h
@@ -397,9 +410,9 @@ __device__ __forceinline__ void lat_step_node(const LatArgs<T> &A, int k, bool i
     V2<T> *gout = reinterpret_cast<V2<T> *>(A.fout + 10 * np);
     auto pair_update = [&](auto qc) {
         constexpr int q = decltype(qc)::value;
-        const V2<T> hs = s_psi[q][tid], gs = s_psi[4 + q][tid];
+        const V2<T> hs = s_psi[q][tid];
         V2<T> ho, go;
-        collide_pair<T, q>(cp, hs, gs, ho, go);
+        collide_pair<T, q>(cp, hs, gq[q], ho, go);
         dsum += (ho.x - hs.x) + (ho.y - hs.y);
         hout[(size_t)q * np + i] = ho;
         gout[(size_t)q * np + i] = go;
@@ -424,48 +437,152 @@ __device__ __forceinline__ void lat_step_node(const LatArgs<T> &A, int k, bool i
     }
 }
 
-// Step pass of tile (bx, by).
-template <typename T, bool INTERIOR>
-__device__ __forceinline__ void lat_step_tile_impl(const LatArgs<T> &A, int bx, int by, StepSmem<T> &S,
-                                                   unsigned char *lat_dsm) {
-    constexpr int RW = kRW, RH = kRH, GW = kGW, GH = kGH, MW = kMW, MH = kMH;
+// TMA state of a block walking its tiles (same value in every thread).
+struct TilePipe {
+    unsigned ph[2] = {0u, 0u};  // parity of the next phase of bar[0] (h group), bar[1] (g group)
+    bool h_issued = false;      // the current tile's h group was requested during the previous tile
+};
+
+// The block's next tile (known to thread 0 only): its h group is requested
+// as soon as the current tile has formed rho (tma: it loads by TMA, from
+// the same mesh).  Thread 0 publishes it in S.nt (flags: bit 0 valid, bit 1
+// h group requested) for the whole block after the tile.
+struct NextTile {
+    int t, bx, by;
+    bool valid, tma;
+};
+
+// Request the h group (4 h pair tiles + the rest tile) of tile (x0, y0).
+template <typename T>
+__device__ __forceinline__ void issue_h_group(const LatArgs<T> &A, int x0, int y0, StepSmem<T> &S,
+                                              unsigned char *dsm) {
+    using L = LatSmem<T>;
+    using PH = PairTile<T, kHD>;
+    constexpr int WPN = (int)sizeof(V2<T>) / 4, SPN = (int)sizeof(T) / 4;  // 4-byte words per element
+    fence_proxy_async();
+    mbar_expect_tx(&S.bar[0], L::hT_bytes + L::h0_bytes);
+    tma_load_3d(dsm + L::hT, A.tmap + 0, (x0 - PH::XH) * WPN, y0 - kHD, 0, &S.bar[0]);
+    tma_load_2d(dsm + L::h0, A.tmap + 1, (x0 - 4) * SPN, y0 - 3, &S.bar[0]);
+}
+
+// Request the g group (4 g pair tiles) of tile (x0, y0).
+template <typename T>
+__device__ __forceinline__ void issue_g_group(const LatArgs<T> &A, int x0, int y0, StepSmem<T> &S,
+                                              unsigned char *dsm) {
+    using L = LatSmem<T>;
+    using PG = PairTile<T, 1>;
+    constexpr int WPN = (int)sizeof(V2<T>) / 4;
+    fence_proxy_async();
+    mbar_expect_tx(&S.bar[1], L::gT_bytes);
+    tma_load_3d(dsm + L::gT, A.tmap + 2, (x0 - PG::XH) * WPN, y0 - 1, 0, &S.bar[1]);
+}
+
+// A bounded wait for a TMA load ran out: record it, give the loads still in
+// flight one more bounded wait each, and stop (all threads alike).
+template <typename T>
+__device__ __noinline__ bool tma_gave_up(const LatArgs<T> &A, StepSmem<T> &S, const TilePipe &pp) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        atomicOr(A.flag, 4);
+        mbar_wait(&S.bar[0], pp.ph[0]);
+        mbar_wait(&S.bar[1], pp.ph[1]);
+    }
+    __syncthreads();
+    return false;
+}
+
+// One time step of tile (bx, by).  TMA: the halo windows come as TMA boxes
+// (tile_unwrapped, interior tiles) completing on S.bar, else as cp.async
+// fills.  Returns false (all threads alike) when a bounded wait for a TMA
+// load gave up; the flag then carries bit 2.
+template <typename T, bool INTERIOR, bool TMA>
+__device__ __forceinline__ bool lat_tile_impl(const LatArgs<T> &A, int bx, int by, StepSmem<T> &S,
+                                              unsigned char *dsm, TilePipe &pp, const NextTile &next) {
+    using L = LatSmem<T>;
+    using PH = PairTile<T, kHD>;
     auto &s_rho = S.s_rho;
     auto &s_gx = S.s_gx;
     auto &s_gy = S.s_gy;
     auto &s_mu = S.s_mu;
-    V2<T> *tiles = reinterpret_cast<V2<T> *>(lat_dsm);
-    V2<T>(*s_psi)[kLTX * kLTY] =
-        reinterpret_cast<V2<T>(*)[kLTX * kLTY]>(lat_dsm + 8 * PairTile<T>::N * sizeof(V2<T>));
+    V2<T> *hT = reinterpret_cast<V2<T> *>(dsm + L::hT);
+    T(*s_h0)[kH0W] = reinterpret_cast<T(*)[kH0W]>(dsm + L::h0);
+    V2<T> *gT = reinterpret_cast<V2<T> *>(dsm + L::gT);
+    V2<T>(*s_psi)[kNT] = reinterpret_cast<V2<T>(*)[kNT]>(dsm + L::psi);
     const int nx = A.nx, ny = A.ny, walls = A.walls;
     const int x0 = bx * kLTX, y0 = by * kLTY;
     const int tid = threadIdx.y * kLTX + threadIdx.x;
-    constexpr int NT = kLTX * kLTY;
-    const size_t n = (size_t)nx * ny;
-    // 0. request rho with a depth-3 halo (group 1), then the halo tiles of the
-    //    8 pairs (group 2); the populations arrive while the scalar chain is
-    //    computed
-    {
-        constexpr int CE = 16 / (int)sizeof(T);
-        if (INTERIOR || ((nx % CE) == 0 && x0 - 4 >= 0 && x0 + kLTX + 4 <= nx)) {
-            const FillPlan fr = fill_plan<T, RW, RH, true>(tid, NT, x0 - 4, y0 - 3, nx, ny, walls);
-            fill_issue<T, true, 1>(fr, A.rho, 0, &s_rho[0][0], 0);
-        } else {
-            const FillPlan fr = fill_plan<T, RW, RH, false>(tid, NT, x0 - 4, y0 - 3, nx, ny, walls);
-            fill_issue<T, false, 1>(fr, A.rho, 0, &s_rho[0][0], 0);
+    const size_t n = (size_t)nx * ny, np = pad4(n);
+    const T dt = A.P.dt;
+    // 0. request the h pair tiles (depth 4) and the h rest tile (depth 3) as
+    //    group 1, the g pair tiles (depth 1) as group 2; the g tiles arrive
+    //    while rho and the scalar chain are computed
+    if (TMA) {
+        if (tid == 0) {
+            if (!pp.h_issued) issue_h_group<T>(A, x0, y0, S, dsm);
+            issue_g_group<T>(A, x0, y0, S, dsm);
         }
+    } else if (INTERIOR || (nx % 4) == 0) {
+        issue_pair_tiles<T, 0, kHD, true>(A, tid, x0, y0, hT, np);
+        fill_issue<T, true, 1>(fill_plan<T, kH0W, kH0H, true>(tid, kNT, x0 - 4, y0 - 3, nx, ny, walls),
+                               A.fin, 0, &s_h0[0][0], 0);
         cp_async_commit();
+        issue_pair_tiles<T, 1, 1, true>(A, tid, x0, y0, gT, np);
+    } else {
+        issue_pair_tiles<T, 0, kHD, false>(A, tid, x0, y0, hT, np);
+        fill_issue<T, false, 1>(fill_plan<T, kH0W, kH0H, false>(tid, kNT, x0 - 4, y0 - 3, nx, ny, walls),
+                                A.fin, 0, &s_h0[0][0], 0);
+        cp_async_commit();
+        issue_pair_tiles<T, 1, 1, false>(A, tid, x0, y0, gT, np);
     }
-    issue_pair_tiles<T, 0, INTERIOR>(A, tid, x0, y0, tiles, n);
-    issue_pair_tiles<T, 1, INTERIOR>(A, tid, x0, y0, tiles + 4 * PairTile<T>::N, n);
-    cp_async_commit();
-    const auto &rc = A.c.r;  // recovery coefficients
-    // 1. rho (s_rho[r][c] = global (x0 - 4 + c, y0 - 3 + r); zero outside a
-    //    walled domain, where only zero coefficients meet it)
-    cp_async_wait_group<1>();
+    if (!TMA) cp_async_commit();
+    // rows of the rho region (y0 - 3 .. y0 + 10) all of kind 0 and inside
+    const bool rows_in = INTERIOR || !walls || (y0 >= kHD && y0 + kLTY + kHD <= ny);
+    if (TMA) {
+        if (__syncthreads_or(!mbar_wait(&S.bar[0], pp.ph[0]))) return tma_gave_up(A, S, pp);
+        pp.ph[0] ^= 1u;
+    } else {
+        cp_async_wait_group<1>();
+        __syncthreads();
+    }
+    // the node's own rest population, read before the h tiles are reused
+    const T h0 = s_h0[threadIdx.y + 3][threadIdx.x + 4];
+    // 1. rho = sum of the streamed, bounced-back h on the depth-3 region
+    //    (s_rho[r][c] = global (x0 - 4 + c, y0 - 3 + r); zero outside a walled
+    //    domain, where only zero coefficients meet it); the tile's own
+    //    streamed h pairs are kept for the collision
+    for (int q = tid; q < kQW * kQH; q += kNT) {
+        const int ry = q / kQW, rx = q - ry * kQW;
+        const int gy = y0 + ry - 3;
+        T r = T(0);
+        if (rows_in || (gy >= 0 && gy < ny)) {
+            const int k = rows_in ? 0 : lat_kind(walls, gy, ny);
+            const int c = (ry + 1) * PH::W + rx + (PH::XH - 3);
+            const bool own = (unsigned)(rx - 3) < (unsigned)kLTX && (unsigned)(ry - 3) < (unsigned)kLTY;
+            const int o = (ry - 3) * kLTX + (rx - 3);
+            r = s_h0[ry][rx + 1];
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                const V2<T> v = bounce_pair<T>(k, p, stream_pair<T, PH::W>(A.c, k, p, hT + p * PH::N, c, dt));
+                r += v.x + v.y;
+                if (own) s_psi[p][o] = v;
+            }
+        }
+        s_rho[ry][rx + 1] = r;
+    }
     __syncthreads();
+    // the h pair tiles and the rest tile are dead (nothing below reads them):
+    // request the next tile's h group now, so that it arrives while this
+    // tile finishes
+    if (tid == 0) {
+        if (next.tma) issue_h_group<T>(A, next.bx * kLTX, next.by * kLTY, S, dsm);
+        S.nt[0] = next.t;
+        S.nt[1] = next.bx;
+        S.nt[2] = next.by;
+        S.nt[3] = (next.valid ? 1 : 0) | (next.tma ? 2 : 0);
+    }
+    const auto &rc = A.c.r;  // recovery coefficients
     // 2. recovered grad rho on the depth-2 region
-    for (int q = tid; q < GW * GH; q += NT) {
-        const int ly = q / GW, lx = q - ly * GW;
+    for (int q = tid; q < kGW * kGH; q += kNT) {
+        const int ly = q / kGW, lx = q - ly * kGW;
         const int gy = y0 + ly - 2;
         const int k = (!INTERIOR && walls && (gy == 0 || gy == ny - 1)) ? (gy == 0 ? 1 : 2) : 0;
         const T c0 = s_rho[ly + 1][lx + 2];
@@ -482,8 +599,8 @@ __device__ __forceinline__ void lat_step_tile_impl(const LatArgs<T> &A, int bx, 
     __syncthreads();
     // 3. lap rho and mu on the depth-1 region
     const Phys<T> &P = A.P;
-    for (int q = tid; q < MW * MH; q += NT) {
-        const int ly = q / MW, lx = q - ly * MW;
+    for (int q = tid; q < kMW * kMH; q += kNT) {
+        const int ly = q / kMW, lx = q - ly * kMW;
         const int gy = y0 + ly - 1;
         const int k = (!INTERIOR && walls && (gy == 0 || gy == ny - 1)) ? (gy == 0 ? 1 : 2) : 0;
         const T gxc = s_gx[ly + 1][lx + 1], gyc = s_gy[ly + 1][lx + 1];
@@ -496,13 +613,12 @@ __device__ __forceinline__ void lat_step_tile_impl(const LatArgs<T> &A, int bx, 
         s_mu[ly][lx] = mu_bulk<T>(P, s_rho[ly + 2][lx + 3]) - P.kappa * lap;
     }
     __syncthreads();
-    // 4. per node: grad mu, stress force, streaming, collision.  Threads of
-    //    a ragged tile outside the mesh take part in every barrier.
+    // 4. per node: grad mu, stress force, then the collision.  Threads of a
+    //    ragged tile outside the mesh take part in every barrier.
     const int lx = threadIdx.x, ly = threadIdx.y;
     const int x = x0 + lx, y = y0 + ly;
-    const bool valid = x < nx && y < ny;
-    const int k = (INTERIOR || !valid) ? 0 : lat_kind(walls, y, ny);
-    const bool interior = INTERIOR || !walls || (y0 > 0 && y0 + kLTY < ny);
+    const bool valid = INTERIOR || (x < nx && y < ny);
+    const int k = (rows_in || !valid) ? 0 : lat_kind(walls, y, ny);
     T dmx, dmy, kx, ky;
     {
         T smx = T(0), smy = T(0), skx = T(0), sky = T(0);
@@ -529,27 +645,71 @@ __device__ __forceinline__ void lat_step_tile_impl(const LatArgs<T> &A, int bx, 
     const T r0 = s_rho[ly + 3][lx + 4];
     const T drx = s_gx[ly + 2][lx + 2], dry = s_gy[ly + 2][lx + 2];
     const int32_t i = valid ? x + nx * y : 0;
-    cp_async_wait_group<0>();
-    __syncthreads();
-    if (valid) lat_step_node<T>(A, k, interior, lx, ly, tid, i, n, r0, drx, dry, dmx, dmy, kx, ky,
-                                tiles, s_psi);
+    if (TMA) {
+        if (__syncthreads_or(!mbar_wait(&S.bar[1], pp.ph[1]))) return tma_gave_up(A, S, pp);
+        pp.ph[1] ^= 1u;
+    } else {
+        cp_async_wait_group<0>();
+        __syncthreads();
+    }
+    if (valid)
+        lat_node<T>(A, k, lx, ly, tid, i, n, h0, r0, drx, dry, dmx, dmy, kx, ky, gT, s_psi);
     __syncthreads();  // the caller may reuse shared memory for the next tile
+    return true;
 }
 
+// Barriers of the TMA loads; once per block before its first tile.
 template <typename T>
-__device__ __forceinline__ void lat_step_tile(const LatArgs<T> &A, int bx, int by, StepSmem<T> &S,
-                                              unsigned char *lat_dsm) {
-    if (tile_interior<T>(bx * kLTX, by * kLTY, A.nx, A.ny, A.walls))
-        lat_step_tile_impl<T, true>(A, bx, by, S, lat_dsm);
-    else
-        lat_step_tile_impl<T, false>(A, bx, by, S, lat_dsm);
+__device__ __forceinline__ void lat_block_init(StepSmem<T> &S) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        mbar_init(&S.bar[0], 1);
+        mbar_init(&S.bar[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
 }
 
+// Whether tile (bx, by) loads its halo windows by TMA.
 template <typename T>
-__global__ void __launch_bounds__(kLTX *kLTY, 4) k_lat_step(LatArgs<T> A) {
+__device__ __forceinline__ bool tile_tma(const LatArgs<T> &A, int bx, int by, const unsigned char *dsm) {
+    const int x0 = bx * kLTX, y0 = by * kLTY;
+    return A.tmap && tile_interior(x0, y0, A.nx, A.ny, A.walls) && tile_unwrapped(x0, y0, A.nx, A.ny) &&
+           (smem_u32(dsm) & 127u) == 0;
+}
+
+// One tile of a block's walk (pp carries the TMA barrier phases and whether
+// this tile's h group was already requested; next is the block's next tile).
+// False when a bounded wait gave up.
+template <typename T>
+__device__ __forceinline__ bool lat_tile(const LatArgs<T> &A, int bx, int by, StepSmem<T> &S,
+                                         unsigned char *dsm, TilePipe &pp, const NextTile &next) {
+    if (tile_tma(A, bx, by, dsm)) return lat_tile_impl<T, true, true>(A, bx, by, S, dsm, pp, next);
+    if (tile_interior(bx * kLTX, by * kLTY, A.nx, A.ny, A.walls))
+        return lat_tile_impl<T, true, false>(A, bx, by, S, dsm, pp, next);
+    return lat_tile_impl<T, false, false>(A, bx, by, S, dsm, pp, next);
+}
+
+// After a tile: the published next tile (false: none), and whether its h
+// group was requested.
+template <typename T>
+__device__ __forceinline__ bool take_next(const StepSmem<T> &S, TilePipe &pp) {
+    const int f = S.nt[3];
+    pp.h_issued = (f & 2) != 0;
+    return (f & 1) != 0;
+}
+
+// One tile per block (grid ntx x nty).  Halo windows of interior tiles come
+// by TMA; walking several tiles per block with the next tile's h group
+// requested early measured slower for a single mesh (more instructions per
+// node, no better issue rate), so that walk is left to the batched kernel.
+template <typename T>
+__global__ void __launch_bounds__(kNT, (sizeof(T) == 4 ? 1024 : 512) / kNT) k_lat_step(LatArgs<T> A) {
     __shared__ StepSmem<T> S;
-    extern __shared__ __align__(16) unsigned char lat_dsm[];
-    lat_step_tile<T>(A, blockIdx.x, blockIdx.y, S, lat_dsm);
+    extern __shared__ __align__(128) unsigned char lat_dsm[];
+    lat_block_init<T>(S);
+    TilePipe pp;
+    const NextTile none{0, 0, 0, false, false};
+    lat_tile<T>(A, blockIdx.x, blockIdx.y, S, lat_dsm, pp, none);
 }
 
 }  // namespace felbm

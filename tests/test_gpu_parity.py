@@ -72,6 +72,17 @@ def test_fp64_structured_ragged(general):
     assert max(e.values()) <= 1e-12, e
 
 
+def test_fp64_structured_odd_width():
+    # 37 x 29: rows not 16-byte aligned (element-wise halo fills), ragged
+    # tiles in x and y, periodic wrap through both
+    prob = _droplet(37, 29, 9.0)
+    m, kind = run_gpu(prob, "fp64", 60)
+    assert kind == 1
+    o = run_oracle(prob, 60)
+    e = errors(m, o)
+    assert max(e.values()) <= 1e-12, e
+
+
 def test_fp64_unstructured_delaunay():
     xy, tri, box, tag = inputs.jittered_delaunay_mesh(40, 36, 0.25, seed=7)
     rho0, u0, p0 = inputs.droplet_fields(xy, box, (20, 18), 10.0, 1.0, 0.1, 4.0)
@@ -83,12 +94,27 @@ def test_fp64_unstructured_delaunay():
     assert max(e.values()) <= 1e-12, e
 
 
-def test_fp64_walls_rayleigh_taylor_small():
-    prob = configs.c3_rayleigh_taylor(nx=32, ny=64, steps=0)
+@pytest.mark.parametrize("nx,ny", [(32, 64), (30, 45)])
+def test_fp64_walls_rayleigh_taylor_small(nx, ny):
+    # 32 x 64: wall tiles and interior tiles; 30 x 45: odd width and a ragged
+    # top tile row next to the wall
+    prob = configs.c3_rayleigh_taylor(nx=nx, ny=ny, steps=0)
     prob.params["gravity"] = (0.0, -1e-4)
     m, kind = run_gpu(prob, "fp64", 80)
     assert kind == 1
     o = run_oracle(prob, 80)
+    e = errors(m, o)
+    assert max(e.values()) <= 1e-12, e
+
+
+def test_fp64_walls_many_tiles():
+    # 512 x 384 with walls: 768 tiles; interior tiles load their halo by TMA
+    # and mix with x-wrap tiles (cp.async fills) and wall tiles
+    prob = configs.c3_rayleigh_taylor(nx=512, ny=384, steps=0)
+    prob.params["gravity"] = (0.0, -1e-4)
+    m, kind = run_gpu(prob, "fp64", 6)
+    assert kind == 1
+    o = run_oracle(prob, 6)
     e = errors(m, o)
     assert max(e.values()) <= 1e-12, e
 
