@@ -11,9 +11,10 @@ Every quantity is FP64.  Distributions are stored population-major
 
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests in
 ``tests/test_oracle_*.py`` (closed forms, invariants, dense brute force,
-special cases), except the wall bounce-back, which the paper states only by
-name ("parity unpinned" for the wall treatment beyond the rest-state and
-mass checks).
+special cases).  The wall bounce-back, which the paper states only by name,
+is pinned by steady channel flows: the Poiseuille parabola (curvature -g/nu,
+no slip at the wall rows) and the co-current two-phase profile against the
+steady momentum balance.
 """
 from __future__ import annotations
 
