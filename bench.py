@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=40)
+    ap.add_argument("--workload", default="rayleigh_taylor_512x2048",
+                    choices=["rayleigh_taylor_512x2048", "droplet_2048x2048"],
+                    help="droplet_2048x2048: supplementary single-mesh case (periodic, 4.2 M nodes)")
     return ap.parse_args()
 
 
@@ -128,16 +131,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def workload():
+def workload(name="rayleigh_taylor_512x2048"):
     from paper_1608_01906_gb300 import configs
 
+    if name == "droplet_2048x2048":
+        return configs.droplet_structured(2048, 0.3 * 2048, 100.0, configs.DROPLET_XI, 0.01, 0.1,
+                                          0.1, 0.5, 0, "fp32", name)
     return configs.c3_rayleigh_taylor()
 
 
-def config_dict(prob, precision):
-    return {"workload": "rayleigh_taylor_512x2048", "nodes": prob.n_nodes,
-            "triangles": int(len(prob.tri)), "mesh": "structured P1 split, walls y, periodic x",
-            "lattice": "D2Q9", "precision": precision, "Re": 3000, "atwood": 0.5,
+def config_dict(prob, precision, name="rayleigh_taylor_512x2048"):
+    if name == "droplet_2048x2048":
+        phys = {"mesh": "structured P1 split, periodic x and y", "ratio": 100.0,
+                "radius": 0.3 * 2048, "xi": prob.params["xi"]}
+    else:
+        phys = {"mesh": "structured P1 split, walls y, periodic x", "Re": 3000, "atwood": 0.5}
+    return {"workload": name, "nodes": prob.n_nodes, "triangles": int(len(prob.tri)),
+            "lattice": "D2Q9", "precision": precision, **phys,
             "dt": prob.params["dt"],
             "l2": "inputs > L2: double-buffered state %.0f MB vs 126 MB L2, no flush"
                   % (2 * 18 * prob.n_nodes * (4 if precision == "fp32" else 8) / 1e6),
@@ -173,12 +183,19 @@ def run_reference(args):
     orc.build()
     from oracle.oracle import Oracle, Params
 
-    full = workload()
+    full = workload(args.workload)
     # each step: one oracle time step of a bounded sample of the same workload
-    # (a 64 x 256 window of the Rayleigh-Taylor problem, same physics)
-    samp = configs.c3_rayleigh_taylor(nx=64, ny=256)
-    g_full = full.params["gravity"]
-    samp.params["gravity"] = g_full
+    # (same physics on a smaller mesh)
+    if args.workload == "droplet_2048x2048":
+        samp = configs.droplet_structured(128, 0.3 * 128, 100.0, configs.DROPLET_XI, 0.01, 0.1, 0.1,
+                                          0.5, 0, "fp32", "droplet_sample")
+        sample = ("oracle (FP64 C, 1 thread) time step of a 128x128 periodic droplet with the "
+                  "physics of the 2048x2048 case (16,384 nodes) per step")
+    else:
+        samp = configs.c3_rayleigh_taylor(nx=64, ny=256)
+        samp.params["gravity"] = full.params["gravity"]
+        sample = ("oracle (FP64 C, 1 thread) time step on a 64x256 window of the 512x2048 "
+                  "Rayleigh-Taylor problem (16,384 nodes) per step")
     o = Oracle(samp.xy, samp.tri, samp.box, samp.tag, Params(**samp.params))
     o.init(samp.rho0, samp.u0, samp.p0)
     o.step(args.warmup)
@@ -186,12 +203,10 @@ def run_reference(args):
     o.step(args.steps)
     el = time.perf_counter() - t
     v = samp.n_nodes * args.steps / el / 1e6
-    sample = ("oracle (FP64 C, 1 thread) time step on a 64x256 window of the 512x2048 "
-              "Rayleigh-Taylor problem (16,384 nodes) per step")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_dict(full, "fp64"),
+            "data": "synthetic", "config": config_dict(full, "fp64", args.workload),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -288,7 +303,7 @@ def main():
     __graft_entry__.build()
     from paper_1608_01906_gb300 import felbm
 
-    prob = workload()
+    prob = workload(args.workload)
     stream = torch.cuda.Stream()
     mesh = felbm.Mesh(prob.xy, prob.tri, prob.box, prob.tag, stream=stream.cuda_stream)
     params = felbm.make_params(precision=args.precision, **prob.params)
@@ -365,8 +380,8 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, nsteps, el = oracle_rate(prob, args.cpu_seconds)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "FP64 C oracle (1 thread), full 512x2048 mesh, %d time steps, %.1f s"
-                         % (nsteps, el)}
+               "sample": "FP64 C oracle (1 thread), full %s mesh, %d time steps, %.1f s"
+                         % (args.workload, nsteps, el)}
     batched = serving = None
     if rank == 0 and world == 1 and not args.skip_batched:
         # the headline line prints even if a secondary measurement fails
@@ -384,7 +399,7 @@ def main():
                 "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
-                "data": "synthetic", "config": dict(config_dict(prob, args.precision),
+                "data": "synthetic", "config": dict(config_dict(prob, args.precision, args.workload),
                                                     mesh_kind=kind),
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,

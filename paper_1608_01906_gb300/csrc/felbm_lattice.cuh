@@ -196,6 +196,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
     }
     return false;
 }
+// Block-wide wait for a TMA load group: the first warp polls the barrier,
+// the others wait at the block barrier (no issue slots spent polling).
+// True when the phase completed, the same in every thread.
+__device__ __forceinline__ bool block_mbar_wait(uint64_t *bar, unsigned parity) {
+    const bool ok = threadIdx.y != 0 || mbar_wait(bar, parity);
+    return !__syncthreads_or(!ok);
+}
+
 // order this thread's earlier generic-proxy shared accesses (as released to
 // it by a barrier) before later async-proxy writes
 __device__ __forceinline__ void fence_proxy_async() {
@@ -385,12 +393,11 @@ __device__ __forceinline__ bool tile_unwrapped(int x0, int y0, int nx, int ny) {
 // tiles, the h pairs were streamed by the density stage.
 template <typename T>
 __device__ __forceinline__ void lat_node(const LatArgs<T> &A, int k, int lx, int ly, int tid, int32_t i,
-                                         size_t n, T h0, T r0, T drx, T dry, T dmx, T dmy, T kx, T ky,
+                                         size_t n, T h0, T g0, T r0, T drx, T dry, T dmx, T dmy, T kx, T ky,
                                          const V2<T> *gT, const V2<T> (*s_psi)[kNT]) {
     using PG = PairTile<T, 1>;
     const Phys<T> &P = A.P;
     const size_t np = pad4(n);
-    const T g0 = __ldg(A.fin + 9 * np + i);
     const int c = (ly + 1) * PG::W + lx + PG::XH;
     V2<T> gq[4];
 #pragma unroll
@@ -534,10 +541,16 @@ __device__ __forceinline__ bool lat_tile_impl(const LatArgs<T> &A, int bx, int b
         issue_pair_tiles<T, 1, 1, false>(A, tid, x0, y0, gT, np);
     }
     if (!TMA) cp_async_commit();
+    // the node's g rest population (not moved by streaming): requested now so
+    // that its latency overlaps the density stage and the scalar chain
+    const int x = x0 + (int)threadIdx.x, y = y0 + (int)threadIdx.y;
+    const bool valid = INTERIOR || (x < nx && y < ny);
+    const int32_t i = valid ? x + nx * y : 0;
+    const T g0 = valid ? __ldg(A.fin + 9 * np + i) : T(0);
     // rows of the rho region (y0 - 3 .. y0 + 10) all of kind 0 and inside
     const bool rows_in = INTERIOR || !walls || (y0 >= kHD && y0 + kLTY + kHD <= ny);
     if (TMA) {
-        if (__syncthreads_or(!mbar_wait(&S.bar[0], pp.ph[0]))) return tma_gave_up(A, S, pp);
+        if (!block_mbar_wait(&S.bar[0], pp.ph[0])) return tma_gave_up(A, S, pp);
         pp.ph[0] ^= 1u;
     } else {
         cp_async_wait_group<1>();
@@ -616,8 +629,6 @@ __device__ __forceinline__ bool lat_tile_impl(const LatArgs<T> &A, int bx, int b
     // 4. per node: grad mu, stress force, then the collision.  Threads of a
     //    ragged tile outside the mesh take part in every barrier.
     const int lx = threadIdx.x, ly = threadIdx.y;
-    const int x = x0 + lx, y = y0 + ly;
-    const bool valid = INTERIOR || (x < nx && y < ny);
     const int k = (rows_in || !valid) ? 0 : lat_kind(walls, y, ny);
     T dmx, dmy, kx, ky;
     {
@@ -644,16 +655,15 @@ __device__ __forceinline__ bool lat_tile_impl(const LatArgs<T> &A, int bx, int b
     }
     const T r0 = s_rho[ly + 3][lx + 4];
     const T drx = s_gx[ly + 2][lx + 2], dry = s_gy[ly + 2][lx + 2];
-    const int32_t i = valid ? x + nx * y : 0;
     if (TMA) {
-        if (__syncthreads_or(!mbar_wait(&S.bar[1], pp.ph[1]))) return tma_gave_up(A, S, pp);
+        if (!block_mbar_wait(&S.bar[1], pp.ph[1])) return tma_gave_up(A, S, pp);
         pp.ph[1] ^= 1u;
     } else {
         cp_async_wait_group<0>();
         __syncthreads();
     }
     if (valid)
-        lat_node<T>(A, k, lx, ly, tid, i, n, h0, r0, drx, dry, dmx, dmy, kx, ky, gT, s_psi);
+        lat_node<T>(A, k, lx, ly, tid, i, n, h0, g0, r0, drx, dry, dmx, dmy, kx, ky, gT, s_psi);
     __syncthreads();  // the caller may reuse shared memory for the next tile
     return true;
 }
