@@ -127,6 +127,7 @@ static DevLattice<T> dev_lattice(const felbm_mesh *m) {
     d.nx = m->sinfo.nx;
     d.ny = m->sinfo.ny;
     d.walls = m->sinfo.walls ? 1 : 0;
+    d.pitch = m->sinfo.pitch;
     for (int k = 0; k < 3; ++k)
         for (int o = 0; o < 6; ++o) {
             d.c[k][o][0] = (T)m->sinfo.a[k][o][0];
@@ -244,6 +245,7 @@ static void do_steps(felbm_state *s, int64_t n) {
         LatArgs<T> A;
         A.nx = m->sinfo.nx;
         A.ny = m->sinfo.ny;
+        A.pitch = m->sinfo.pitch;
         A.walls = m->sinfo.walls ? 1 : 0;
         A.c = lat_coef<T>(m, s->params.dt);
         A.P = phys_of<T>(s->params);
@@ -464,8 +466,8 @@ int felbm_state_init(const felbm_mesh *mesh, const felbm_params *params, const d
     auto alloc = [&](void **p, size_t bytes) {
         if (e == cudaSuccess) e = cudaMalloc(p, bytes);
     };
-    alloc(&s->f[0], 18 * pad4(N) * es);
-    alloc(&s->f[1], 18 * pad4(N) * es);
+    alloc(&s->f[0], 18 * pad4(pop_slots(mesh)) * es);
+    alloc(&s->f[1], 18 * pad4(pop_slots(mesh)) * es);
     alloc(&s->scratch, 6 * N * es);
     alloc(&s->mom, 4 * N * es);
     alloc((void **)&s->d_out, (5 * N + 3 * (kTotalsBlocks + 1)) * sizeof(double));
@@ -495,6 +497,9 @@ int felbm_state_init(const felbm_mesh *mesh, const felbm_params *params, const d
     }
     e = cudaMemcpyAsync(s->mom, hm.data(), hm.size(), cudaMemcpyHostToDevice, mesh->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->d_flag, 0, sizeof(int), mesh->stream);
+    // padding slots of structured rows are never read; zeroed all the same
+    for (int c = 0; c < 2 && e == cudaSuccess; ++c)
+        e = cudaMemsetAsync(s->f[c], 0, 18 * pad4(pop_slots(mesh)) * es, mesh->stream);
     if (e == cudaSuccess) {
         if (es == 8)
             init_any<double>(s);
@@ -562,8 +567,8 @@ int felbm_moments_get(felbm_state *s, double *rho, double *C, double *u, double 
 
 int felbm_state_export(felbm_state *s, double *hbar, double *gbar) {
     if (!s || !hbar || !gbar) return FELBM_ERR_INVALID_ARG;
-    const size_t N = (size_t)s->mesh->n_nodes, es = s->esize;
-    std::vector<unsigned char> buf(18 * pad4(N) * es);
+    const size_t N = (size_t)s->mesh->n_nodes, es = s->esize, S = pop_slots(s->mesh);
+    std::vector<unsigned char> buf(18 * pad4(S) * es);
     cudaError_t e = cudaMemcpyAsync(buf.data(), s->f[s->cur], buf.size(), cudaMemcpyDeviceToHost,
                                     s->mesh->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->mesh->stream);
@@ -572,7 +577,7 @@ int felbm_state_export(felbm_state *s, double *hbar, double *gbar) {
     for (int a = 0; a < 18; ++a)
         for (size_t k = 0; k < N; ++k) {
             const size_t c = perm ? (size_t)s->mesh->host.perm[k] : k;
-            const size_t q = pop_index(a, k, N);
+            const size_t q = pop_index(a, pop_slot(s->mesh, k), S);
             const double v = es == 8 ? reinterpret_cast<double *>(buf.data())[q]
                                      : (double)reinterpret_cast<float *>(buf.data())[q];
             (a < 9 ? hbar : gbar)[(a % 9) * N + c] = v;
@@ -582,18 +587,19 @@ int felbm_state_export(felbm_state *s, double *hbar, double *gbar) {
 
 int felbm_state_import(felbm_state *s, const double *hbar, const double *gbar) {
     if (!s || !hbar || !gbar) return FELBM_ERR_INVALID_ARG;
-    const size_t N = (size_t)s->mesh->n_nodes, es = s->esize;
-    std::vector<unsigned char> buf(18 * pad4(N) * es, 0);
+    const size_t N = (size_t)s->mesh->n_nodes, es = s->esize, S = pop_slots(s->mesh);
+    std::vector<unsigned char> buf(18 * pad4(S) * es, 0);
     const bool perm = s->mesh->kind == 0;
     for (int a = 0; a < 18; ++a)
         for (size_t k = 0; k < N; ++k) {
             const size_t c = perm ? (size_t)s->mesh->host.perm[k] : k;
             const double v = (a < 9 ? hbar : gbar)[(a % 9) * N + c];
             if (!std::isfinite(v)) return FELBM_ERR_INVALID_ARG;
+            const size_t q = pop_index(a, pop_slot(s->mesh, k), S);
             if (es == 8)
-                reinterpret_cast<double *>(buf.data())[pop_index(a, k, N)] = v;
+                reinterpret_cast<double *>(buf.data())[q] = v;
             else
-                reinterpret_cast<float *>(buf.data())[pop_index(a, k, N)] = (float)v;
+                reinterpret_cast<float *>(buf.data())[q] = (float)v;
         }
     cudaError_t e = cudaMemcpyAsync(s->f[s->cur], buf.data(), buf.size(), cudaMemcpyHostToDevice,
                                     s->mesh->stream);

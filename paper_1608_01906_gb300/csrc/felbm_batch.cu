@@ -103,6 +103,27 @@ __global__ void __launch_bounds__(kNT, (sizeof(T) == 4 ? 768 : 512) / kNT) k_bat
     }
 }
 
+// One block per tile of the batch's tile list, at the register budget of
+// the single-mesh step (4 blocks per SM in FP32).  Zeroes both tile counters,
+// so that a walking launch after it starts from zero.
+template <typename T>
+__global__ void __launch_bounds__(kNT, (sizeof(T) == 4 ? 1024 : 512) / kNT) k_batch_tile(BatchArgs<T> B) {
+    __shared__ StepSmem<T> S;
+    __shared__ __align__(16) LatArgs<T> sA;
+    extern __shared__ __align__(128) unsigned char bdsm[];
+    if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+        B.ctr[0] = 0u;
+        B.ctr[1] = 0u;
+    }
+    lat_block_init<T>(S);
+    const TileRef r = B.tiles[blockIdx.x];
+    int cur = -1;
+    load_mesh<T>(B, r.mesh, sA, cur);
+    TilePipe pp;
+    const NextTile none{0, 0, 0, false, false};
+    lat_tile<T>(sA, r.bx, r.by, S, bdsm, pp, none);
+}
+
 template <typename T>
 static LatCoef<T> lat_coef_b(const felbm_mesh *m, double dt) {
     LatCoef<T> c;
@@ -189,9 +210,12 @@ static cudaError_t batch_launch(felbm_batch *b, int parity, int write_mom) {
     B.ctr = b->d_ctr;
     B.parity = parity;
     B.write_mom = write_mom;
-    const unsigned grid = b->bps > 0 ? (unsigned)(b->bps * b->sm_count) : (unsigned)b->ntiles;
     b->launches++;
-    k_batch_step<T><<<grid, dim3(kLTX, kLTY), batch_smem(sizeof(T)), b->stream>>>(B);
+    if (b->bps > 0)
+        k_batch_step<T><<<(unsigned)(b->bps * b->sm_count), dim3(kLTX, kLTY), batch_smem(sizeof(T)),
+                          b->stream>>>(B);
+    else
+        k_batch_tile<T><<<(unsigned)b->ntiles, dim3(kLTX, kLTY), batch_smem(sizeof(T)), b->stream>>>(B);
     return cudaGetLastError();
 }
 
@@ -245,6 +269,7 @@ static int setup_meshes(felbm_batch *b) {
         std::memset(&bm, 0, sizeof(bm));
         bm.a.nx = m->sinfo.nx;
         bm.a.ny = m->sinfo.ny;
+        bm.a.pitch = m->sinfo.pitch;
         bm.a.walls = m->sinfo.walls ? 1 : 0;
         bm.a.c = lat_coef_b<T>(m, s->params.dt);
         bm.a.P = phys_b<T>(s->params);
@@ -263,7 +288,10 @@ static int setup_meshes(felbm_batch *b) {
 template <typename T>
 static int occupancy(felbm_batch *b) {
     int bps = 0;
-    cudaError_t e = cudaFuncSetAttribute(k_batch_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_batch_tile<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)batch_smem(sizeof(T)));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_batch_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)batch_smem(sizeof(T)));
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_batch_step<T>, kLTX * kLTY,

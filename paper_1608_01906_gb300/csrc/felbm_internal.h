@@ -32,6 +32,7 @@ struct HostCSR {
 struct StructuredInfo {
     bool ok = false;
     int32_t nx = 0, ny = 0;
+    int32_t pitch = 0;   // population row pitch: nx rounded up to a multiple of 4
     bool walls = false;  // non-periodic y with walls on the first and last row
     double h = 1.0;
     // 6 neighbour offsets (dx, dy) and their assembled a/b coefficients of an
@@ -71,12 +72,17 @@ struct DevCSR {
                __ldg(byy + p));
     }
     __device__ __forceinline__ int tag_of(int32_t i) const { return tag ? (int)tag[i] : 0; }
+    // population storage: slot of node i, slots per population array
+    __device__ __forceinline__ size_t slot(int32_t i) const { return (size_t)i; }
+    __device__ __forceinline__ size_t slots() const { return (size_t)n; }
 #endif
 };
 
 // Structured lattice split (node i = x + nx*y): six neighbours at fixed
 // offsets, coefficients of three row kinds (0 interior, 1 bottom wall row,
-// 2 top wall row) held in the kernel parameters.
+// 2 top wall row) held in the kernel parameters.  Populations are stored in
+// rows of `pitch` slots (x + pitch*y), pitch = nx rounded up to a multiple
+// of 4, so that every row starts 16-byte aligned.
 // offsets o = 0..5: (1,0), (1,1), (0,1), (-1,0), (-1,-1), (0,-1)
 #ifdef __CUDACC__
 __host__ __device__
@@ -89,7 +95,7 @@ constexpr int lat_dy(int o) { return o == 1 || o == 2 ? 1 : (o == 4 || o == 5 ? 
 
 template <typename T>
 struct DevLattice {
-    int32_t n, nx, ny, walls;
+    int32_t n, nx, ny, walls, pitch;
     T c[3][6][5];  // ax, ay, bxx, bxy, byy
 #ifdef __CUDACC__
     template <typename Fn>
@@ -112,6 +118,11 @@ struct DevLattice {
         const int32_t y = i / nx;
         return y == 0 ? 2 : (y == ny - 1 ? 4 : 0);
     }
+    __device__ __forceinline__ size_t slot(int32_t i) const {
+        const int32_t y = i / nx;
+        return (size_t)(i - y * nx) + (size_t)pitch * (size_t)y;
+    }
+    __device__ __forceinline__ size_t slots() const { return (size_t)pitch * (size_t)ny; }
 #endif
 };
 
@@ -122,11 +133,12 @@ struct Phys {
 };
 
 // Storage of the 18 populations of a state: direction pairs interleaved.
-// With Np = N rounded up to a multiple of 4 (keeps every pair array 16-byte
-// aligned): h_0 at [0, N); the h pairs q = 0..3 of opposite directions
-// (1,3), (2,4), (5,7), (6,8) at Np + 2 Np q + 2 i + s, slot s = 0 for 1, 2,
-// 5, 6 and s = 1 for 3, 4, 7, 8; g the same from offset 9 Np.  A state
-// buffer holds 18 Np values.
+// Each population array has S slots (S = N on general meshes, pitch * ny on
+// structured ones; slot i of node i, or x + pitch*y).  With Np = S rounded up
+// to a multiple of 4 (keeps every pair array 16-byte aligned): h_0 at
+// [0, S); the h pairs q = 0..3 of opposite directions (1,3), (2,4), (5,7),
+// (6,8) at Np + 2 Np q + 2 i + s, slot s = 0 for 1, 2, 5, 6 and s = 1 for 3,
+// 4, 7, 8; g the same from offset 9 Np.  A state buffer holds 18 Np values.
 // A pair is one 8-byte (FP32) or 16-byte (FP64) word per node, read and
 // streamed together with packed two-wide arithmetic.
 #ifdef __CUDACC__
@@ -191,6 +203,17 @@ struct felbm_mesh {
     uint8_t *d_tag = nullptr;
     int64_t device_bytes = 0;
 };
+
+// Population slots per array of a state on mesh m, and the slot of node i
+// (internal order).
+inline size_t pop_slots(const felbm_mesh *m) {
+    return m->kind == 1 ? (size_t)m->sinfo.pitch * (size_t)m->sinfo.ny : (size_t)m->n_nodes;
+}
+inline size_t pop_slot(const felbm_mesh *m, size_t i) {
+    if (m->kind != 1) return i;
+    const size_t nx = (size_t)m->sinfo.nx;
+    return i % nx + (size_t)m->sinfo.pitch * (i / nx);
+}
 
 struct felbm_state {
     const felbm_mesh *mesh = nullptr;

@@ -53,8 +53,9 @@ struct StreamAcc {
     __device__ __forceinline__ static void run(const Topo &m, const T *__restrict__ pops,
                                                int32_t i, T dt, const T *self, T *acc) {
         const T hdt = T(0.5) * dt;
-        const int32_t n = m.n;
+        const size_t S = m.slots();
         m.for_each(i, [&](int32_t j, T ax, T ay, T bxx, T bxy, T byy) {
+            const size_t sj = m.slot(j);
             const T hbxx = hdt * bxx, hbxy = hdt * bxy, hbyy = hdt * byy;
 #pragma unroll
             for (int a = A0; a < A1; ++a) {
@@ -71,7 +72,7 @@ struct StreamAcc {
                     case 7: c = stream_coef<T, 7>(ax, ay, hbxx, hbxy, hbyy); break;
                     default: c = stream_coef<T, 8>(ax, ay, hbxx, hbxy, hbyy); break;
                 }
-                acc[a - A0] += c * (__ldg(pops + pop_index(a, (size_t)j, (size_t)n)) - self[a - A0]);
+                acc[a - A0] += c * (__ldg(pops + pop_index(a, sj, S)) - self[a - A0]);
             }
         });
     }
@@ -92,11 +93,11 @@ __global__ void __launch_bounds__(256) k_rho(Topo m, const T *__restrict__ f, T 
                                              T *__restrict__ rho) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m.n) return;
-    const size_t n = (size_t)m.n;
+    const size_t si = m.slot(i), S = m.slots();
     T h[9], acc[9];
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-        h[a] = f[pop_index(a, (size_t)i, n)];
+        h[a] = f[pop_index(a, si, S)];
         acc[a] = T(0);
     }
     StreamAcc<T, 0, 9>::run(m, f, i, dt, h, acc);
@@ -321,7 +322,7 @@ __global__ void __launch_bounds__(256) k_collide(CollideArgs<T, Topo> A) {
         T self[18], acc[18];
 #pragma unroll
         for (int a = 0; a < 18; ++a) {
-            self[a] = A.fin[pop_index(a, (size_t)i, n)];
+            self[a] = A.fin[pop_index(a, m.slot(i), m.slots())];
             acc[a] = T(0);
         }
         StreamAcc<T, 0, 18>::run(m, A.fin, i, A.P.dt, self, acc);
@@ -344,8 +345,8 @@ __global__ void __launch_bounds__(256) k_collide(CollideArgs<T, Topo> A) {
                     gout, ux, uy, p);
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-        A.fout[pop_index(a, (size_t)i, n)] = hout[a];
-        A.fout[pop_index(9 + a, (size_t)i, n)] = gout[a];
+        A.fout[pop_index(a, m.slot(i), m.slots())] = hout[a];
+        A.fout[pop_index(9 + a, m.slot(i), m.slots())] = gout[a];
     }
     if (!(finite_val(r) && finite_val(ux) && finite_val(uy) && finite_val(p))) atomicOr(A.flag, 1);
     if (A.mom) {
@@ -388,8 +389,8 @@ __global__ void __launch_bounds__(256) k_init(Topo m, T *__restrict__ fout, Fiel
         const T Fa = hdt * T(3) * (eX - uX) * gam;
         const T Ga = hdt * (eD - uD) * gmw + hdt * T(3) * (eK - uK) * gam;
         const T Ba = T(0.5) * r * wa * (T(3) * edu + T(4.5) * edu * (T(2) * eu + edu) - T(1.5) * udu);
-        fout[pop_index(a, (size_t)i, n)] = r * gam + Fa;
-        fout[pop_index(9 + a, (size_t)i, n)] = wa * T(3) * p + r * gmw + Ga + Ba;
+        fout[pop_index(a, m.slot(i), m.slots())] = r * gam + Fa;
+        fout[pop_index(9 + a, m.slot(i), m.slots())] = wa * T(3) * p + r * gmw + Ga + Ba;
     }
 }
 

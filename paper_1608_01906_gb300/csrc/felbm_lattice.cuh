@@ -16,9 +16,12 @@
 // Opposite directions (a, abar) are stored interleaved (pop_index): the
 // stencil of a pair reads one 8-byte (FP32) word per neighbour and runs in
 // packed two-wide arithmetic (FFMA2 on sm_103a), each lane with its own
-// coefficient.  All tiles are requested with cp.async (16-byte chunks when
-// nx % 4 == 0) when the block starts; the g tiles arrive while rho and the
-// scalar chain are computed.
+// coefficient.  Population rows are stored with a pitch of nx rounded up to
+// a multiple of 4 slots, so every row starts 16-byte aligned.  Halo windows
+// that need no periodic wrap arrive as TMA boxes, the others by cp.async
+// (16-byte chunks unless a chunk would straddle the wrap of a row whose
+// length is not a multiple of 4); all are requested when the block starts,
+// and the g tiles arrive while rho and the scalar chain are computed.
 //
 // Coefficient tables: for each row kind (interior, bottom wall row, top wall
 // row), offset o and pair q, the streaming coefficients of the pair's two
@@ -74,6 +77,7 @@ struct LatCoef {
 template <typename T>
 struct LatArgs {
     int32_t nx, ny, walls;
+    int32_t pitch;  // population row pitch (slots), nx rounded up to a multiple of 4
     LatCoef<T> c;
     Phys<T> P;
     const T *fin;
@@ -104,7 +108,7 @@ struct FillPlan {
 };
 
 template <typename E, int W, int H, bool VEC>
-__device__ __forceinline__ FillPlan fill_plan(int tid, int nthreads, int gx0, int gy0, int nx, int ny,
+__device__ __forceinline__ FillPlan fill_plan(int tid, int nthreads, int gx0, int gy0, int nx, int pitch, int ny,
                                               int walls) {
     constexpr int CE = 16 / (int)sizeof(E);
     constexpr int PER_ROW = VEC ? W / CE : W;
@@ -130,7 +134,7 @@ __device__ __forceinline__ FillPlan fill_plan(int tid, int nthreads, int gx0, in
                 while (gy < 0) gy += ny;
                 while (gy >= ny) gy -= ny;
             }
-            f.src[t] = inside ? gx + nx * gy : 0;
+            f.src[t] = inside ? gx + pitch * gy : 0;
             f.ok[t] = inside;
             f.dst[t] = r * W + col;
             f.n = t + 1;
@@ -253,7 +257,8 @@ struct PairTile {
 };
 
 // Request the depth-D halo tiles of the 4 pairs of h (G = 0) or g (G = 1).
-// VEC: 16-byte chunks (needs nx % 4 == 0, so no chunk straddles the x wrap).
+// VEC: 16-byte chunks (needs a window without x wrap, or nx % 4 == 0, so
+// that no chunk straddles the wrap).
 template <typename T, int G, int D, bool VEC>
 __device__ __forceinline__ void issue_pair_tiles(const LatArgs<T> &A, int tid, int x0, int y0,
                                                  V2<T> *tiles, size_t np) {
@@ -261,7 +266,7 @@ __device__ __forceinline__ void issue_pair_tiles(const LatArgs<T> &A, int tid, i
     using PT = PairTile<T, D>;
     const E *src = reinterpret_cast<const E *>(A.fin + (G ? 10 : 1) * np);  // pair 0; pair q at + q np
     const FillPlan f =
-        fill_plan<E, PT::W, PT::H, VEC>(tid, kLTX * kLTY, x0 - PT::XH, y0 - D, A.nx, A.ny, A.walls);
+        fill_plan<E, PT::W, PT::H, VEC>(tid, kLTX * kLTY, x0 - PT::XH, y0 - D, A.nx, A.pitch, A.ny, A.walls);
     fill_issue<E, VEC, 4>(f, src, np, tiles, PT::N);
 }
 
@@ -374,13 +379,20 @@ constexpr size_t lat_smem() {
     return LatSmem<T>::bytes;
 }
 
+// Whether the halo windows of a tile at x0 may be filled in 16-byte chunks:
+// rows are 16-byte aligned (pitch), so unless a window wraps around a row
+// whose length is not a multiple of 4.
+__device__ __forceinline__ bool vec_fills(int x0, int nx) {
+    return (nx % 4) == 0 || (x0 >= kHD && x0 + kLTX + kHD <= nx);
+}
+
 // Whether tile (x0, y0) is whole (no node outside the mesh), its rho region
 // and h tiles hold no wall row nor a row outside a walled domain, and rows
 // are 16-byte aligned: such tiles run with the row kind fixed at compile
 // time and vector fills only.
 __device__ __forceinline__ bool tile_interior(int x0, int y0, int nx, int ny, int walls) {
     const bool yin = walls ? (y0 >= kHD && y0 + kLTY + kHD <= ny) : (y0 + kLTY <= ny);
-    return yin && (nx % 4) == 0 && x0 + kLTX <= nx;
+    return yin && x0 + kLTX <= nx && vec_fills(x0, nx);
 }
 
 // Whether the halo windows of tile (x0, y0) lie inside the mesh without a
@@ -393,11 +405,11 @@ __device__ __forceinline__ bool tile_unwrapped(int x0, int y0, int nx, int ny) {
 // tiles, the h pairs were streamed by the density stage.
 template <typename T>
 __device__ __forceinline__ void lat_node(const LatArgs<T> &A, int k, int lx, int ly, int tid, int32_t i,
-                                         size_t n, T h0, T g0, T r0, T drx, T dry, T dmx, T dmy, T kx, T ky,
-                                         const V2<T> *gT, const V2<T> (*s_psi)[kNT]) {
+                                         size_t ip, size_t n, size_t np, T h0, T g0, T r0, T drx, T dry,
+                                         T dmx, T dmy, T kx, T ky, const V2<T> *gT,
+                                         const V2<T> (*s_psi)[kNT]) {
     using PG = PairTile<T, 1>;
     const Phys<T> &P = A.P;
-    const size_t np = pad4(n);
     const int c = (ly + 1) * PG::W + lx + PG::XH;
     V2<T> gq[4];
 #pragma unroll
@@ -421,8 +433,8 @@ __device__ __forceinline__ void lat_node(const LatArgs<T> &A, int k, int lx, int
         V2<T> ho, go;
         collide_pair<T, q>(cp, hs, gq[q], ho, go);
         dsum += (ho.x - hs.x) + (ho.y - hs.y);
-        hout[(size_t)q * np + i] = ho;
-        gout[(size_t)q * np + i] = go;
+        hout[(size_t)q * np + ip] = ho;
+        gout[(size_t)q * np + ip] = go;
     };
     pair_update(IntC<0>{});
     pair_update(IntC<1>{});
@@ -432,8 +444,8 @@ __device__ __forceinline__ void lat_node(const LatArgs<T> &A, int k, int lx, int
         T ho, go;
         collide_pop_rt<T>(cp, 0, h0, g0, ho, go);
         dsum += ho - h0;
-        A.fout[i] = ho - dsum;
-        A.fout[9 * np + i] = go;
+        A.fout[ip] = ho - dsum;
+        A.fout[9 * np + ip] = go;
     }
     if (!(finite_val(r) && finite_val(ux) && finite_val(uy) && finite_val(p))) atomicOr(A.flag, 1);
     if (A.mom) {
@@ -517,7 +529,7 @@ __device__ __forceinline__ bool lat_tile_impl(const LatArgs<T> &A, int bx, int b
     const int nx = A.nx, ny = A.ny, walls = A.walls;
     const int x0 = bx * kLTX, y0 = by * kLTY;
     const int tid = threadIdx.y * kLTX + threadIdx.x;
-    const size_t n = (size_t)nx * ny, np = pad4(n);
+    const size_t n = (size_t)nx * ny, np = pad4((size_t)A.pitch * ny);
     const T dt = A.P.dt;
     // 0. request the h pair tiles (depth 4) and the h rest tile (depth 3) as
     //    group 1, the g pair tiles (depth 1) as group 2; the g tiles arrive
@@ -527,15 +539,15 @@ __device__ __forceinline__ bool lat_tile_impl(const LatArgs<T> &A, int bx, int b
             if (!pp.h_issued) issue_h_group<T>(A, x0, y0, S, dsm);
             issue_g_group<T>(A, x0, y0, S, dsm);
         }
-    } else if (INTERIOR || (nx % 4) == 0) {
+    } else if (INTERIOR || vec_fills(x0, nx)) {
         issue_pair_tiles<T, 0, kHD, true>(A, tid, x0, y0, hT, np);
-        fill_issue<T, true, 1>(fill_plan<T, kH0W, kH0H, true>(tid, kNT, x0 - 4, y0 - 3, nx, ny, walls),
+        fill_issue<T, true, 1>(fill_plan<T, kH0W, kH0H, true>(tid, kNT, x0 - 4, y0 - 3, nx, A.pitch, ny, walls),
                                A.fin, 0, &s_h0[0][0], 0);
         cp_async_commit();
         issue_pair_tiles<T, 1, 1, true>(A, tid, x0, y0, gT, np);
     } else {
         issue_pair_tiles<T, 0, kHD, false>(A, tid, x0, y0, hT, np);
-        fill_issue<T, false, 1>(fill_plan<T, kH0W, kH0H, false>(tid, kNT, x0 - 4, y0 - 3, nx, ny, walls),
+        fill_issue<T, false, 1>(fill_plan<T, kH0W, kH0H, false>(tid, kNT, x0 - 4, y0 - 3, nx, A.pitch, ny, walls),
                                 A.fin, 0, &s_h0[0][0], 0);
         cp_async_commit();
         issue_pair_tiles<T, 1, 1, false>(A, tid, x0, y0, gT, np);
@@ -545,8 +557,9 @@ __device__ __forceinline__ bool lat_tile_impl(const LatArgs<T> &A, int bx, int b
     // that its latency overlaps the density stage and the scalar chain
     const int x = x0 + (int)threadIdx.x, y = y0 + (int)threadIdx.y;
     const bool valid = INTERIOR || (x < nx && y < ny);
-    const int32_t i = valid ? x + nx * y : 0;
-    const T g0 = valid ? __ldg(A.fin + 9 * np + i) : T(0);
+    const int32_t i = valid ? x + nx * y : 0;                        // node (moments)
+    const size_t ip = valid ? (size_t)x + (size_t)A.pitch * y : 0;  // population slot
+    const T g0 = valid ? __ldg(A.fin + 9 * np + ip) : T(0);
     // rows of the rho region (y0 - 3 .. y0 + 10) all of kind 0 and inside
     const bool rows_in = INTERIOR || !walls || (y0 >= kHD && y0 + kLTY + kHD <= ny);
     if (TMA) {
@@ -663,7 +676,7 @@ __device__ __forceinline__ bool lat_tile_impl(const LatArgs<T> &A, int bx, int b
         __syncthreads();
     }
     if (valid)
-        lat_node<T>(A, k, lx, ly, tid, i, n, h0, g0, r0, drx, dry, dmx, dmy, kx, ky, gT, s_psi);
+        lat_node<T>(A, k, lx, ly, tid, i, ip, n, np, h0, g0, r0, drx, dry, dmx, dmy, kx, ky, gT, s_psi);
     __syncthreads();  // the caller may reuse shared memory for the next tile
     return true;
 }

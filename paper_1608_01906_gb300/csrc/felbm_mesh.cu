@@ -330,6 +330,7 @@ void detect_structured(const double *xy, int64_t n_nodes, const int32_t *tri, in
         }
     }
     info.nx = (int32_t)nx;
+    info.pitch = (int32_t)((nx + 3) & ~(int64_t)3);
     info.ny = (int32_t)ny;
     info.walls = walls;
     info.h = h;

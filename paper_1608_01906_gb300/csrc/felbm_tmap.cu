@@ -8,8 +8,9 @@
 //   2  the 4 g pairs: 3-D, box of the depth-1 pair tile.
 // Coordinates outside the mesh load zeros (walls); tiles whose windows would
 // wrap periodically use cp.async fills instead.  The maps need rows of a
-// multiple of 16 bytes (nx % 4 == 0) and the driver's encoder; where either
-// is missing the state keeps d_tmap null and every tile uses cp.async.
+// multiple of 16 bytes (the row pitch, a multiple of 4 slots) and the
+// driver's encoder; without it the state keeps d_tmap null and every tile
+// uses cp.async.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -61,15 +62,16 @@ static bool encode_state(PFN_cuTensorMapEncodeTiled_v12000 fn, const felbm_state
     using PH = PairTile<T, kHD>;
     using PG = PairTile<T, 1>;
     const uint64_t nx = (uint64_t)s->mesh->sinfo.nx, ny = (uint64_t)s->mesh->sinfo.ny;
-    const uint64_t np = pad4((size_t)s->mesh->n_nodes);
+    const uint64_t pitch = (uint64_t)s->mesh->sinfo.pitch;
+    const uint64_t np = pad4(pop_slots(s->mesh));
     const uint64_t wpn = sizeof(T) * 2 / 4, spn = sizeof(T) / 4;  // words per pair, per scalar
     for (int c = 0; c < 2; ++c) {
         T *f = reinterpret_cast<T *>(s->f[c]);
-        const uint64_t pair_rows = nx * wpn * 4, pair_planes = 2 * np * sizeof(T);
+        const uint64_t pair_rows = pitch * wpn * 4, pair_planes = 2 * np * sizeof(T);
         if (!encode(fn, &maps[3 * c + 0], f + np, 3, nx * wpn, ny, 4, pair_rows, pair_planes,
                     (uint32_t)(PH::W * wpn), (uint32_t)PH::H, 4))
             return false;
-        if (!encode(fn, &maps[3 * c + 1], f, 2, nx * spn, ny, 1, nx * spn * 4, 0, (uint32_t)(kH0W * spn),
+        if (!encode(fn, &maps[3 * c + 1], f, 2, nx * spn, ny, 1, pitch * spn * 4, 0, (uint32_t)(kH0W * spn),
                     (uint32_t)kH0H, 1))
             return false;
         if (!encode(fn, &maps[3 * c + 2], f + 10 * np, 3, nx * wpn, ny, 4, pair_rows, pair_planes,
@@ -82,7 +84,7 @@ static bool encode_state(PFN_cuTensorMapEncodeTiled_v12000 fn, const felbm_state
 void lattice_tmaps(felbm_state *s) {
     s->d_tmap = nullptr;
     const felbm_mesh *m = s->mesh;
-    if (m->kind != 1 || m->sinfo.nx % 4 != 0) return;
+    if (m->kind != 1 || m->sinfo.pitch % 4 != 0) return;
     PFN_cuTensorMapEncodeTiled_v12000 fn = encoder();
     if (!fn) return;
     TMap maps[6];

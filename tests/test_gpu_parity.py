@@ -177,8 +177,10 @@ def test_fp32_droplet_1000_steps(general):
     assert e["C"] <= 1e-6 and e["u"] <= 2e-5, e
 
 
-def test_checkpoint_restart_bitwise():
-    prob = _droplet(40, 40, 10.0)
+@pytest.mark.parametrize("nx,ny", [(40, 40), (38, 30)])
+def test_checkpoint_restart_bitwise(nx, ny):
+    # 38 x 30: population rows padded to a pitch of 40 slots
+    prob = _droplet(nx, ny, 10.0)
     mesh = felbm.Mesh(prob.xy, prob.tri, prob.box, prob.tag)
     pr = felbm.make_params(precision="fp64", **prob.params)
     a = felbm.State(mesh, pr, prob.rho0)
@@ -187,6 +189,8 @@ def test_checkpoint_restart_bitwise():
     b = felbm.State(mesh, pr, prob.rho0)
     b.step(20)
     h, g = b.export()
+    o = run_oracle(prob, 20)  # exported populations in caller order
+    assert rel_l2(h.ravel(), o.h.ravel()) <= 1e-12 and rel_l2(g.ravel(), o.g.ravel()) <= 1e-12
     c = felbm.State(mesh, pr, np.ones(prob.n_nodes))
     c.import_(h, g)
     c.step(20)
