@@ -86,6 +86,7 @@ static Phys<T> phys_of(const felbm_params &p) {
     P.dt = (T)p.dt;
     P.gx = (T)p.gravity[0];
     P.gy = (T)p.gravity[1];
+    P.inv_drho = (T)(1.0 / (p.rho_l - p.rho_v));
     return P;
 }
 

@@ -130,6 +130,7 @@ struct DevLattice {
 template <typename T>
 struct Phys {
     T rho_l, rho_v, beta, kappa, inv_tau_l, inv_tau_v, dt, gx, gy;
+    T inv_drho;  // 1 / (rho_l - rho_v)
 };
 
 // Storage of the 18 populations of a state: direction pairs interleaved.

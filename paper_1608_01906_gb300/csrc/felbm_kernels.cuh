@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(256) k_mu(Topo m, Fields<T> F, Phys<T> P) {
 // (in FP32 the other order repeats the same O(ulp(rho)) error every step).
 template <typename T>
 struct CollidePrep {
-    T r, ux, uy, p, w, omw, opw, hdt, Xx, Xy, uX, uD, uK, uu, dux, duy, udu, drx, dry, kx, ky;
+    T r, ux, uy, p, omw, opw, hdt, Xx, Xy, uX, uD, uK, uu, dux, duy, udu, drx, dry, kx, ky;
 };
 
 // sg = sum_a g*_a, mx, my = sum_a e_a g*_a of the streamed (and bounced) g.
@@ -202,12 +202,14 @@ __device__ __forceinline__ CollidePrep<T> collide_prep(const Phys<T> &P, T sg, T
     c.ux = (mx + c.hdt * kx + c.hdt * r * P.gx) * inv_r;
     c.uy = (my + c.hdt * ky + c.hdt * r * P.gy) * inv_r;
     c.p = cs2 * (sg + c.hdt * (c.ux * drx + c.uy * dry));
-    T C = (r - P.rho_v) / (P.rho_l - P.rho_v);
+    T C = (r - P.rho_v) * P.inv_drho;
     C = C < T(0) ? T(0) : (C > T(1) ? T(1) : C);
-    const T tau = T(1) / (C * P.inv_tau_l + (T(1) - C) * P.inv_tau_v);
-    c.w = (T(2) * tau - T(1)) / (T(2) * tau + T(1));
-    c.omw = T(2) / (T(2) * tau + T(1));        // 1 - w
-    c.opw = T(4) * tau / (T(2) * tau + T(1));  // 1 + w
+    // 1/tau = C/tau_l + (1-C)/tau_v; w = (2 tau - 1)/(2 tau + 1) gives, with
+    // s = 1/tau, 1 - w = 2 s/(2 + s) and 1 + w = 4/(2 + s): one reciprocal
+    const T s = C * P.inv_tau_l + (T(1) - C) * P.inv_tau_v;
+    const T d = T(1) / (T(2) + s);
+    c.omw = T(2) * s * d;  // 1 - w
+    c.opw = T(4) * d;      // 1 + w
     c.Xx = cs2 * drx - r * dmx;  // F: c_s^2 grad rho - rho grad mu
     c.Xy = cs2 * dry - r * dmy;
     c.uX = c.ux * c.Xx + c.uy * c.Xy;
