@@ -31,6 +31,13 @@ METRIC = "MNUPS"
 UNIT = "MNUPS"
 ALGO_BYTES_PER_NODE = {"fp32": 144, "fp64": 288}  # 18 populations read + 18 written
 FALLBACK_HBM_GBS = 6800.0
+# FP64 runs are bound by the FP64 pipe (about 85% busy), not by HBM.  Peak:
+# the nominal dense FP64 rate of the part.  Algorithmic flops per node update
+# in FP64: the 1251 flops ncu counts per node (2 DFMA + DADD + DMUL) less the
+# halo recompute of the tile step (h streaming on the depth-3 halo, 1.08x
+# extra; grad rho 0.69x; mu 0.33x; about 220 flops)
+FP64_PEAK_TFLOPS = 1.25
+FP64_ALGO_FLOPS_PER_NODE = 1030
 
 
 def parse():
@@ -358,6 +365,13 @@ def main():
                 "kernel_ms": dom_avg_ms, "peak_source": peak_kind + " copy bandwidth",
                 "step_gbs": algo * args.steps / (ms * 1e-3) / 1e9,
                 "kernel_share": dom_ms / max(sum(v[0] for v in prof.values()), 1e-12)}
+    if args.precision == "fp64":
+        tf = FP64_ALGO_FLOPS_PER_NODE * prob.n_nodes / (dom_avg_ms * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": tf / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": dom_name,
+                    "kernel_ms": dom_avg_ms, "peak_source": "nominal dense FP64 rate",
+                    "hbm_gbs": achieved, "hbm_frac": achieved / peak,
+                    "kernel_share": dom_ms / max(sum(v[0] for v in prof.values()), 1e-12)}
 
     # ---- end to end through the C ABI with host buffers
     torch.cuda.synchronize()
