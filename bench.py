@@ -53,8 +53,11 @@ def parse():
     ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=40)
     ap.add_argument("--workload", default="rayleigh_taylor_512x2048",
-                    choices=["rayleigh_taylor_512x2048", "droplet_2048x2048"],
-                    help="droplet_2048x2048: supplementary single-mesh case (periodic, 4.2 M nodes)")
+                    choices=["rayleigh_taylor_512x2048", "droplet_2048x2048",
+                             "delaunay_droplet_256x256"],
+                    help="droplet_2048x2048: supplementary single-mesh case (periodic, 4.2 M "
+                         "nodes); delaunay_droplet_256x256: the unstructured case (general "
+                         "meshes, L2-resident)")
     return ap.parse_args()
 
 
@@ -144,6 +147,8 @@ def workload(name="rayleigh_taylor_512x2048"):
     if name == "droplet_2048x2048":
         return configs.droplet_structured(2048, 0.3 * 2048, 100.0, configs.DROPLET_XI, 0.01, 0.1,
                                           0.1, 0.5, 0, "fp32", name)
+    if name == "delaunay_droplet_256x256":
+        return configs.c2_unstructured_droplet()
     return configs.c3_rayleigh_taylor()
 
 
@@ -151,6 +156,9 @@ def config_dict(prob, precision, name="rayleigh_taylor_512x2048"):
     if name == "droplet_2048x2048":
         phys = {"mesh": "structured P1 split, periodic x and y", "ratio": 100.0,
                 "radius": 0.3 * 2048, "xi": prob.params["xi"]}
+    elif name == "delaunay_droplet_256x256":
+        phys = {"mesh": "jittered Delaunay (seed 1608), periodic x and y", "ratio": 1000.0,
+                "radius": 48.0, "xi": prob.params["xi"], "nu_ratio": 40.0}
     else:
         phys = {"mesh": "structured P1 split, walls y, periodic x", "Re": 3000, "atwood": 0.5}
     return {"workload": name, "nodes": prob.n_nodes, "triangles": int(len(prob.tri)),
@@ -198,6 +206,10 @@ def run_reference(args):
                                           0.5, 0, "fp32", "droplet_sample")
         sample = ("oracle (FP64 C, 1 thread) time step of a 128x128 periodic droplet with the "
                   "physics of the 2048x2048 case (16,384 nodes) per step")
+    elif args.workload == "delaunay_droplet_256x256":
+        samp = configs.c2_unstructured_droplet(n=64, R=12.0)
+        sample = ("oracle (FP64 C, 1 thread) time step of a 64x64 jittered Delaunay droplet "
+                  "with the physics of the 256x256 case (4,096 nodes) per step")
     else:
         samp = configs.c3_rayleigh_taylor(nx=64, ny=256)
         samp.params["gravity"] = full.params["gravity"]
