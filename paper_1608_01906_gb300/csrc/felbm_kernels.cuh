@@ -33,6 +33,34 @@ __host__ __device__ constexpr T kW(int a) { return a == 0 ? T(4) / T(9) : (a <= 
 template <typename T>
 __device__ __forceinline__ bool finite_val(T v) { return isfinite(v); }
 
+// ---- packed two-wide arithmetic on a pair of opposite populations ----
+
+template <typename T>
+struct V2T;
+template <>
+struct V2T<float> {
+    using type = float2;
+};
+template <>
+struct V2T<double> {
+    using type = double2;
+};
+template <typename T>
+using V2 = typename V2T<T>::type;
+
+// packed two-wide arithmetic (one instruction per operation in FP32)
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double2 vfma(double2 a, double2 b, double2 c) {
+    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ float2 vset(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 vset(double a, double b) { return make_double2(a, b); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ double2 vadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ double2 vmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+
+
 // Streaming coefficient of direction a from the assembled tensors:
 //   c = e.a_ij + (dt/2) e.b_ij.e
 template <typename T, int A>
@@ -45,38 +73,78 @@ __device__ __forceinline__ T stream_coef(T ax, T ay, T hbxx, T hbxy, T hbyy) {
     return c;
 }
 
-// Accumulate sum_j c^a_ij (psi_j - psi_i) for the populations [A0, A1) of the
-// block starting at pops (SoA, stride n).
-template <typename T, int A0, int A1>
-struct StreamAcc {
-    template <typename Topo>
-    __device__ __forceinline__ static void run(const Topo &m, const T *__restrict__ pops,
-                                               int32_t i, T dt, const T *self, T *acc) {
-        const T hdt = T(0.5) * dt;
-        const size_t S = m.slots();
-        m.for_each(i, [&](int32_t j, T ax, T ay, T bxx, T bxy, T byy) {
-            const size_t sj = m.slot(j);
-            const T hbxx = hdt * bxx, hbxy = hdt * bxy, hbyy = hdt * byy;
-#pragma unroll
-            for (int a = A0; a < A1; ++a) {
-                if (a == 0 || a == 9) continue;
-                const int d = a % 9;
-                T c;
-                switch (d) {
-                    case 1: c = stream_coef<T, 1>(ax, ay, hbxx, hbxy, hbyy); break;
-                    case 2: c = stream_coef<T, 2>(ax, ay, hbxx, hbxy, hbyy); break;
-                    case 3: c = stream_coef<T, 3>(ax, ay, hbxx, hbxy, hbyy); break;
-                    case 4: c = stream_coef<T, 4>(ax, ay, hbxx, hbxy, hbyy); break;
-                    case 5: c = stream_coef<T, 5>(ax, ay, hbxx, hbxy, hbyy); break;
-                    case 6: c = stream_coef<T, 6>(ax, ay, hbxx, hbxy, hbyy); break;
-                    case 7: c = stream_coef<T, 7>(ax, ay, hbxx, hbxy, hbyy); break;
-                    default: c = stream_coef<T, 8>(ax, ay, hbxx, hbxy, hbyy); break;
-                }
-                acc[a - A0] += c * (__ldg(pops + pop_index(a, sj, S)) - self[a - A0]);
-            }
-        });
+// Streaming coefficients of pair q (directions pair_dir(q, 0), its opposite):
+// c = e.a_ij + (dt/2) e.b_ij.e, the odd part e.a flipping sign between the
+// two; the slot-0 directions are (1,0), (0,1), (1,1), (-1,1).
+template <typename T>
+__device__ __forceinline__ V2<T> pair_coef(int q, T ax, T ay, T hbxx, T hbxy, T hbyy) {
+    T odd, even;
+    if (q == 0) {
+        odd = ax;
+        even = hbxx;
+    } else if (q == 1) {
+        odd = ay;
+        even = hbyy;
+    } else if (q == 2) {
+        odd = ax + ay;
+        even = (hbxx + hbyy) + T(2) * hbxy;
+    } else {
+        odd = ay - ax;
+        even = (hbxx + hbyy) - T(2) * hbxy;
     }
-};
+    return vset(even + odd, even - odd);
+}
+
+// Streamed pairs of node i from the state f (pair layout, np = padded slot
+// count): psi* = psi - dt sum_{j != i} c_ij (psi_j - psi_i) for the 4 h
+// pairs and, with G, the 4 g pairs, one 8-byte load per pair and neighbour
+// and the neighbour's coefficients loaded once.
+template <typename T, bool G, typename Topo>
+__device__ __forceinline__ void stream_pairs(const Topo &m, const T *__restrict__ f, size_t np, int32_t i,
+                                             T dt, V2<T> *hp, V2<T> *gp) {
+    const V2<T> *hb = reinterpret_cast<const V2<T> *>(f + np);
+    const V2<T> *gb = reinterpret_cast<const V2<T> *>(f + 10 * np);
+    const size_t si = m.slot(i);
+    const V2<T> m1 = vset(T(-1), T(-1));
+    V2<T> hs[4], ha[4], gs[4], ga[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        hs[q] = hb[q * np + si];
+        ha[q] = vset(T(0), T(0));
+        if (G) {
+            gs[q] = gb[q * np + si];
+            ga[q] = vset(T(0), T(0));
+        }
+    }
+    const T hdt = T(0.5) * dt;
+    m.for_each(i, [&](int32_t j, T ax, T ay, T bxx, T bxy, T byy) {
+        const size_t sj = m.slot(j);
+        const T hbxx = hdt * bxx, hbxy = hdt * bxy, hbyy = hdt * byy;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const V2<T> c = pair_coef<T>(q, ax, ay, hbxx, hbxy, hbyy);
+            ha[q] = vfma(c, vfma(hs[q], m1, __ldg(hb + q * np + sj)), ha[q]);
+            if (G) ga[q] = vfma(c, vfma(gs[q], m1, __ldg(gb + q * np + sj)), ga[q]);
+        }
+    });
+    const V2<T> mdt = vset(-dt, -dt);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        hp[q] = vfma(mdt, ha[q], hs[q]);
+        if (G) gp[q] = vfma(mdt, ga[q], gs[q]);
+    }
+}
+
+// Populations of a node by direction from its rest value and 4 pairs.
+template <typename T>
+__device__ __forceinline__ void unpack_pairs(T rest, const V2<T> *p, T *psi) {
+    psi[0] = rest;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        psi[pair_dir(q, 0)] = p[q].x;
+        psi[pair_dir(q, 1)] = p[q].y;
+    }
+}
 
 // Bounce-back at a wall node with inward normal e_k: every population with
 // e_a . e_k > 0 takes the value of its opposite.  psi holds 9 populations.
@@ -93,16 +161,11 @@ __global__ void __launch_bounds__(256) k_rho(Topo m, const T *__restrict__ f, T 
                                              T *__restrict__ rho) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m.n) return;
-    const size_t si = m.slot(i), S = m.slots();
-    T h[9], acc[9];
-#pragma unroll
-    for (int a = 0; a < 9; ++a) {
-        h[a] = f[pop_index(a, si, S)];
-        acc[a] = T(0);
-    }
-    StreamAcc<T, 0, 9>::run(m, f, i, dt, h, acc);
-#pragma unroll
-    for (int a = 1; a < 9; ++a) h[a] -= dt * acc[a];
+    const size_t np = pad4(m.slots());
+    V2<T> hp[4];
+    stream_pairs<T, false>(m, f, np, i, dt, hp, hp);
+    T h[9];
+    unpack_pairs<T>(f[m.slot(i)], hp, h);
     {
         const int k = m.tag_of(i);
         if (k) bounce_back<T>(k, h);
@@ -319,20 +382,13 @@ __global__ void __launch_bounds__(256) k_collide(CollideArgs<T, Topo> A) {
     const size_t n = (size_t)m.n;
     T dmx, dmy;
     recover(m, A.F.mu, i, dmx, dmy);
+    const size_t np = pad4(m.slots()), si = m.slot(i);
     T hs[9], gs[9];
     {
-        T self[18], acc[18];
-#pragma unroll
-        for (int a = 0; a < 18; ++a) {
-            self[a] = A.fin[pop_index(a, m.slot(i), m.slots())];
-            acc[a] = T(0);
-        }
-        StreamAcc<T, 0, 18>::run(m, A.fin, i, A.P.dt, self, acc);
-#pragma unroll
-        for (int a = 0; a < 9; ++a) {
-            hs[a] = self[a] - A.P.dt * acc[a];
-            gs[a] = self[9 + a] - A.P.dt * acc[9 + a];
-        }
+        V2<T> hp[4], gp[4];
+        stream_pairs<T, true>(m, A.fin, np, i, A.P.dt, hp, gp);
+        unpack_pairs<T>(A.fin[si], hp, hs);
+        unpack_pairs<T>(A.fin[9 * np + si], gp, gs);
     }
     {
         const int k = m.tag_of(i);
@@ -345,11 +401,15 @@ __global__ void __launch_bounds__(256) k_collide(CollideArgs<T, Topo> A) {
     T hout[9], gout[9], ux, uy, p;
     collide_node<T>(A.P, hs, gs, r, A.F.drx[i], A.F.dry[i], dmx, dmy, A.F.kx[i], A.F.ky[i], hout,
                     gout, ux, uy, p);
+    V2<T> *hb = reinterpret_cast<V2<T> *>(A.fout + np);
+    V2<T> *gb = reinterpret_cast<V2<T> *>(A.fout + 10 * np);
 #pragma unroll
-    for (int a = 0; a < 9; ++a) {
-        A.fout[pop_index(a, m.slot(i), m.slots())] = hout[a];
-        A.fout[pop_index(9 + a, m.slot(i), m.slots())] = gout[a];
+    for (int q = 0; q < 4; ++q) {
+        hb[q * np + si] = vset(hout[pair_dir(q, 0)], hout[pair_dir(q, 1)]);
+        gb[q * np + si] = vset(gout[pair_dir(q, 0)], gout[pair_dir(q, 1)]);
     }
+    A.fout[si] = hout[0];
+    A.fout[9 * np + si] = gout[0];
     if (!(finite_val(r) && finite_val(ux) && finite_val(uy) && finite_val(p))) atomicOr(A.flag, 1);
     if (A.mom) {
         A.mom[i] = r;

@@ -44,31 +44,6 @@ struct IntC {
 };
 
 template <typename T>
-struct V2T;
-template <>
-struct V2T<float> {
-    using type = float2;
-};
-template <>
-struct V2T<double> {
-    using type = double2;
-};
-template <typename T>
-using V2 = typename V2T<T>::type;
-
-// packed two-wide arithmetic (one instruction per operation in FP32)
-__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ double2 vfma(double2 a, double2 b, double2 c) {
-    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
-}
-__device__ __forceinline__ float2 vset(float a, float b) { return make_float2(a, b); }
-__device__ __forceinline__ double2 vset(double a, double b) { return make_double2(a, b); }
-__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ double2 vadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ double2 vmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
-
-template <typename T>
 struct LatCoef {
     V2<T> s[3][6][4];  // streaming coefficients per kind, offset, pair
     T r[3][6][2];      // recovery coefficients
