@@ -229,3 +229,74 @@ def shear_wave_fields(xy, box, rho, amplitude):
     u = np.zeros((len(xy), 2))
     u[:, 0] = amplitude * np.sin(2.0 * np.pi * xy[:, 1] / box[1])
     return np.full(len(xy), float(rho)), u, np.zeros(len(xy))
+
+
+# ---- three dimensions (D3Q19 on tetrahedra) -----------------------------
+
+def structured_tet_mesh(nx, ny, nz, h=1.0, periodic_z=True):
+    """Cubic lattice of ``nx * ny * nz`` nodes, each cube split into six
+    tetrahedra around its diagonal from corner (0,0,0) to (1,1,1) (the Kuhn
+    split: one tetrahedron per ordering of the three axes; conforming across
+    cubes and across the periodic wrap).  Periodic in x and y; periodic in z
+    unless ``periodic_z`` is false, in which case the bottom and top node
+    layers are walls with inward normals +z (tag 5) and -z (tag 6) in the
+    D3Q19 order of the oracle.  Periodic directions need at least 3 nodes
+    (with 2 a neighbour sits half a period away and the minimum image is
+    ambiguous).  Node id ``i + nx*(j + ny*k)``.  Returns
+    ``(xyz (N,3), tet (T,4) positively oriented, box (3,), tag (N,))``.
+    """
+    i, j, k = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    i, j, k = i.ravel(order="F"), j.ravel(order="F"), k.ravel(order="F")
+    xyz = np.stack([i, j, k], 1).astype(np.float64) * h
+    nid = lambda a, b, c: (a % nx) + nx * ((b % ny) + ny * (c % nz))  # noqa: E731
+    cz = nz if periodic_z else nz - 1
+    ci, cj, ck = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(cz), indexing="ij")
+    ci, cj, ck = ci.ravel(), cj.ravel(), ck.ravel()
+    unit = np.eye(3, dtype=np.int64)
+    tets = []
+    for perm in ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)):
+        corners = [np.zeros(3, dtype=np.int64)]
+        for ax in perm:
+            corners.append(corners[-1] + unit[ax])
+        v = [nid(ci + c[0], cj + c[1], ck + c[2]) for c in corners]
+        t = np.stack(v, 1)
+        # orientation: det of the edge vectors in unwrapped coordinates
+        e = np.array([corners[1], corners[2], corners[3]], dtype=np.float64)
+        if np.linalg.det(e) < 0:
+            t = t[:, [0, 2, 1, 3]]
+        tets.append(t)
+    tet = np.concatenate(tets, 0).astype(np.int32)
+    box = np.array([nx * h, ny * h, nz * h if periodic_z else 0.0])
+    tag = np.zeros(len(xyz), dtype=np.uint8)
+    if not periodic_z:
+        tag[k == 0] = 5
+        tag[k == nz - 1] = 6
+    return xyz, tet, box, tag
+
+
+def droplet_fields3(xyz, box, center, radius, rho_l, rho_v, xi, u0=(0.0, 0.0, 0.0)):
+    """Spherical liquid drop of radius ``radius`` in vapour: the tanh
+    profile of ``droplet_fields`` in the minimum-image distance to
+    ``center``; uniform velocity ``u0``, zero pressure.  Returns
+    ``(rho0, u0 (N,3), p0)``."""
+    d = np.stack([_wrap(xyz[:, c] - center[c], box[c]) for c in range(3)], 1)
+    r = np.sqrt((d * d).sum(1))
+    rho = 0.5 * (rho_l + rho_v) + 0.5 * (rho_l - rho_v) * np.tanh(2.0 * (radius - r) / xi)
+    u = np.tile(np.asarray(u0, dtype=np.float64), (len(xyz), 1))
+    return rho, u, np.zeros(len(xyz))
+
+
+def slab_fields3(xyz, z_lo, z_hi, rho_l, rho_v, xi):
+    """Flat liquid slab ``z_lo < z < z_hi`` (two tanh interfaces), u = 0,
+    p = 0."""
+    z = xyz[:, 2]
+    t = np.tanh(2.0 * (z - z_lo) / xi) - np.tanh(2.0 * (z - z_hi) / xi)
+    rho = rho_v + 0.5 * (rho_l - rho_v) * t
+    return rho, np.zeros((len(xyz), 3)), np.zeros(len(xyz))
+
+
+def shear_wave_fields3(xyz, box, rho, amplitude):
+    """Uniform density, ``u_x = U sin(2 pi z / Lz)``, other components 0, p = 0."""
+    u = np.zeros((len(xyz), 3))
+    u[:, 0] = amplitude * np.sin(2.0 * np.pi * xyz[:, 2] / box[2])
+    return np.full(len(xyz), float(rho)), u, np.zeros(len(xyz))
