@@ -62,6 +62,7 @@ typedef enum felbm_status {
 #define FELBM_PERIODIC_X 0x1u   /* box[0] > 0 is the period in x */
 #define FELBM_PERIODIC_Y 0x2u   /* box[1] > 0 is the period in y */
 #define FELBM_MESH_GENERAL 0x4u /* never use the structured-lattice kernels */
+#define FELBM_PERIODIC_Z 0x8u   /* tetrahedral meshes: box[2] > 0 is the period in z */
 
 /* precision of the stored distributions and of the bulk arithmetic */
 #define FELBM_FP64 0
@@ -76,14 +77,15 @@ typedef struct felbm_batch felbm_batch;
  * parameter is the C-weighted harmonic mean of tau_l and tau_v; the kinematic
  * viscosity is nu = c_s^2 tau dt.  dt is in the mesh's length unit per unit
  * lattice speed (|e| = 1).  gravity is the body-force acceleration applied by
- * the exact-difference method with du = g dt.  Requirements: rho_l > rho_v > 0,
+ * the exact-difference method with du = g dt (gravity[2], the z component, is
+ * read on tetrahedral meshes only).  Requirements: rho_l > rho_v > 0,
  * sigma >= 0, xi > 0, tau_l > 0, tau_v > 0, dt > 0, all finite. */
 typedef struct felbm_params {
     double rho_l, rho_v;
     double sigma, xi;
     double tau_l, tau_v;
     double dt;
-    double gravity[2];
+    double gravity[3];
     int32_t precision; /* FELBM_FP64 or FELBM_FP32 */
     int32_t flags;     /* must be 0 */
 } felbm_params;
@@ -113,9 +115,36 @@ int felbm_mesh_create(const double *xy, int64_t n_nodes, const int32_t *tri, int
                       const double box[2], uint32_t flags, const uint8_t *node_tag,
                       void *stream, felbm_mesh **out);
 
+/* Create a device-resident tetrahedral mesh: the paper's own
+ * three-dimensional setting (Sec. 2.2.1 linear tetrahedra with the lumped
+ * mass m_i = sum |T|/4, Sec. 2.3 volume-weighted recovery; D3Q19).
+ *   xyz       host, n_nodes x 3 doubles.
+ *   tet       host, n_tet x 4 int32 node ids, positively oriented: the edge
+ *             vectors from the first vertex to the others, at the minimum
+ *             image of the periodic box, have a positive determinant.
+ *   box       host, 3 doubles: periods, read for the flagged directions
+ *             (every element edge shorter than half the period).
+ *   flags     FELBM_PERIODIC_X | FELBM_PERIODIC_Y | FELBM_PERIODIC_Z.
+ *   node_tag  host, n_nodes uint8 or NULL: 0 = fluid; k in 1..18 = no-slip
+ *             wall node whose inward normal is the D3Q19 direction e_k of
+ *             the order (0,0,0), (+-1,0,0), (0,+-1,0), (0,0,+-1), (1,1,0),
+ *             (-1,-1,0), (1,-1,0), (-1,1,0), (1,0,1), (-1,0,-1), (1,0,-1),
+ *             (-1,0,1), (0,1,1), (0,-1,-1), (0,1,-1), (0,-1,1) (opposite
+ *             directions are neighbours).
+ *   stream    as for felbm_mesh_create.
+ * The mesh has kind 2 (felbm_mesh_info) and is stepped by the general
+ * kernels in D3Q19.  On states of such meshes u has 3 components (u0 and u
+ * are n_nodes x 3 doubles), totals has 4 entries (mass and the three
+ * momentum components), and the checkpoint arrays hold 19 x n_nodes
+ * doubles each.  Errors: as felbm_mesh_create (n_nodes < 4, n_tet < 1). */
+int felbm_mesh_create_tet(const double *xyz, int64_t n_nodes, const int32_t *tet, int64_t n_tet,
+                          const double box[3], uint32_t flags, const uint8_t *node_tag,
+                          void *stream, felbm_mesh **out);
+
 /* Mesh facts.  Any output pointer may be NULL.  kind: 0 = general
- * (unstructured CSR kernels), 1 = structured lattice.  device_bytes: device
- * memory held by the mesh. */
+ * (unstructured CSR kernels), 1 = structured lattice, 2 = tetrahedral
+ * (n_tri then counts tetrahedra).  device_bytes: device memory held by the
+ * mesh. */
 int felbm_mesh_info(const felbm_mesh *mesh, int64_t *n_nodes, int64_t *n_tri, int32_t *kind,
                     int64_t *device_bytes);
 
@@ -126,9 +155,11 @@ void felbm_mesh_destroy(felbm_mesh *mesh);
  * distributions to be the equilibria h_eq = rho Gamma(u), g_eq (Eqs. f_eq,
  * g_eq), and stores the pre-collided values psi_eq + source.
  *   rho0  host, n_nodes doubles, > 0.
- *   u0    host, n_nodes x 2 doubles (ux, uy) or NULL for rest.
+ *   u0    host, n_nodes x 2 doubles (ux, uy) or NULL for rest (x 3 on
+ *         tetrahedral meshes).
  *   p0    host, n_nodes doubles or NULL for zero pressure.
  * Device memory: 2 x 18 n_nodes values of the chosen precision plus scratch
+ * (2 x 38 n_nodes on tetrahedral meshes)
  * (structured meshes with nx % 4 == 0: also 768 bytes of TMA tensor maps).
  * Errors: INVALID_ARG, OOM, CUDA. */
 int felbm_state_init(const felbm_mesh *mesh, const felbm_params *params, const double *rho0,
@@ -146,15 +177,17 @@ int felbm_state_sync(felbm_state *state);
 
 /* Moments of the latest step (or of the initial fields before any step):
  *   rho  n_nodes doubles, C n_nodes doubles ((rho - rho_v)/(rho_l - rho_v)),
- *   u    n_nodes x 2 doubles, p n_nodes doubles,
+ *   u    n_nodes x 2 doubles (x 3 on tetrahedral meshes), p n_nodes doubles,
  *   totals 3 doubles: sum_i m_i rho_i, sum_i m_i rho_i ux_i, sum_i m_i rho_i uy_i
+ *   (4 on tetrahedral meshes, with sum_i m_i rho_i uz_i)
  *   with m_i the lumped mass, accumulated in FP64 on the device.
  * Host buffers, any may be NULL.  Synchronises the stream. */
 int felbm_moments_get(felbm_state *state, double *rho, double *C, double *u, double *p,
                       double totals[3]);
 
 /* Checkpoint / restart of the stored pre-collided distributions: hbar and
- * gbar are host arrays of 9 x n_nodes doubles, population-major
+ * gbar are host arrays of 9 x n_nodes doubles (19 x n_nodes on tetrahedral
+ * meshes, D3Q19 order of felbm_mesh_create_tet), population-major
  * (hbar[a * n_nodes + i]), FP64 on the host whatever the state's precision.
  * Export synchronises the stream.  Import converts to the state's precision,
  * clears the non-finite flag, and leaves the state without moments:

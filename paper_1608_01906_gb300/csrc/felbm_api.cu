@@ -35,9 +35,7 @@ __global__ void k_totals_final(int nparts, const double *__restrict__ part, doub
     }
 }
 
-static constexpr int kTotalsBlocks = 304;  // 2 x 152 SMs
-
-static int cuda_status(cudaError_t e) {
+int cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return FELBM_OK;
     if (e == cudaErrorMemoryAllocation) {
         cudaGetLastError();
@@ -280,6 +278,42 @@ static void launch_moments(felbm_state *s) {
     k_totals_final<<<1, 32, 0, m->stream>>>(kTotalsBlocks, part, part + 3 * kTotalsBlocks);
 }
 
+void mesh_free(felbm_mesh *m) {
+    if (!m) return;
+    cudaFree(m->d_rowptr);
+    cudaFree(m->d_col);
+    cudaFree(m->d_perm);
+    cudaFree(m->d_coef64);
+    cudaFree(m->d_coef32);
+    cudaFree(m->d_mass);
+    cudaFree(m->d_tag);
+    delete m;
+}
+
+void state_free(felbm_state *s) {
+    if (!s) return;
+    for (auto &e : s->prof_ev)
+        if (e) cudaEventDestroy(e);
+    cudaFree(s->f[0]);
+    cudaFree(s->f[1]);
+    cudaFree(s->scratch);
+    cudaFree(s->mom);
+    cudaFree(s->d_out);
+    cudaFree(s->d_flag);
+    cudaFree(s->d_tmap);
+    delete s;
+}
+
+bool params_ok(const felbm_params *p) {
+    const double v[] = {p->rho_l, p->rho_v, p->sigma, p->xi, p->tau_l, p->tau_v, p->dt,
+                        p->gravity[0], p->gravity[1], p->gravity[2]};
+    for (double x : v)
+        if (!std::isfinite(x)) return false;
+    return p->rho_l > p->rho_v && p->rho_v > 0.0 && p->sigma >= 0.0 && p->xi > 0.0 &&
+           p->tau_l > 0.0 && p->tau_v > 0.0 && p->dt > 0.0 &&
+           (p->precision == FELBM_FP64 || p->precision == FELBM_FP32) && p->flags == 0;
+}
+
 }  // namespace felbm
 
 // ============================================================================
@@ -299,17 +333,6 @@ const char *felbm_status_string(int st) {
     }
 }
 
-static void mesh_free(felbm_mesh *m) {
-    if (!m) return;
-    cudaFree(m->d_rowptr);
-    cudaFree(m->d_col);
-    cudaFree(m->d_perm);
-    cudaFree(m->d_coef64);
-    cudaFree(m->d_coef32);
-    cudaFree(m->d_mass);
-    cudaFree(m->d_tag);
-    delete m;
-}
 
 int felbm_mesh_create(const double *xy, int64_t n_nodes, const int32_t *tri, int64_t n_tri,
                       const double box[2], uint32_t flags, const uint8_t *node_tag, void *stream,
@@ -425,34 +448,13 @@ int felbm_mesh_info(const felbm_mesh *m, int64_t *n_nodes, int64_t *n_tri, int32
 
 void felbm_mesh_destroy(felbm_mesh *m) { mesh_free(m); }
 
-static void state_free(felbm_state *s) {
-    if (!s) return;
-    for (auto &e : s->prof_ev)
-        if (e) cudaEventDestroy(e);
-    cudaFree(s->f[0]);
-    cudaFree(s->f[1]);
-    cudaFree(s->scratch);
-    cudaFree(s->mom);
-    cudaFree(s->d_out);
-    cudaFree(s->d_flag);
-    cudaFree(s->d_tmap);
-    delete s;
-}
 
-static bool params_ok(const felbm_params *p) {
-    const double v[] = {p->rho_l, p->rho_v, p->sigma, p->xi, p->tau_l, p->tau_v, p->dt,
-                        p->gravity[0], p->gravity[1]};
-    for (double x : v)
-        if (!std::isfinite(x)) return false;
-    return p->rho_l > p->rho_v && p->rho_v > 0.0 && p->sigma >= 0.0 && p->xi > 0.0 &&
-           p->tau_l > 0.0 && p->tau_v > 0.0 && p->dt > 0.0 &&
-           (p->precision == FELBM_FP64 || p->precision == FELBM_FP32) && p->flags == 0;
-}
 
 int felbm_state_init(const felbm_mesh *mesh, const felbm_params *params, const double *rho0,
                      const double *u0, const double *p0, felbm_state **out) {
     if (!mesh || !params || !rho0 || !out) return FELBM_ERR_INVALID_ARG;
     if (!params_ok(params)) return FELBM_ERR_INVALID_ARG;
+    if (mesh->kind == 2) return state_init3(mesh, params, rho0, u0, p0, out);
     const size_t N = (size_t)mesh->n_nodes;
     for (size_t i = 0; i < N; ++i)
         if (!(rho0[i] > 0.0) || !std::isfinite(rho0[i])) return FELBM_ERR_INVALID_ARG;
@@ -523,7 +525,9 @@ int felbm_state_init(const felbm_mesh *mesh, const felbm_params *params, const d
 int felbm_step(felbm_state *s, int64_t n_steps) {
     if (!s || n_steps < 0) return FELBM_ERR_INVALID_ARG;
     if (n_steps == 0) return FELBM_OK;
-    if (s->esize == 8)
+    if (s->mesh->kind == 2)
+        steps3(s, n_steps);
+    else if (s->esize == 8)
         do_steps<double>(s, n_steps);
     else
         do_steps<float>(s, n_steps);
@@ -548,6 +552,10 @@ int felbm_state_sync(felbm_state *s) {
 int felbm_moments_get(felbm_state *s, double *rho, double *C, double *u, double *p, double totals[3]) {
     if (!s) return FELBM_ERR_INVALID_ARG;
     if (!s->have_moments) return FELBM_ERR_INVALID_ARG;
+    if (s->mesh->kind == 2) {
+        const int st3 = moments3(s, rho, C, u, p, totals);
+        return st3 != FELBM_OK ? st3 : check_flag(s);
+    }
     const size_t N = (size_t)s->mesh->n_nodes;
     const cudaStream_t st = s->mesh->stream;
     if (s->esize == 8)
@@ -568,6 +576,10 @@ int felbm_moments_get(felbm_state *s, double *rho, double *C, double *u, double 
 
 int felbm_state_export(felbm_state *s, double *hbar, double *gbar) {
     if (!s || !hbar || !gbar) return FELBM_ERR_INVALID_ARG;
+    if (s->mesh->kind == 2) {
+        const int st3 = export3(s, hbar, gbar);
+        return st3 != FELBM_OK ? st3 : check_flag(s);
+    }
     const size_t N = (size_t)s->mesh->n_nodes, es = s->esize, S = pop_slots(s->mesh);
     std::vector<unsigned char> buf(18 * pad4(S) * es);
     cudaError_t e = cudaMemcpyAsync(buf.data(), s->f[s->cur], buf.size(), cudaMemcpyDeviceToHost,
@@ -588,6 +600,7 @@ int felbm_state_export(felbm_state *s, double *hbar, double *gbar) {
 
 int felbm_state_import(felbm_state *s, const double *hbar, const double *gbar) {
     if (!s || !hbar || !gbar) return FELBM_ERR_INVALID_ARG;
+    if (s->mesh->kind == 2) return import3(s, hbar, gbar);
     const size_t N = (size_t)s->mesh->n_nodes, es = s->esize, S = pop_slots(s->mesh);
     std::vector<unsigned char> buf(18 * pad4(S) * es, 0);
     const bool perm = s->mesh->kind == 0;

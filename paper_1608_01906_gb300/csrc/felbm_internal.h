@@ -29,6 +29,20 @@ struct HostCSR {
     std::vector<int32_t> iperm;    // iperm[caller] = internal id
 };
 
+// General tetrahedral mesh (3-D), same conventions: for each neighbour j != i
+// a_ij = sum_{T∋i,j} |T| grad N_j / (4 m_i) (3 components) and the symmetric
+// part of b_ij = sum |T|/m_i grad N_i (x) grad N_j (6 components: xx, xy, xz,
+// yy, yz, zz).
+struct HostCSR3 {
+    int32_t n = 0;
+    std::vector<int32_t> rowptr, col;
+    std::vector<double> coef;      // 9 * nnz, SoA: ax, ay, az, bxx, bxy, bxz, byy, byz, bzz
+    std::vector<double> mass;      // lumped mass m_i = sum |T|/4, internal order
+    std::vector<uint8_t> tag;      // internal order, empty if no walls (1..18: inward e_k)
+    std::vector<int32_t> perm;     // perm[internal] = caller id
+    std::vector<int32_t> iperm;    // iperm[caller] = internal id
+};
+
 struct StructuredInfo {
     bool ok = false;
     int32_t nx = 0, ny = 0;
@@ -43,6 +57,12 @@ struct StructuredInfo {
 
 int build_csr(const double *xy, int64_t n_nodes, const int32_t *tri, int64_t n_tri,
               const double box[2], uint32_t flags, const uint8_t *tag, HostCSR &out);
+// Tetrahedral mesh: validation, geometry, assembly, RCM (felbm_mesh3.cu).
+int build_csr3(const double *xyz, int64_t n_nodes, const int32_t *tet, int64_t n_tet,
+               const double box[3], uint32_t flags, const uint8_t *tag, HostCSR3 &out);
+// Reverse Cuthill-McKee order of a node graph given as CSR without self loops.
+std::vector<int32_t> rcm_order(int32_t n, const std::vector<int32_t> &rp,
+                               const std::vector<int32_t> &cl);
 // Recognise the structured lattice split; on success fills info (sizes and
 // the coefficients of the three row kinds) and the lumped mass (lattice order).
 void detect_structured(const double *xy, int64_t n_nodes, const int32_t *tri, int64_t n_tri,
@@ -193,12 +213,13 @@ struct felbm_mesh {
     int64_t n_nodes = 0, n_tri = 0;
     uint32_t flags = 0;
     cudaStream_t stream = nullptr;
-    int kind = 0;  // 0 general, 1 structured
+    int kind = 0;  // 0 general triangles, 1 structured triangles, 2 general tetrahedra
     felbm::HostCSR host;
+    felbm::HostCSR3 host3;
     felbm::StructuredInfo sinfo;
     // device arrays
     int32_t *d_rowptr = nullptr, *d_col = nullptr, *d_perm = nullptr;
-    double *d_coef64 = nullptr;  // 5 * nnz, SoA: ax, ay, bxx, bxy, byy
+    double *d_coef64 = nullptr;  // 5 * nnz, SoA: ax, ay, bxx, bxy, byy (kind 2: 9 * nnz, HostCSR3)
     float *d_coef32 = nullptr;
     double *d_mass = nullptr;
     uint8_t *d_tag = nullptr;
@@ -207,6 +228,8 @@ struct felbm_mesh {
 
 // Population slots per array of a state on mesh m, and the slot of node i
 // (internal order).
+inline int mesh_dim(const felbm_mesh *m) { return m->kind == 2 ? 3 : 2; }
+inline int mesh_q(const felbm_mesh *m) { return m->kind == 2 ? 19 : 9; }
 inline size_t pop_slots(const felbm_mesh *m) {
     return m->kind == 1 ? (size_t)m->sinfo.pitch * (size_t)m->sinfo.ny : (size_t)m->n_nodes;
 }
@@ -242,6 +265,19 @@ namespace felbm {
 // Record the launch of a kernel of the given kind; when profiling, the
 // returned event index brackets it (-1: not timed).
 int prof_begin(felbm_state *s, int kind);
+// Shared helpers of the C ABI (felbm_api.cu) and its 3-D part (felbm_api3.cu).
+constexpr int kTotalsBlocks = 304;  // 2 x 152 SMs
+int cuda_status(cudaError_t e);
+bool params_ok(const felbm_params *p);
+void mesh_free(felbm_mesh *m);
+void state_free(felbm_state *s);
+// Tetrahedral meshes (felbm_api3.cu): the state entry points of mesh kind 2.
+int state_init3(const felbm_mesh *mesh, const felbm_params *params, const double *rho0,
+                const double *u0, const double *p0, felbm_state **out);
+void steps3(felbm_state *s, int64_t n);
+int moments3(felbm_state *s, double *rho, double *C, double *u, double *p, double *totals);
+int export3(felbm_state *s, double *hbar, double *gbar);
+int import3(felbm_state *s, const double *hbar, const double *gbar);
 // Encode and upload the tensor maps of a state on a structured mesh
 // (felbm_tmap.cu); leaves d_tmap null where TMA is not usable.
 void lattice_tmaps(felbm_state *s);

@@ -1,0 +1,475 @@
+// Device kernels of one FE-LBM time step on tetrahedral meshes (D3Q19, the
+// paper's own setting), general CSR path.  Same four dependent passes as the
+// two-dimensional general path (felbm_kernels.cuh):
+//   k_rho3      Taylor-Galerkin streaming of the 19 h populations (Sec.
+//               2.2.1, lumped mass), wall bounce-back, rho = sum_a h_a;
+//   k_grad3     recovered grad rho (Sec. 2.3);
+//   k_mu3       Laplacian of rho, the stress force
+//               K_i = kappa [d_i |grad rho|^2 - d_j (d_i rho d_j rho)] and
+//               mu = mu_phi(rho) - kappa lap rho (Sec. 2.1);
+//   k_collide3  recovered grad mu, streaming of all 38 populations,
+//               bounce-back, moments (Eqs. velocity, pressure) and the
+//               post- and next pre-streaming collision (Sec. 2.2).
+// D3Q19 directions are ordered so that 2q+1 and 2q+2 are opposite (q =
+// 0..8); the populations are stored as the rest value plus 9 interleaved
+// opposite pairs (pop layout of felbm_internal.h with 19 per distribution).
+#pragma once
+
+#include "felbm_internal.h"
+#include "felbm_kernels.cuh"
+
+namespace felbm {
+
+// D3Q19: rest, +-x, +-y, +-z, then the 12 edge directions in opposite pairs.
+__host__ __device__ constexpr int e3x(int a) {
+    return (a == 1 || a == 7 || a == 9 || a == 11 || a == 13) ? 1
+           : (a == 2 || a == 8 || a == 10 || a == 12 || a == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int e3y(int a) {
+    return (a == 3 || a == 7 || a == 10 || a == 15 || a == 17) ? 1
+           : (a == 4 || a == 8 || a == 9 || a == 16 || a == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int e3z(int a) {
+    return (a == 5 || a == 11 || a == 14 || a == 15 || a == 18) ? 1
+           : (a == 6 || a == 12 || a == 13 || a == 16 || a == 17) ? -1 : 0;
+}
+template <typename T>
+__host__ __device__ constexpr T w3(int a) {
+    return a == 0 ? T(1) / T(3) : (a <= 6 ? T(1) / T(18) : T(1) / T(36));
+}
+
+// Model constants of one state (Sec. 2.1) with three-component gravity.
+template <typename T>
+struct Phys3 {
+    T rho_l, rho_v, beta, kappa, inv_tau_l, inv_tau_v, dt, g[3];
+    T inv_drho;  // 1 / (rho_l - rho_v)
+};
+
+template <typename T>
+__device__ __forceinline__ T mu_bulk3(const Phys3<T> &P, T r) {
+    return T(4) * P.beta * (r - P.rho_v) * (r - P.rho_l) * (r - T(0.5) * (P.rho_v + P.rho_l));
+}
+
+// General tetrahedral mesh: CSR in reverse Cuthill-McKee order with the
+// coefficient arrays of HostCSR3 (a: 3, b: 6 symmetric components).
+template <typename T>
+struct DevCSR3 {
+    int32_t n;
+    const int32_t *rowptr;
+    const int32_t *col;
+    const T *c[9];       // ax, ay, az, bxx, bxy, bxz, byy, byz, bzz (nnz each)
+    const uint8_t *tag;  // nullptr if no walls
+#ifdef __CUDACC__
+    template <typename Fn>
+    __device__ __forceinline__ void for_each(int32_t i, Fn &&fn) const {
+        const int32_t p1 = __ldg(rowptr + i + 1);
+        for (int32_t p = __ldg(rowptr + i); p < p1; ++p) {
+            T cf[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) cf[k] = __ldg(c[k] + p);
+            fn(__ldg(col + p), cf);
+        }
+    }
+    __device__ __forceinline__ int tag_of(int32_t i) const { return tag ? (int)tag[i] : 0; }
+#endif
+};
+
+// Scalar fields of one time level (N each): rho, grad rho, mu, K.
+template <typename T>
+struct Fields3 {
+    T *rho, *dr[3], *mu, *k[3];
+};
+
+// Streamed values of the 9 pairs of h (G = 0) or h and g (G = 1) of node i:
+// psi* = psi - dt sum_j (e.a_ij + dt/2 e.b_ij.e) (psi_j - psi_i).
+template <typename T, bool G>
+__device__ __forceinline__ void stream_pairs3(const DevCSR3<T> &m, const T *__restrict__ f, size_t np,
+                                              int32_t i, T dt, V2<T> *hp, V2<T> *gp) {
+    const V2<T> *hb = reinterpret_cast<const V2<T> *>(f + np);
+    const V2<T> *gb = reinterpret_cast<const V2<T> *>(f + 20 * np);
+    const V2<T> m1 = vset(T(-1), T(-1));
+    V2<T> hs[9], ha[9], gs[9], ga[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        hs[q] = hb[q * np + i];
+        ha[q] = vset(T(0), T(0));
+        if (G) {
+            gs[q] = gb[q * np + i];
+            ga[q] = vset(T(0), T(0));
+        }
+    }
+    const T hdt = T(0.5) * dt;
+    m.for_each(i, [&](int32_t j, const T *cf) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const int a = 2 * q + 1;
+            const T ex = T(e3x(a)), ey = T(e3y(a)), ez = T(e3z(a));
+            const T odd = ex * cf[0] + ey * cf[1] + ez * cf[2];
+            const T even = hdt * ((ex * ex * cf[3] + ey * ey * cf[6] + ez * ez * cf[8]) +
+                                  T(2) * (ex * ey * cf[4] + ex * ez * cf[5] + ey * ez * cf[7]));
+            const V2<T> c = vset(even + odd, even - odd);
+            ha[q] = vfma(c, vfma(hs[q], m1, __ldg(hb + q * np + j)), ha[q]);
+            if (G) ga[q] = vfma(c, vfma(gs[q], m1, __ldg(gb + q * np + j)), ga[q]);
+        }
+    });
+    const V2<T> mdt = vset(-dt, -dt);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        hp[q] = vfma(mdt, ha[q], hs[q]);
+        if (G) gp[q] = vfma(mdt, ga[q], gs[q]);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void unpack3(T rest, const V2<T> *p, T *psi) {
+    psi[0] = rest;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        psi[2 * q + 1] = p[q].x;
+        psi[2 * q + 2] = p[q].y;
+    }
+}
+
+// Bounce-back at a wall node with inward normal e_k: every population with
+// e_a . e_k > 0 takes the value of its opposite.
+template <typename T>
+__device__ __forceinline__ void bounce_back3(int k, T *psi) {
+    const int kx = e3x(k), ky = e3y(k), kz = e3z(k);
+#pragma unroll
+    for (int a = 1; a < 19; ++a)
+        if (e3x(a) * kx + e3y(a) * ky + e3z(a) * kz > 0) psi[a] = psi[a % 2 ? a + 1 : a - 1];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_rho3(DevCSR3<T> m, const T *__restrict__ f, T dt,
+                                              T *__restrict__ rho) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m.n) return;
+    const size_t np = pad4((size_t)m.n);
+    V2<T> hp[9];
+    stream_pairs3<T, false>(m, f, np, i, dt, hp, hp);
+    T h[19];
+    unpack3<T>(f[i], hp, h);
+    const int k = m.tag_of(i);
+    if (k) bounce_back3<T>(k, h);
+    T r = T(0);
+#pragma unroll
+    for (int a = 0; a < 19; ++a) r += h[a];
+    rho[i] = r;
+}
+
+// Recovered gradient of a scalar field (3 components).
+template <typename T>
+__device__ __forceinline__ void recover3(const DevCSR3<T> &m, const T *__restrict__ f, int32_t i, T *g) {
+    const T fi = f[i];
+    T s0 = T(0), s1 = T(0), s2 = T(0);
+    m.for_each(i, [&](int32_t j, const T *cf) {
+        const T d = __ldg(f + j) - fi;
+        s0 += cf[0] * d;
+        s1 += cf[1] * d;
+        s2 += cf[2] * d;
+    });
+    g[0] = s0;
+    g[1] = s1;
+    g[2] = s2;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_grad3(DevCSR3<T> m, Fields3<T> F) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m.n) return;
+    T g[3];
+    recover3<T>(m, F.rho, i, g);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) F.dr[c][i] = g[c];
+}
+
+// lap rho = sum_c R_c(d_c rho);
+// K_i = kappa [sum_{k != i} R_i((d_k rho)^2) - sum_{j != i} R_j(d_i rho d_j rho)]
+// (the printed form with the identical (d_i rho)^2 contributions cancelled);
+// differences of the products in product form.
+template <typename T>
+__global__ void __launch_bounds__(256) k_mu3(DevCSR3<T> m, Fields3<T> F, Phys3<T> P) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m.n) return;
+    T gi[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) gi[c] = F.dr[c][i];
+    T lap = T(0), K[3] = {T(0), T(0), T(0)};
+    m.for_each(i, [&](int32_t j, const T *cf) {
+        T gj[3], d[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            gj[c] = __ldg(F.dr[c] + j);
+            d[c] = gj[c] - gi[c];
+            lap += cf[c] * d[c];
+        }
+        T sq[3];  // differences of (d_c rho)^2
+#pragma unroll
+        for (int c = 0; c < 3; ++c) sq[c] = d[c] * (gj[c] + gi[c]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            T acc = T(0);
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                if (b == a) continue;
+                const T dab = gj[a] * d[b] + gi[b] * d[a];  // difference of d_a rho d_b rho
+                acc += cf[a] * sq[b] - cf[b] * dab;
+            }
+            K[a] += acc;
+        }
+    });
+    F.mu[i] = mu_bulk3<T>(P, F.rho[i]) - P.kappa * lap;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) F.k[c][i] = P.kappa * K[c];
+}
+
+// Per-node scalars of the collision (3-D form of CollidePrep).
+template <typename T>
+struct Prep3 {
+    T r, u[3], p, omw, opw, hdt, X[3], dr[3], K[3], du[3], uX, uD, uK, uu, udu;
+};
+
+template <typename T>
+__device__ __forceinline__ Prep3<T> prep3(const Phys3<T> &P, T sg, const T *mg, T r, const T *dr,
+                                          const T *dm, const T *K) {
+    constexpr T cs2 = T(1) / T(3);
+    Prep3<T> c;
+    c.hdt = T(0.5) * P.dt;
+    c.r = r;
+    const T inv_r = T(1) / r;
+    T ud = T(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        c.u[k] = (mg[k] + c.hdt * K[k] + c.hdt * r * P.g[k]) * inv_r;
+        ud += c.u[k] * dr[k];
+    }
+    c.p = cs2 * (sg + c.hdt * ud);
+    T C = (r - P.rho_v) * P.inv_drho;
+    C = C < T(0) ? T(0) : (C > T(1) ? T(1) : C);
+    const T s = C * P.inv_tau_l + (T(1) - C) * P.inv_tau_v;  // 1/tau
+    const T d = T(1) / (T(2) + s);
+    c.omw = T(2) * s * d;  // 1 - w
+    c.opw = T(4) * d;      // 1 + w
+    c.uX = c.uD = c.uK = c.uu = c.udu = T(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        c.X[k] = cs2 * dr[k] - r * dm[k];
+        c.dr[k] = dr[k];
+        c.K[k] = K[k];
+        c.du[k] = P.g[k] * P.dt;
+        c.uX += c.u[k] * c.X[k];
+        c.uD += c.u[k] * dr[k];
+        c.uK += c.u[k] * K[k];
+        c.uu += c.u[k] * c.u[k];
+        c.udu += c.du[k] * (T(2) * c.u[k] + c.du[k]);
+    }
+    return c;
+}
+
+// Update of population a (same increment form as collide_pop).
+template <typename T>
+__device__ __forceinline__ void collide_pop3(const Prep3<T> &c, int a, T hs, T gs, T &hout, T &gout) {
+    const T ex = T(e3x(a)), ey = T(e3y(a)), ez = T(e3z(a));
+    const T wa = w3<T>(a);
+    const T eu = ex * c.u[0] + ey * c.u[1] + ez * c.u[2];
+    const T gmw = wa * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * c.uu);  // Gamma - w
+    const T gam = wa + gmw;
+    const T eX = ex * c.X[0] + ey * c.X[1] + ez * c.X[2];
+    const T eD = ex * c.dr[0] + ey * c.dr[1] + ez * c.dr[2];
+    const T eK = ex * c.K[0] + ey * c.K[1] + ez * c.K[2];
+    const T edu = ex * c.du[0] + ey * c.du[1] + ez * c.du[2];
+    const T Fa = c.hdt * T(3) * (eX - c.uX) * gam;
+    const T Ga = c.hdt * (eD - c.uD) * gmw + c.hdt * T(3) * (eK - c.uK) * gam;
+    const T Ba = T(0.5) * c.r * wa * (T(3) * edu + T(4.5) * edu * (T(2) * eu + edu) - T(1.5) * c.udu);
+    const T dh = fma(c.r, wa, -hs) + c.r * gmw;
+    const T dg = fma(wa * T(3), c.p, -gs) + c.r * gmw;
+    hout = hs + (c.omw * dh + c.opw * Fa);
+    gout = gs + (c.omw * dg + c.opw * (Ga + Ba));
+}
+
+template <typename T>
+struct Collide3Args {
+    DevCSR3<T> m;
+    const T *fin;
+    T *fout;
+    Fields3<T> F;
+    Phys3<T> P;
+    T *mom;  // 5N (rho, ux, uy, uz, p) or nullptr
+    int *flag;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_collide3(Collide3Args<T> A) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const DevCSR3<T> &m = A.m;
+    if (i >= m.n) return;
+    const size_t n = (size_t)m.n, np = pad4(n);
+    T dm[3];
+    recover3<T>(m, A.F.mu, i, dm);
+    T hs[19], gs[19];
+    {
+        V2<T> hp[9], gp[9];
+        stream_pairs3<T, true>(m, A.fin, np, i, A.P.dt, hp, gp);
+        unpack3<T>(A.fin[i], hp, hs);
+        unpack3<T>(A.fin[19 * np + i], gp, gs);
+    }
+    const int k = m.tag_of(i);
+    if (k) {
+        bounce_back3<T>(k, hs);
+        bounce_back3<T>(k, gs);
+    }
+    // moments of g: first moments from the differences of opposite pairs
+    T sg = gs[0], mg[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        const int a = 2 * q + 1;
+        const T d = gs[a] - gs[a + 1];
+        sg += gs[a] + gs[a + 1];
+        mg[0] += T(e3x(a)) * d;
+        mg[1] += T(e3y(a)) * d;
+        mg[2] += T(e3z(a)) * d;
+    }
+    const T r = A.F.rho[i];
+    T dr[3], K[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        dr[c] = A.F.dr[c][i];
+        K[c] = A.F.k[c][i];
+    }
+    const Prep3<T> c = prep3<T>(A.P, sg, mg, r, dr, dm, K);
+    T hout[19], gout[19];
+    T dsum = T(0);
+#pragma unroll
+    for (int a = 1; a < 19; ++a) {
+        collide_pop3<T>(c, a, hs[a], gs[a], hout[a], gout[a]);
+        dsum += hout[a] - hs[a];
+    }
+    collide_pop3<T>(c, 0, hs[0], gs[0], hout[0], gout[0]);
+    dsum += hout[0] - hs[0];
+    hout[0] -= dsum;  // local mass: sum_a hbar_a = sum_a h*_a up to one rounding
+    V2<T> *hb = reinterpret_cast<V2<T> *>(A.fout + np);
+    V2<T> *gb = reinterpret_cast<V2<T> *>(A.fout + 20 * np);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        hb[q * np + i] = vset(hout[2 * q + 1], hout[2 * q + 2]);
+        gb[q * np + i] = vset(gout[2 * q + 1], gout[2 * q + 2]);
+    }
+    A.fout[i] = hout[0];
+    A.fout[19 * np + i] = gout[0];
+    if (!(finite_val(r) && finite_val(c.u[0]) && finite_val(c.u[1]) && finite_val(c.u[2]) &&
+          finite_val(c.p)))
+        atomicOr(A.flag, 1);
+    if (A.mom) {
+        A.mom[i] = r;
+        A.mom[n + i] = c.u[0];
+        A.mom[2 * n + i] = c.u[1];
+        A.mom[3 * n + i] = c.u[2];
+        A.mom[4 * n + i] = c.p;
+    }
+}
+
+// Initial pre-collided state psibar = eq + S of (rho, u, p) in mom.
+template <typename T>
+__global__ void __launch_bounds__(128) k_init3(DevCSR3<T> m, T *__restrict__ fout, Fields3<T> F,
+                                               Phys3<T> P, const T *__restrict__ mom) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m.n) return;
+    const size_t n = (size_t)m.n, np = pad4(n);
+    T dm[3], dr[3], K[3];
+    recover3<T>(m, F.mu, i, dm);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        dr[c] = F.dr[c][i];
+        K[c] = F.k[c][i];
+    }
+    const T r = mom[i];
+    Prep3<T> c;
+    constexpr T cs2 = T(1) / T(3);
+    c.hdt = T(0.5) * P.dt;
+    c.r = r;
+    c.p = mom[4 * n + i];
+    c.uX = c.uD = c.uK = c.uu = c.udu = T(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        c.u[k] = mom[(1 + k) * n + i];
+        c.X[k] = cs2 * dr[k] - r * dm[k];
+        c.dr[k] = dr[k];
+        c.K[k] = K[k];
+        c.du[k] = P.g[k] * P.dt;
+        c.uX += c.u[k] * c.X[k];
+        c.uD += c.u[k] * dr[k];
+        c.uK += c.u[k] * K[k];
+        c.uu += c.u[k] * c.u[k];
+        c.udu += c.du[k] * (T(2) * c.u[k] + c.du[k]);
+    }
+    // eq + S: the collision increment form with 1 - w = 1 and 1 + w = 1
+    // applied to psi* = 0 gives eq + F (h) and eq + G + B (g)
+    c.omw = T(1);
+    c.opw = T(1);
+    T h[19], g[19];
+#pragma unroll
+    for (int a = 0; a < 19; ++a) collide_pop3<T>(c, a, T(0), T(0), h[a], g[a]);
+    V2<T> *hb = reinterpret_cast<V2<T> *>(fout + np);
+    V2<T> *gb = reinterpret_cast<V2<T> *>(fout + 20 * np);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        hb[q * np + i] = vset(h[2 * q + 1], h[2 * q + 2]);
+        gb[q * np + i] = vset(g[2 * q + 1], g[2 * q + 2]);
+    }
+    fout[i] = h[0];
+    fout[19 * np + i] = g[0];
+}
+
+// Moments in caller order, FP64: out[0..N) rho, [N..2N) C, [2N..5N) u
+// interleaved (ux, uy, uz), [5N..6N) p.
+template <typename T>
+__global__ void k_gather_moments3(int32_t n, const T *__restrict__ mom, const int32_t *__restrict__ iperm,
+                                  double rho_l, double rho_v, double *__restrict__ out) {
+    const int32_t c = blockIdx.x * blockDim.x + threadIdx.x;  // caller id
+    if (c >= n) return;
+    const int32_t i = iperm[c];
+    const size_t N = (size_t)n;
+    const double r = (double)mom[i];
+    out[c] = r;
+    out[N + c] = (r - rho_v) / (rho_l - rho_v);
+    for (int k = 0; k < 3; ++k) out[2 * N + 3 * (size_t)c + k] = (double)mom[(1 + k) * N + i];
+    out[5 * N + c] = (double)mom[4 * N + i];
+}
+
+// FP64 totals: per-block partials of sum m rho and sum m rho u (4 values,
+// [4][blocks]), then one warp reduces them in a fixed order.
+template <typename T>
+__global__ void __launch_bounds__(256) k_totals3_partial(int32_t n, const T *__restrict__ mom,
+                                                         const double *__restrict__ mass,
+                                                         double *__restrict__ part) {
+    __shared__ double s[4][256];
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    const size_t N = (size_t)n;
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double mr = mass[i] * (double)mom[i];
+        acc[0] += mr;
+        for (int k = 0; k < 3; ++k) acc[1 + k] += mr * (double)mom[(1 + k) * N + i];
+    }
+    for (int k = 0; k < 4; ++k) s[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int k = 0; k < 4; ++k) s[k][threadIdx.x] += s[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 4; ++k) part[(size_t)k * gridDim.x + blockIdx.x] = s[k][0];
+}
+
+__global__ void k_totals3_final(int nparts, const double *__restrict__ part, double *__restrict__ out) {
+    const int l = threadIdx.x;
+    for (int k = 0; k < 4; ++k) {
+        double v = 0.0;
+        for (int b = l; b < nparts; b += 32) v += part[(size_t)k * nparts + b];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (l == 0) out[k] = v;
+    }
+}
+
+}  // namespace felbm

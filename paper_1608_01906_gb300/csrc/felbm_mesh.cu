@@ -50,8 +50,8 @@ struct Entry {
 // Reverse Cuthill-McKee on the node graph given as CSR (rowptr/col, no
 // self loops).  Every connected component is ordered from a pseudo-peripheral
 // start node (lowest degree, then the farthest node of a BFS from it).
-static std::vector<int32_t> rcm_order(int32_t n, const std::vector<int32_t> &rp,
-                                      const std::vector<int32_t> &cl) {
+std::vector<int32_t> rcm_order(int32_t n, const std::vector<int32_t> &rp,
+                               const std::vector<int32_t> &cl) {
     std::vector<int32_t> order;
     order.reserve(n);
     std::vector<char> seen(n, 0);

@@ -27,11 +27,12 @@ FELBM_ERR_UNSUPPORTED = -7
 FELBM_PERIODIC_X = 0x1
 FELBM_PERIODIC_Y = 0x2
 FELBM_MESH_GENERAL = 0x4
+FELBM_PERIODIC_Z = 0x8
 FELBM_FP64 = 0
 FELBM_FP32 = 1
 
 EXPORTED = [
-    "felbm_mesh_create", "felbm_mesh_info", "felbm_mesh_destroy", "felbm_state_init",
+    "felbm_mesh_create", "felbm_mesh_create_tet", "felbm_mesh_info", "felbm_mesh_destroy", "felbm_state_init",
     "felbm_step", "felbm_state_sync", "felbm_moments_get", "felbm_state_export",
     "felbm_state_import", "felbm_state_destroy", "felbm_status_string",
     "felbm_profile_enable", "felbm_profile_read", "felbm_profile_kind_name",
@@ -54,7 +55,7 @@ class felbm_params(C.Structure):
         ("rho_l", C.c_double), ("rho_v", C.c_double),
         ("sigma", C.c_double), ("xi", C.c_double),
         ("tau_l", C.c_double), ("tau_v", C.c_double),
-        ("dt", C.c_double), ("gravity", C.c_double * 2),
+        ("dt", C.c_double), ("gravity", C.c_double * 3),
         ("precision", C.c_int32), ("flags", C.c_int32),
     ]
 
@@ -75,6 +76,8 @@ def load(path: str = LIB_PATH):
     pp = C.POINTER(C.c_void_p)
     lib.felbm_mesh_create.restype = C.c_int
     lib.felbm_mesh_create.argtypes = [vp, i64, vp, i64, vp, C.c_uint32, vp, vp, pp]
+    lib.felbm_mesh_create_tet.restype = C.c_int
+    lib.felbm_mesh_create_tet.argtypes = [vp, i64, vp, i64, vp, C.c_uint32, vp, vp, pp]
     lib.felbm_mesh_info.restype = C.c_int
     lib.felbm_mesh_info.argtypes = [vp, vp, vp, vp, vp]
     lib.felbm_mesh_destroy.restype = None
@@ -156,6 +159,18 @@ def felbm_mesh_create(xy, tri, box, flags, node_tag=None, stream=None):
     return st, out
 
 
+def felbm_mesh_create_tet(xyz, tet, box, flags, node_tag=None, stream=None):
+    lib = load()
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    tet = np.ascontiguousarray(tet, dtype=np.int32)
+    box = np.ascontiguousarray(box, dtype=np.float64)
+    tag = None if node_tag is None else np.ascontiguousarray(node_tag, dtype=np.uint8)
+    out = C.c_void_p()
+    st = lib.felbm_mesh_create_tet(_p(xyz), len(xyz), _p(tet), len(tet), _p(box), flags, _p(tag),
+                                   stream, C.byref(out))
+    return st, out
+
+
 def felbm_state_init(mesh, params: felbm_params, rho0, u0=None, p0=None):
     lib = load()
     rho0 = np.ascontiguousarray(rho0, dtype=np.float64)
@@ -200,10 +215,21 @@ def flags_for(box, general=False):
 
 
 class Mesh:
+    """Triangles (dim 2, D2Q9) or, given (N, 3) coordinates and (T, 4)
+    tetrahedra, a tetrahedral mesh (dim 3, D3Q19)."""
+
     def __init__(self, xy, tri, box, node_tag=None, general=False, stream=None):
         self.n_nodes = len(xy)
-        st, h = felbm_mesh_create(xy, tri, box, flags_for(box, general), node_tag, stream)
-        _check(st, "felbm_mesh_create")
+        self.dim = np.shape(xy)[1]
+        if self.dim == 3:
+            f = sum(bit for bit, L in zip((FELBM_PERIODIC_X, FELBM_PERIODIC_Y, FELBM_PERIODIC_Z), box)
+                    if L > 0)
+            st, h = felbm_mesh_create_tet(xy, tri, box, f, node_tag, stream)
+            _check(st, "felbm_mesh_create_tet")
+        else:
+            st, h = felbm_mesh_create(xy, tri, box, flags_for(box, general), node_tag, stream)
+            _check(st, "felbm_mesh_create")
+        self.q = 19 if self.dim == 3 else 9
         self.handle = h
 
     def info(self):
@@ -228,7 +254,8 @@ def make_params(rho_l, rho_v, sigma, xi, tau_l, tau_v, dt, gravity=(0.0, 0.0), p
     p = felbm_params()
     p.rho_l, p.rho_v, p.sigma, p.xi = rho_l, rho_v, sigma, xi
     p.tau_l, p.tau_v, p.dt = tau_l, tau_v, dt
-    p.gravity[0], p.gravity[1] = gravity
+    g = tuple(gravity) + (0.0,) * (3 - len(gravity))
+    p.gravity[0], p.gravity[1], p.gravity[2] = g
     p.precision = FELBM_FP64 if precision in ("fp64", FELBM_FP64) else FELBM_FP32
     p.flags = 0
     return p
@@ -249,16 +276,16 @@ class State:
         _check(felbm_state_sync(self.handle), "felbm_state_sync")
 
     def moments(self):
-        n = self.n
+        n, d = self.n, self.mesh.dim
         rho, Cf, p = np.empty(n), np.empty(n), np.empty(n)
-        u = np.empty((n, 2))
-        tot = np.empty(3)
+        u = np.empty((n, d))
+        tot = np.empty(1 + d)
         _check(felbm_moments_get(self.handle, rho, Cf, u, p, tot), "felbm_moments_get")
         return {"rho": rho, "C": Cf, "u": u, "p": p, "totals": tot}
 
     def export(self):
-        h = np.empty((9, self.n))
-        g = np.empty((9, self.n))
+        h = np.empty((self.mesh.q, self.n))
+        g = np.empty((self.mesh.q, self.n))
         _check(felbm_state_export(self.handle, h, g), "felbm_state_export")
         return h, g
 
