@@ -24,6 +24,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -54,10 +56,10 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=40)
     ap.add_argument("--workload", default="rayleigh_taylor_512x2048",
                     choices=["rayleigh_taylor_512x2048", "droplet_2048x2048",
-                             "delaunay_droplet_256x256"],
+                             "delaunay_droplet_256x256", "droplet3d_64x64x64"],
                     help="droplet_2048x2048: supplementary single-mesh case (periodic, 4.2 M "
                          "nodes); delaunay_droplet_256x256: the unstructured case (general "
-                         "meshes, L2-resident)")
+                         "meshes, L2-resident); droplet3d_64x64x64: D3Q19 on tetrahedra")
     return ap.parse_args()
 
 
@@ -149,6 +151,8 @@ def workload(name="rayleigh_taylor_512x2048"):
                                           0.1, 0.5, 0, "fp32", name)
     if name == "delaunay_droplet_256x256":
         return configs.c2_unstructured_droplet()
+    if name == "droplet3d_64x64x64":
+        return configs.droplet_3d(64)
     return configs.c3_rayleigh_taylor()
 
 
@@ -156,13 +160,17 @@ def config_dict(prob, precision, name="rayleigh_taylor_512x2048"):
     if name == "droplet_2048x2048":
         phys = {"mesh": "structured P1 split, periodic x and y", "ratio": 100.0,
                 "radius": 0.3 * 2048, "xi": prob.params["xi"]}
+    elif name == "droplet3d_64x64x64":
+        phys = {"mesh": "64^3 cube, 6 Kuhn tetrahedra per cube, periodic x, y, z",
+                "ratio": 10.0, "radius": 16.0, "xi": prob.params["xi"]}
     elif name == "delaunay_droplet_256x256":
         phys = {"mesh": "jittered Delaunay (seed 1608), periodic x and y", "ratio": 1000.0,
                 "radius": 48.0, "xi": prob.params["xi"], "nu_ratio": 40.0}
     else:
         phys = {"mesh": "structured P1 split, walls y, periodic x", "Re": 3000, "atwood": 0.5}
     return {"workload": name, "nodes": prob.n_nodes, "triangles": int(len(prob.tri)),
-            "lattice": "D2Q9", "precision": precision, **phys,
+            "lattice": "D3Q19" if name == "droplet3d_64x64x64" else "D2Q9",
+            "precision": precision, **phys,
             "dt": prob.params["dt"],
             "l2": "inputs > L2: double-buffered state %.0f MB vs 126 MB L2, no flush"
                   % (2 * 18 * prob.n_nodes * (4 if precision == "fp32" else 8) / 1e6),
@@ -170,11 +178,20 @@ def config_dict(prob, precision, name="rayleigh_taylor_512x2048"):
 
 
 # --------------------------------------------------------------------- oracle
-def oracle_rate(prob, seconds, max_steps=None):
-    """Time the FP64 oracle as it stands on this host (one thread)."""
+def make_oracle(prob):
+    """The FP64 oracle of a problem: triangles (2-D) or tetrahedra (3-D)."""
+    if np.shape(prob.xy)[1] == 3:
+        from oracle.oracle3d import Oracle3, Params3
+
+        return Oracle3(prob.xy, prob.tri, prob.box, prob.tag, Params3(**prob.params))
     from oracle.oracle import Oracle, Params
 
-    o = Oracle(prob.xy, prob.tri, prob.box, prob.tag, Params(**prob.params))
+    return Oracle(prob.xy, prob.tri, prob.box, prob.tag, Params(**prob.params))
+
+
+def oracle_rate(prob, seconds, max_steps=None):
+    """Time the FP64 oracle as it stands on this host (one thread)."""
+    o = make_oracle(prob)
     o.init(prob.rho0, prob.u0, prob.p0)
     t = time.perf_counter()
     o.step(1)
@@ -196,8 +213,6 @@ def run_reference(args):
     from paper_1608_01906_gb300 import configs
 
     orc.build()
-    from oracle.oracle import Oracle, Params
-
     full = workload(args.workload)
     # each step: one oracle time step of a bounded sample of the same workload
     # (same physics on a smaller mesh)
@@ -210,12 +225,16 @@ def run_reference(args):
         samp = configs.c2_unstructured_droplet(n=64, R=12.0)
         sample = ("oracle (FP64 C, 1 thread) time step of a 64x64 jittered Delaunay droplet "
                   "with the physics of the 256x256 case (4,096 nodes) per step")
+    elif args.workload == "droplet3d_64x64x64":
+        samp = configs.droplet_3d(16)
+        sample = ("3-D oracle (FP64 C, 1 thread) time step of a 16^3 tetrahedral droplet with "
+                  "the physics of the 64^3 case (4,096 nodes) per step")
     else:
         samp = configs.c3_rayleigh_taylor(nx=64, ny=256)
         samp.params["gravity"] = full.params["gravity"]
         sample = ("oracle (FP64 C, 1 thread) time step on a 64x256 window of the 512x2048 "
                   "Rayleigh-Taylor problem (16,384 nodes) per step")
-    o = Oracle(samp.xy, samp.tri, samp.box, samp.tag, Params(**samp.params))
+    o = make_oracle(samp)
     o.init(samp.rho0, samp.u0, samp.p0)
     o.step(args.warmup)
     t = time.perf_counter()
@@ -361,7 +380,9 @@ def main():
     dom_name, (dom_ms, dom_timed, _) = dom
     dom_avg_ms = dom_ms / max(dom_timed, 1)
     peak, peak_kind = hbm_peak()
-    algo = ALGO_BYTES_PER_NODE[args.precision] * prob.n_nodes
+    dim = int(np.shape(prob.xy)[1])
+    # 2 x Q populations per node, read once and written once
+    algo = ALGO_BYTES_PER_NODE[args.precision] * (19 if dim == 3 else 9) // 9 * prob.n_nodes
     achieved = algo / (dom_avg_ms * 1e-3) / 1e9
     traffic = None
     tr_path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -399,8 +420,8 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_val = world * prob.n_nodes * args.steps / float(t.item()) / 1e6
     n = prob.n_nodes
-    h2d = (n * 8 + 2 * n * 8 + n * 8) / args.steps
-    d2h = (5 * n * 8 + 3 * 8) / args.steps
+    h2d = (n * 8 + dim * n * 8 + n * 8) / args.steps          # rho0, u0, p0
+    d2h = ((3 + dim) * n * 8 + (1 + dim) * 8) / args.steps  # rho, C, u, p, totals
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -114,6 +114,18 @@ def c3_rayleigh_taylor(nx=512, ny=2048, steps=20000, Re=3000.0, uref=0.08):
                    {"nx": nx, "ny": ny, "Re": Re, "At": 0.5, "g": g, "nu": nu})
 
 
+def droplet_3d(n=64, R=None, ratio=10.0, xi=4.0, sigma=0.01, tau_l=0.5, tau_v=0.5, dt=0.5,
+               steps=0, precision="fp32", name=None):
+    """Periodic n^3 cube of Kuhn-split tetrahedra (D3Q19, the paper's own
+    setting) with a spherical drop of radius R (default n/4) at rest."""
+    R = n / 4.0 if R is None else R
+    xyz, tet, box, _ = inputs.structured_tet_mesh(n, n, n)
+    rho0, u0, p0 = inputs.droplet_fields3(xyz, box, (n / 2, n / 2, n / 2), R, 1.0, 1.0 / ratio, xi)
+    return Problem(name or "droplet3d_%d" % n, xyz, tet, box, None, rho0, u0, p0,
+                   params(1.0, 1.0 / ratio, sigma, xi, tau_l, tau_v, dt, (0.0, 0.0, 0.0)), steps,
+                   precision, {"n": n, "R": R, "ratio": ratio})
+
+
 DROPLET_XI = 24.0
 
 
