@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
+    ap.add_argument("--general", action="store_true",
+                    help="force the general CSR kernels on a structured mesh")
     ap.add_argument("--serve-requests", type=int, default=40)
     ap.add_argument("--workload", default="rayleigh_taylor_512x2048",
                     choices=["rayleigh_taylor_512x2048", "droplet_2048x2048",
@@ -343,7 +345,8 @@ def main():
 
     prob = workload(args.workload)
     stream = torch.cuda.Stream()
-    mesh = felbm.Mesh(prob.xy, prob.tri, prob.box, prob.tag, stream=stream.cuda_stream)
+    mesh = felbm.Mesh(prob.xy, prob.tri, prob.box, prob.tag, general=args.general,
+                      stream=stream.cuda_stream)
     params = felbm.make_params(precision=args.precision, **prob.params)
     st = felbm.State(mesh, params, prob.rho0, prob.u0, prob.p0)
     st.step(args.warmup)

@@ -454,7 +454,7 @@ int felbm_state_init(const felbm_mesh *mesh, const felbm_params *params, const d
                      const double *u0, const double *p0, felbm_state **out) {
     if (!mesh || !params || !rho0 || !out) return FELBM_ERR_INVALID_ARG;
     if (!params_ok(params)) return FELBM_ERR_INVALID_ARG;
-    if (mesh->kind == 2) return state_init3(mesh, params, rho0, u0, p0, out);
+    if (mesh->kind >= 2) return state_init3(mesh, params, rho0, u0, p0, out);
     const size_t N = (size_t)mesh->n_nodes;
     for (size_t i = 0; i < N; ++i)
         if (!(rho0[i] > 0.0) || !std::isfinite(rho0[i])) return FELBM_ERR_INVALID_ARG;
@@ -525,7 +525,7 @@ int felbm_state_init(const felbm_mesh *mesh, const felbm_params *params, const d
 int felbm_step(felbm_state *s, int64_t n_steps) {
     if (!s || n_steps < 0) return FELBM_ERR_INVALID_ARG;
     if (n_steps == 0) return FELBM_OK;
-    if (s->mesh->kind == 2)
+    if (s->mesh->kind >= 2)
         steps3(s, n_steps);
     else if (s->esize == 8)
         do_steps<double>(s, n_steps);
@@ -552,7 +552,7 @@ int felbm_state_sync(felbm_state *s) {
 int felbm_moments_get(felbm_state *s, double *rho, double *C, double *u, double *p, double totals[3]) {
     if (!s) return FELBM_ERR_INVALID_ARG;
     if (!s->have_moments) return FELBM_ERR_INVALID_ARG;
-    if (s->mesh->kind == 2) {
+    if (s->mesh->kind >= 2) {
         const int st3 = moments3(s, rho, C, u, p, totals);
         return st3 != FELBM_OK ? st3 : check_flag(s);
     }
@@ -576,7 +576,7 @@ int felbm_moments_get(felbm_state *s, double *rho, double *C, double *u, double 
 
 int felbm_state_export(felbm_state *s, double *hbar, double *gbar) {
     if (!s || !hbar || !gbar) return FELBM_ERR_INVALID_ARG;
-    if (s->mesh->kind == 2) {
+    if (s->mesh->kind >= 2) {
         const int st3 = export3(s, hbar, gbar);
         return st3 != FELBM_OK ? st3 : check_flag(s);
     }
@@ -600,7 +600,7 @@ int felbm_state_export(felbm_state *s, double *hbar, double *gbar) {
 
 int felbm_state_import(felbm_state *s, const double *hbar, const double *gbar) {
     if (!s || !hbar || !gbar) return FELBM_ERR_INVALID_ARG;
-    if (s->mesh->kind == 2) return import3(s, hbar, gbar);
+    if (s->mesh->kind >= 2) return import3(s, hbar, gbar);
     const size_t N = (size_t)s->mesh->n_nodes, es = s->esize, S = pop_slots(s->mesh);
     std::vector<unsigned char> buf(18 * pad4(S) * es, 0);
     const bool perm = s->mesh->kind == 0;

@@ -1,7 +1,9 @@
-// C ABI on tetrahedral meshes (kind 2, D3Q19): mesh creation and the
-// per-state work the common entry points of felbm_api.cu hand over here.
+// C ABI on tetrahedral meshes (D3Q19; kind 2 general CSR, kind 3 Kuhn
+// lattice): mesh creation and the per-state work the common entry points of
+// felbm_api.cu hand over here.
 #include <cmath>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "felbm_internal.h"
@@ -38,6 +40,33 @@ static DevCSR3<T> dev_csr3(const felbm_mesh *m) {
 }
 
 template <typename T>
+static DevLattice3<T> dev_lat3(const felbm_mesh *m, double dt) {
+    const Lattice3Info &L = m->linfo3;
+    DevLattice3<T> d;
+    d.n = (int32_t)m->n_nodes;
+    d.nx = L.nx;
+    d.ny = L.ny;
+    d.nz = L.nz;
+    d.walls = L.walls ? 1 : 0;
+    const double hdt = 0.5 * dt;
+    for (int k = 0; k < 3; ++k)
+        for (int o = 0; o < 14; ++o) {
+            const double *cf = L.c[k][o];
+            for (int q = 0; q < 9; ++q) {
+                const int a = 2 * q + 1;
+                const double ex = e3x(a), ey = e3y(a), ez = e3z(a);
+                const double odd = ex * cf[0] + ey * cf[1] + ez * cf[2];
+                const double even = hdt * ((ex * ex * cf[3] + ey * ey * cf[6] + ez * ez * cf[8]) +
+                                           2.0 * (ex * ey * cf[4] + ex * ez * cf[5] + ey * ez * cf[7]));
+                d.k.pc[k][o][q].x = (T)(even + odd);
+                d.k.pc[k][o][q].y = (T)(even - odd);
+            }
+            for (int c = 0; c < 3; ++c) d.k.a[k][o][c] = (T)cf[c];
+        }
+    return d;
+}
+
+template <typename T>
 static Phys3<T> phys3_of(const felbm_params &p) {
     const double dd = p.rho_l - p.rho_v;
     Phys3<T> P;
@@ -67,41 +96,51 @@ static Fields3<T> fields3_of(felbm_state *s) {
 }
 
 // grad rho, then lap rho, K and mu, from F.rho.
-template <typename T>
-static void chain3(felbm_state *s, const DevCSR3<T> &d, const Fields3<T> &F, const Phys3<T> &P) {
+template <typename T, typename Topo>
+static void chain3(felbm_state *s, const Topo &d, const Fields3<T> &F, const Phys3<T> &P) {
     const felbm_mesh *m = s->mesh;
     const unsigned g = nblocks3(m->n_nodes, 256);
     int sl = prof_begin(s, 1);
-    k_grad3<T><<<g, 256, 0, m->stream>>>(d, F);
+    k_grad3<T, Topo><<<g, 256, 0, m->stream>>>(d, F);
     prof_end(s, sl);
     sl = prof_begin(s, 2);
-    k_mu3<T><<<g, 256, 0, m->stream>>>(d, F, P);
+    k_mu3<T, Topo><<<g, 256, 0, m->stream>>>(d, F, P);
     prof_end(s, sl);
+}
+
+// Calls fn(topology) with the device view of the state's mesh.
+template <typename T, typename Fn>
+static void with_topo(felbm_state *s, Fn &&fn) {
+    if (s->mesh->kind == 3)
+        fn(dev_lat3<T>(s->mesh, s->params.dt));
+    else
+        fn(dev_csr3<T>(s->mesh));
 }
 
 template <typename T>
 static void init3(felbm_state *s) {
-    const felbm_mesh *m = s->mesh;
-    const DevCSR3<T> d = dev_csr3<T>(m);
-    const Fields3<T> F = fields3_of<T>(s);
-    const Phys3<T> P = phys3_of<T>(s->params);
-    cudaMemcpyAsync(F.rho, s->mom, (size_t)m->n_nodes * sizeof(T), cudaMemcpyDeviceToDevice, m->stream);
-    chain3<T>(s, d, F, P);
-    k_init3<T><<<nblocks3(m->n_nodes, 128), 128, 0, m->stream>>>(
-        d, reinterpret_cast<T *>(s->f[s->cur]), F, P, reinterpret_cast<const T *>(s->mom));
+    with_topo<T>(s, [&](const auto &d) {
+        using Topo = std::decay_t<decltype(d)>;
+        const felbm_mesh *m = s->mesh;
+        const Fields3<T> F = fields3_of<T>(s);
+        const Phys3<T> P = phys3_of<T>(s->params);
+        cudaMemcpyAsync(F.rho, s->mom, (size_t)m->n_nodes * sizeof(T), cudaMemcpyDeviceToDevice, m->stream);
+        chain3<T>(s, d, F, P);
+        k_init3<T, Topo><<<nblocks3(m->n_nodes, 128), 128, 0, m->stream>>>(
+            d, reinterpret_cast<T *>(s->f[s->cur]), F, P, reinterpret_cast<const T *>(s->mom));
+    });
 }
 
-template <typename T>
-static void step3(felbm_state *s, const DevCSR3<T> &d, const Fields3<T> &F, const Phys3<T> &P,
-                  bool write_mom) {
+template <typename T, typename Topo>
+static void step3(felbm_state *s, const Topo &d, const Fields3<T> &F, const Phys3<T> &P, bool write_mom) {
     const felbm_mesh *m = s->mesh;
     const T *fin = reinterpret_cast<const T *>(s->f[s->cur]);
     T *fout = reinterpret_cast<T *>(s->f[s->cur ^ 1]);
     int sl = prof_begin(s, 0);
-    k_rho3<T><<<nblocks3(m->n_nodes, 256), 256, 0, m->stream>>>(d, fin, P.dt, F.rho);
+    k_rho3<T, Topo><<<nblocks3(m->n_nodes, 256), 256, 0, m->stream>>>(d, fin, P.dt, F.rho);
     prof_end(s, sl);
     chain3<T>(s, d, F, P);
-    Collide3Args<T> A;
+    Collide3Args<T, Topo> A;
     A.m = d;
     A.fin = fin;
     A.fout = fout;
@@ -110,17 +149,18 @@ static void step3(felbm_state *s, const DevCSR3<T> &d, const Fields3<T> &F, cons
     A.mom = write_mom ? reinterpret_cast<T *>(s->mom) : nullptr;
     A.flag = s->d_flag;
     sl = prof_begin(s, 3);
-    k_collide3<T><<<nblocks3(m->n_nodes, 128), 128, 0, m->stream>>>(A);
+    k_collide3<T, Topo><<<nblocks3(m->n_nodes, 128), 128, 0, m->stream>>>(A);
     prof_end(s, sl);
     s->cur ^= 1;
 }
 
 template <typename T>
 static void steps3_t(felbm_state *s, int64_t n) {
-    const DevCSR3<T> d = dev_csr3<T>(s->mesh);
-    const Fields3<T> F = fields3_of<T>(s);
-    const Phys3<T> P = phys3_of<T>(s->params);
-    for (int64_t k = 0; k < n; ++k) step3<T>(s, d, F, P, k == n - 1);
+    with_topo<T>(s, [&](const auto &d) {
+        const Fields3<T> F = fields3_of<T>(s);
+        const Phys3<T> P = phys3_of<T>(s->params);
+        for (int64_t k = 0; k < n; ++k) step3<T>(s, d, F, P, k == n - 1);
+    });
 }
 
 void steps3(felbm_state *s, int64_t n) {
@@ -278,7 +318,8 @@ extern "C" int felbm_mesh_create_tet(const double *xyz, int64_t n_nodes, const i
     if (!xyz || !tet || !box || !out) return FELBM_ERR_INVALID_ARG;
     if (n_nodes < 4 || n_tet < 1 || n_nodes > 0x7fffffffLL || n_tet > 0x7fffffffLL / 4)
         return FELBM_ERR_INVALID_ARG;
-    if (flags & ~(FELBM_PERIODIC_X | FELBM_PERIODIC_Y | FELBM_PERIODIC_Z)) return FELBM_ERR_INVALID_ARG;
+    if (flags & ~(FELBM_PERIODIC_X | FELBM_PERIODIC_Y | FELBM_PERIODIC_Z | FELBM_MESH_GENERAL))
+        return FELBM_ERR_INVALID_ARG;
     felbm_mesh *m = new (std::nothrow) felbm_mesh();
     if (!m) return FELBM_ERR_OOM;
     m->n_nodes = n_nodes;
@@ -296,7 +337,22 @@ extern "C" int felbm_mesh_create_tet(const double *xyz, int64_t n_nodes, const i
         delete m;
         return st;
     }
-    const HostCSR3 &H = m->host3;
+    HostCSR3 &H = m->host3;
+    if (!(flags & FELBM_MESH_GENERAL)) detect_lattice3(xyz, n_nodes, box, flags, node_tag, H, m->linfo3);
+    if (m->linfo3.ok) {
+        // the lattice kernels take neighbours and coefficients from the node
+        // position: natural order, no assembled arrays on the device
+        m->kind = 3;
+        std::vector<double> mass(H.n);
+        for (int32_t c = 0; c < H.n; ++c) {
+            mass[c] = H.mass[H.iperm[c]];
+            H.perm[c] = H.iperm[c] = c;
+        }
+        H.mass.swap(mass);
+        std::vector<int32_t>().swap(H.col);
+        std::vector<double>().swap(H.coef);
+        std::vector<uint8_t>().swap(H.tag);
+    }
     const size_t N = (size_t)n_nodes, nnz = H.col.size();
     cudaError_t e = cudaSuccess;
     auto alloc = [&](void **p, size_t bytes) {
@@ -305,13 +361,16 @@ extern "C" int felbm_mesh_create_tet(const double *xyz, int64_t n_nodes, const i
             if (e == cudaSuccess) m->device_bytes += (int64_t)bytes;
         }
     };
+    const bool csr = m->kind == 2;
     alloc((void **)&m->d_mass, N * sizeof(double));
-    alloc((void **)&m->d_rowptr, (N + 1) * sizeof(int32_t));
-    alloc((void **)&m->d_col, nnz * sizeof(int32_t));
     alloc((void **)&m->d_perm, 2 * N * sizeof(int32_t));
-    alloc((void **)&m->d_coef64, 9 * nnz * sizeof(double));
-    alloc((void **)&m->d_coef32, 9 * nnz * sizeof(float));
-    if (!H.tag.empty()) alloc((void **)&m->d_tag, N);
+    if (csr) {
+        alloc((void **)&m->d_rowptr, (N + 1) * sizeof(int32_t));
+        alloc((void **)&m->d_col, nnz * sizeof(int32_t));
+        alloc((void **)&m->d_coef64, 9 * nnz * sizeof(double));
+        alloc((void **)&m->d_coef32, 9 * nnz * sizeof(float));
+        if (!H.tag.empty()) alloc((void **)&m->d_tag, N);
+    }
     std::vector<float> c32;
     try {
         c32.resize(9 * nnz);
@@ -320,15 +379,17 @@ extern "C" int felbm_mesh_create_tet(const double *xyz, int64_t n_nodes, const i
     }
     for (size_t q = 0; q < c32.size(); ++q) c32[q] = (float)H.coef[q];
     if (e == cudaSuccess) e = cudaMemcpy(m->d_mass, H.mass.data(), N * sizeof(double), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && csr)
         e = cudaMemcpy(m->d_rowptr, H.rowptr.data(), (N + 1) * sizeof(int32_t), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(m->d_col, H.col.data(), nnz * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && csr)
+        e = cudaMemcpy(m->d_col, H.col.data(), nnz * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(m->d_perm, H.perm.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(m->d_perm + N, H.iperm.data(), N * sizeof(int32_t), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && csr)
         e = cudaMemcpy(m->d_coef64, H.coef.data(), 9 * nnz * sizeof(double), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(m->d_coef32, c32.data(), 9 * nnz * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && csr)
+        e = cudaMemcpy(m->d_coef32, c32.data(), 9 * nnz * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && m->d_tag) e = cudaMemcpy(m->d_tag, H.tag.data(), N, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         const int rs = cuda_status(e);

@@ -43,6 +43,39 @@ struct HostCSR3 {
     std::vector<int32_t> iperm;    // iperm[caller] = internal id
 };
 
+// Kuhn-split cube lattice (3-D): node i = x + nx (y + ny z) at (x, y, z) h,
+// every cube cut into the six tetrahedra around its (0,0,0)-(1,1,1)
+// diagonal, periodic in x and y, periodic in z or walled (tags 5 on z = 0,
+// 6 on z = nz - 1).  The 14 neighbour offsets are lat3_d*(o); c holds the
+// assembled coefficients (HostCSR3 order) per z-layer kind (0 interior, 1
+// bottom wall layer, 2 top wall layer) and offset, zero where the offset
+// leaves a walled domain.
+struct Lattice3Info {
+    bool ok = false;
+    int32_t nx = 0, ny = 0, nz = 0;
+    bool walls = false;
+    double c[3][14][9];
+};
+
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+constexpr int lat3_dx(int o) {
+    return (o == 0 || o == 6 || o == 8 || o == 12) ? 1 : (o == 1 || o == 7 || o == 9 || o == 13) ? -1 : 0;
+}
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+constexpr int lat3_dy(int o) {
+    return (o == 2 || o == 6 || o == 10 || o == 12) ? 1 : (o == 3 || o == 7 || o == 11 || o == 13) ? -1 : 0;
+}
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+constexpr int lat3_dz(int o) {
+    return (o == 4 || o == 8 || o == 10 || o == 12) ? 1 : (o == 5 || o == 9 || o == 11 || o == 13) ? -1 : 0;
+}
+
 struct StructuredInfo {
     bool ok = false;
     int32_t nx = 0, ny = 0;
@@ -60,6 +93,10 @@ int build_csr(const double *xy, int64_t n_nodes, const int32_t *tri, int64_t n_t
 // Tetrahedral mesh: validation, geometry, assembly, RCM (felbm_mesh3.cu).
 int build_csr3(const double *xyz, int64_t n_nodes, const int32_t *tet, int64_t n_tet,
                const double box[3], uint32_t flags, const uint8_t *tag, HostCSR3 &out);
+// Recognise the Kuhn lattice in an assembled tetrahedral mesh (H in RCM
+// order); on success fills info (felbm_mesh3.cu).
+void detect_lattice3(const double *xyz, int64_t n_nodes, const double box[3], uint32_t flags,
+                     const uint8_t *tag, const HostCSR3 &H, Lattice3Info &info);
 // Reverse Cuthill-McKee order of a node graph given as CSR without self loops.
 std::vector<int32_t> rcm_order(int32_t n, const std::vector<int32_t> &rp,
                                const std::vector<int32_t> &cl);
@@ -213,9 +250,10 @@ struct felbm_mesh {
     int64_t n_nodes = 0, n_tri = 0;
     uint32_t flags = 0;
     cudaStream_t stream = nullptr;
-    int kind = 0;  // 0 general triangles, 1 structured triangles, 2 general tetrahedra
+    int kind = 0;  // 0 general triangles, 1 structured triangles, 2 general tetrahedra, 3 tet lattice
     felbm::HostCSR host;
     felbm::HostCSR3 host3;
+    felbm::Lattice3Info linfo3;
     felbm::StructuredInfo sinfo;
     // device arrays
     int32_t *d_rowptr = nullptr, *d_col = nullptr, *d_perm = nullptr;
@@ -228,8 +266,8 @@ struct felbm_mesh {
 
 // Population slots per array of a state on mesh m, and the slot of node i
 // (internal order).
-inline int mesh_dim(const felbm_mesh *m) { return m->kind == 2 ? 3 : 2; }
-inline int mesh_q(const felbm_mesh *m) { return m->kind == 2 ? 19 : 9; }
+inline int mesh_dim(const felbm_mesh *m) { return m->kind >= 2 ? 3 : 2; }
+inline int mesh_q(const felbm_mesh *m) { return m->kind >= 2 ? 19 : 9; }
 inline size_t pop_slots(const felbm_mesh *m) {
     return m->kind == 1 ? (size_t)m->sinfo.pitch * (size_t)m->sinfo.ny : (size_t)m->n_nodes;
 }

@@ -1,5 +1,6 @@
 // Device kernels of one FE-LBM time step on tetrahedral meshes (D3Q19, the
-// paper's own setting), general CSR path.  Same four dependent passes as the
+// paper's own setting), on two topologies: the general CSR (DevCSR3) and the
+// Kuhn-split cube lattice (DevLattice3).  Same four dependent passes as the
 // two-dimensional general path (felbm_kernels.cuh):
 //   k_rho3      Taylor-Galerkin streaming of the 19 h populations (Sec.
 //               2.2.1, lumped mass), wall bounce-back, rho = sum_a h_a;
@@ -14,6 +15,8 @@
 // 0..8); the populations are stored as the rest value plus 9 interleaved
 // opposite pairs (pop layout of felbm_internal.h with 19 per distribution).
 #pragma once
+
+#include <type_traits>
 
 #include "felbm_internal.h"
 #include "felbm_kernels.cuh"
@@ -52,15 +55,21 @@ __device__ __forceinline__ T mu_bulk3(const Phys3<T> &P, T r) {
 
 // General tetrahedral mesh: CSR in reverse Cuthill-McKee order with the
 // coefficient arrays of HostCSR3 (a: 3, b: 6 symmetric components).
+// Both topologies give, for node i, the neighbours j with their
+// coefficients: for_each<K>(i, fn(j, a)) with a = (a_x, a_y, a_z) at least,
+// for_each_pair<K>(i, dt/2, fn(j, c)) with c[q] = (e.a + dt/2 e.b.e) for the
+// pair q = (2q+1, 2q+2) as (first, second) = (even + odd, even - odd) parts.
+// K >= 0 promises that node i is of z-layer kind K (lattice only; -1 = any).
 template <typename T>
 struct DevCSR3 {
+    static constexpr bool kLattice = false;
     int32_t n;
     const int32_t *rowptr;
     const int32_t *col;
     const T *c[9];       // ax, ay, az, bxx, bxy, bxz, byy, byz, bzz (nnz each)
     const uint8_t *tag;  // nullptr if no walls
 #ifdef __CUDACC__
-    template <typename Fn>
+    template <int K, typename Fn>
     __device__ __forceinline__ void for_each(int32_t i, Fn &&fn) const {
         const int32_t p1 = __ldg(rowptr + i + 1);
         for (int32_t p = __ldg(rowptr + i); p < p1; ++p) {
@@ -70,9 +79,110 @@ struct DevCSR3 {
             fn(__ldg(col + p), cf);
         }
     }
+    template <int K, typename Fn>
+    __device__ __forceinline__ void for_each_pair(int32_t i, T hdt, Fn &&fn) const {
+        for_each<K>(i, [&](int32_t j, const T *cf) {
+            V2<T> c[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) {
+                const int a = 2 * q + 1;
+                const T ex = T(e3x(a)), ey = T(e3y(a)), ez = T(e3z(a));
+                const T odd = ex * cf[0] + ey * cf[1] + ez * cf[2];
+                const T even = hdt * ((ex * ex * cf[3] + ey * ey * cf[6] + ez * ez * cf[8]) +
+                                      T(2) * (ex * ey * cf[4] + ex * ez * cf[5] + ey * ez * cf[7]));
+                c[q] = vset(even + odd, even - odd);
+            }
+            fn(j, c);
+        });
+    }
+    __device__ __forceinline__ int kind_of(int32_t) const { return -1; }
     __device__ __forceinline__ int tag_of(int32_t i) const { return tag ? (int)tag[i] : 0; }
 #endif
 };
+
+// Coefficients of the Kuhn lattice per z-layer kind (0 interior, 1 bottom
+// wall layer, 2 top wall layer) and neighbour offset o (lat3_d*(o)), passed
+// as kernel parameters: the pair form of the streaming coefficients with
+// dt/2 folded in, and the recovery coefficients a_ij.
+template <typename T>
+struct Lat3Coef {
+    V2<T> pc[3][14][9];
+    T a[3][14][3];
+};
+
+// Kuhn-split cube lattice in natural order (i = x + nx (y + ny z)): the 14
+// neighbour ids follow from the node's position; a walled z direction has
+// tags 5 (bottom layer, inward normal +z) and 6 (top layer).
+template <typename T>
+struct DevLattice3 {
+    static constexpr bool kLattice = true;
+    int32_t n, nx, ny, nz;
+    int32_t walls;
+    Lat3Coef<T> k;
+#ifdef __CUDACC__
+    __device__ __forceinline__ int kind_of(int32_t i) const {
+        if (!walls) return 0;
+        const int32_t z = i / (nx * ny);
+        return z == 0 ? 1 : (z == nz - 1 ? 2 : 0);
+    }
+    __device__ __forceinline__ int tag_of(int32_t i) const {
+        const int kd = kind_of(i);
+        return kd == 0 ? 0 : 4 + kd;
+    }
+    // Where an offset leaves a walled domain its coefficients are zero and
+    // the id is an in-range stand-in (the wrapped x-y neighbour in-layer).
+    __device__ __forceinline__ void nbrs(int32_t i, int32_t *j) const {
+        const int32_t L = nx * ny;
+        const int32_t z = i / L, r = i - z * L, y = r / nx, x = r - y * nx;
+        const int32_t xp = x == nx - 1 ? 1 - nx : 1, xm = x == 0 ? nx - 1 : -1;
+        const int32_t yp = (y == ny - 1 ? 1 - ny : 1) * nx, ym = (y == 0 ? ny - 1 : -1) * nx;
+        int32_t zp, zm;
+        if (walls) {
+            zp = z == nz - 1 ? 0 : L;
+            zm = z == 0 ? 0 : -L;
+        } else {
+            zp = (z == nz - 1 ? 1 - nz : 1) * L;
+            zm = (z == 0 ? nz - 1 : -1) * L;
+        }
+#pragma unroll
+        for (int o = 0; o < 14; ++o)
+            j[o] = i + (lat3_dx(o) > 0 ? xp : (lat3_dx(o) < 0 ? xm : 0)) +
+                   (lat3_dy(o) > 0 ? yp : (lat3_dy(o) < 0 ? ym : 0)) +
+                   (lat3_dz(o) > 0 ? zp : (lat3_dz(o) < 0 ? zm : 0));
+    }
+    template <int K, typename Fn>
+    __device__ __forceinline__ void for_each(int32_t i, Fn &&fn) const {
+        int32_t j[14];
+        nbrs(i, j);
+        const int kd = K >= 0 ? K : kind_of(i);
+#pragma unroll
+        for (int o = 0; o < 14; ++o) fn(j[o], k.a[kd][o]);
+    }
+    template <int K, typename Fn>
+    __device__ __forceinline__ void for_each_pair(int32_t i, T, Fn &&fn) const {
+        int32_t j[14];
+        nbrs(i, j);
+        const int kd = K >= 0 ? K : kind_of(i);
+#pragma unroll
+        for (int o = 0; o < 14; ++o) fn(j[o], k.pc[kd][o]);
+    }
+#endif
+};
+
+#ifdef __CUDACC__
+// Runs fn(integral_constant<K>) with K = 0 for interior lattice nodes (the
+// coefficients are then compile-time parameter offsets) and K = -1 otherwise.
+template <typename Topo, typename Fn>
+__device__ __forceinline__ void by_kind(const Topo &m, int32_t i, Fn &&fn) {
+    if constexpr (Topo::kLattice) {
+        if (m.kind_of(i) == 0) {
+            fn(std::integral_constant<int, 0>());
+            return;
+        }
+    }
+    fn(std::integral_constant<int, -1>());
+}
+#endif
 
 // Scalar fields of one time level (N each): rho, grad rho, mu, K.
 template <typename T>
@@ -82,9 +192,9 @@ struct Fields3 {
 
 // Streamed values of the 9 pairs of h (G = 0) or h and g (G = 1) of node i:
 // psi* = psi - dt sum_j (e.a_ij + dt/2 e.b_ij.e) (psi_j - psi_i).
-template <typename T, bool G>
-__device__ __forceinline__ void stream_pairs3(const DevCSR3<T> &m, const T *__restrict__ f, size_t np,
-                                              int32_t i, T dt, V2<T> *hp, V2<T> *gp) {
+template <typename T, bool G, int K, typename Topo>
+__device__ __forceinline__ void stream_pairs3(const Topo &m, const T *__restrict__ f, size_t np, int32_t i,
+                                              T dt, V2<T> *hp, V2<T> *gp) {
     const V2<T> *hb = reinterpret_cast<const V2<T> *>(f + np);
     const V2<T> *gb = reinterpret_cast<const V2<T> *>(f + 20 * np);
     const V2<T> m1 = vset(T(-1), T(-1));
@@ -98,18 +208,11 @@ __device__ __forceinline__ void stream_pairs3(const DevCSR3<T> &m, const T *__re
             ga[q] = vset(T(0), T(0));
         }
     }
-    const T hdt = T(0.5) * dt;
-    m.for_each(i, [&](int32_t j, const T *cf) {
+    m.template for_each_pair<K>(i, T(0.5) * dt, [&](int32_t j, const V2<T> *c) {
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
-            const int a = 2 * q + 1;
-            const T ex = T(e3x(a)), ey = T(e3y(a)), ez = T(e3z(a));
-            const T odd = ex * cf[0] + ey * cf[1] + ez * cf[2];
-            const T even = hdt * ((ex * ex * cf[3] + ey * ey * cf[6] + ez * ez * cf[8]) +
-                                  T(2) * (ex * ey * cf[4] + ex * ez * cf[5] + ey * ez * cf[7]));
-            const V2<T> c = vset(even + odd, even - odd);
-            ha[q] = vfma(c, vfma(hs[q], m1, __ldg(hb + q * np + j)), ha[q]);
-            if (G) ga[q] = vfma(c, vfma(gs[q], m1, __ldg(gb + q * np + j)), ga[q]);
+            ha[q] = vfma(c[q], vfma(hs[q], m1, __ldg(hb + q * np + j)), ha[q]);
+            if (G) ga[q] = vfma(c[q], vfma(gs[q], m1, __ldg(gb + q * np + j)), ga[q]);
         }
     });
     const V2<T> mdt = vset(-dt, -dt);
@@ -140,14 +243,14 @@ __device__ __forceinline__ void bounce_back3(int k, T *psi) {
         if (e3x(a) * kx + e3y(a) * ky + e3z(a) * kz > 0) psi[a] = psi[a % 2 ? a + 1 : a - 1];
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_rho3(DevCSR3<T> m, const T *__restrict__ f, T dt,
+template <typename T, typename Topo>
+__global__ void __launch_bounds__(256) k_rho3(const __grid_constant__ Topo m, const T *__restrict__ f, T dt,
                                               T *__restrict__ rho) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m.n) return;
     const size_t np = pad4((size_t)m.n);
     V2<T> hp[9];
-    stream_pairs3<T, false>(m, f, np, i, dt, hp, hp);
+    by_kind(m, i, [&](auto K) { stream_pairs3<T, false, decltype(K)::value>(m, f, np, i, dt, hp, hp); });
     T h[19];
     unpack3<T>(f[i], hp, h);
     const int k = m.tag_of(i);
@@ -159,11 +262,11 @@ __global__ void __launch_bounds__(256) k_rho3(DevCSR3<T> m, const T *__restrict_
 }
 
 // Recovered gradient of a scalar field (3 components).
-template <typename T>
-__device__ __forceinline__ void recover3(const DevCSR3<T> &m, const T *__restrict__ f, int32_t i, T *g) {
+template <typename T, int K, typename Topo>
+__device__ __forceinline__ void recover3(const Topo &m, const T *__restrict__ f, int32_t i, T *g) {
     const T fi = f[i];
     T s0 = T(0), s1 = T(0), s2 = T(0);
-    m.for_each(i, [&](int32_t j, const T *cf) {
+    m.template for_each<K>(i, [&](int32_t j, const T *cf) {
         const T d = __ldg(f + j) - fi;
         s0 += cf[0] * d;
         s1 += cf[1] * d;
@@ -174,12 +277,12 @@ __device__ __forceinline__ void recover3(const DevCSR3<T> &m, const T *__restric
     g[2] = s2;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_grad3(DevCSR3<T> m, Fields3<T> F) {
+template <typename T, typename Topo>
+__global__ void __launch_bounds__(256) k_grad3(const __grid_constant__ Topo m, Fields3<T> F) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m.n) return;
     T g[3];
-    recover3<T>(m, F.rho, i, g);
+    by_kind(m, i, [&](auto K) { recover3<T, decltype(K)::value>(m, F.rho, i, g); });
 #pragma unroll
     for (int c = 0; c < 3; ++c) F.dr[c][i] = g[c];
 }
@@ -188,15 +291,10 @@ __global__ void __launch_bounds__(256) k_grad3(DevCSR3<T> m, Fields3<T> F) {
 // K_i = kappa [sum_{k != i} R_i((d_k rho)^2) - sum_{j != i} R_j(d_i rho d_j rho)]
 // (the printed form with the identical (d_i rho)^2 contributions cancelled);
 // differences of the products in product form.
-template <typename T>
-__global__ void __launch_bounds__(256) k_mu3(DevCSR3<T> m, Fields3<T> F, Phys3<T> P) {
-    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m.n) return;
-    T gi[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) gi[c] = F.dr[c][i];
-    T lap = T(0), K[3] = {T(0), T(0), T(0)};
-    m.for_each(i, [&](int32_t j, const T *cf) {
+template <typename T, int K, typename Topo>
+__device__ __forceinline__ void mu_sums3(const Topo &m, const Fields3<T> &F, int32_t i, const T *gi, T &lap,
+                                         T *K3) {
+    m.template for_each<K>(i, [&](int32_t j, const T *cf) {
         T gj[3], d[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -216,9 +314,20 @@ __global__ void __launch_bounds__(256) k_mu3(DevCSR3<T> m, Fields3<T> F, Phys3<T
                 const T dab = gj[a] * d[b] + gi[b] * d[a];  // difference of d_a rho d_b rho
                 acc += cf[a] * sq[b] - cf[b] * dab;
             }
-            K[a] += acc;
+            K3[a] += acc;
         }
     });
+}
+
+template <typename T, typename Topo>
+__global__ void __launch_bounds__(256) k_mu3(const __grid_constant__ Topo m, Fields3<T> F, Phys3<T> P) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m.n) return;
+    T gi[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) gi[c] = F.dr[c][i];
+    T lap = T(0), K[3] = {T(0), T(0), T(0)};
+    by_kind(m, i, [&](auto KD) { mu_sums3<T, decltype(KD)::value>(m, F, i, gi, lap, K); });
     F.mu[i] = mu_bulk3<T>(P, F.rho[i]) - P.kappa * lap;
 #pragma unroll
     for (int c = 0; c < 3; ++c) F.k[c][i] = P.kappa * K[c];
@@ -288,9 +397,9 @@ __device__ __forceinline__ void collide_pop3(const Prep3<T> &c, int a, T hs, T g
     gout = gs + (c.omw * dg + c.opw * (Ga + Ba));
 }
 
-template <typename T>
+template <typename T, typename Topo>
 struct Collide3Args {
-    DevCSR3<T> m;
+    Topo m;
     const T *fin;
     T *fout;
     Fields3<T> F;
@@ -299,18 +408,20 @@ struct Collide3Args {
     int *flag;
 };
 
-template <typename T>
-__global__ void __launch_bounds__(128) k_collide3(Collide3Args<T> A) {
+template <typename T, typename Topo>
+__global__ void __launch_bounds__(128) k_collide3(const __grid_constant__ Collide3Args<T, Topo> A) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    const DevCSR3<T> &m = A.m;
+    const Topo &m = A.m;
     if (i >= m.n) return;
     const size_t n = (size_t)m.n, np = pad4(n);
     T dm[3];
-    recover3<T>(m, A.F.mu, i, dm);
     T hs[19], gs[19];
     {
         V2<T> hp[9], gp[9];
-        stream_pairs3<T, true>(m, A.fin, np, i, A.P.dt, hp, gp);
+        by_kind(m, i, [&](auto K) {
+            recover3<T, decltype(K)::value>(m, A.F.mu, i, dm);
+            stream_pairs3<T, true, decltype(K)::value>(m, A.fin, np, i, A.P.dt, hp, gp);
+        });
         unpack3<T>(A.fin[i], hp, hs);
         unpack3<T>(A.fin[19 * np + i], gp, gs);
     }
@@ -370,14 +481,14 @@ __global__ void __launch_bounds__(128) k_collide3(Collide3Args<T> A) {
 }
 
 // Initial pre-collided state psibar = eq + S of (rho, u, p) in mom.
-template <typename T>
-__global__ void __launch_bounds__(128) k_init3(DevCSR3<T> m, T *__restrict__ fout, Fields3<T> F,
-                                               Phys3<T> P, const T *__restrict__ mom) {
+template <typename T, typename Topo>
+__global__ void __launch_bounds__(128) k_init3(const __grid_constant__ Topo m, T *__restrict__ fout,
+                                               Fields3<T> F, Phys3<T> P, const T *__restrict__ mom) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m.n) return;
     const size_t n = (size_t)m.n, np = pad4(n);
     T dm[3], dr[3], K[3];
-    recover3<T>(m, F.mu, i, dm);
+    by_kind(m, i, [&](auto KD) { recover3<T, decltype(KD)::value>(m, F.mu, i, dm); });
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         dr[c] = F.dr[c][i];

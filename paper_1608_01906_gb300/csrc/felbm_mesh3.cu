@@ -170,3 +170,102 @@ int build_csr3(const double *xyz, int64_t n_nodes, const int32_t *tet, int64_t n
 }
 
 }  // namespace felbm
+
+namespace felbm {
+
+static int offset_index3(int dx, int dy, int dz) {
+    for (int o = 0; o < 14; ++o)
+        if (lat3_dx(o) == dx && lat3_dy(o) == dy && lat3_dz(o) == dz) return o;
+    return -1;
+}
+
+// The mesh is the Kuhn lattice when the nodes sit on an (nx, ny, nz) grid in
+// id order, the flags and tags are those of structured_tet_mesh (periodic x
+// and y, z periodic or walled by tags 5 and 6), every node's neighbours are
+// the 14 lattice offsets and every node's assembled coefficients equal those
+// of the first node of its z-layer kind (to 1e-12 of the largest).
+void detect_lattice3(const double *xyz, int64_t n_nodes, const double box[3], uint32_t flags,
+                     const uint8_t *tag, const HostCSR3 &H, Lattice3Info &info) {
+    info.ok = false;
+    if (!(flags & FELBM_PERIODIC_X) || !(flags & FELBM_PERIODIC_Y) || n_nodes < 27) return;
+    const double h = xyz[3] - xyz[0];
+    if (!(h > 0.0)) return;
+    int64_t nx = 0;
+    while (nx < n_nodes && std::fabs(xyz[3 * nx + 1] - xyz[1]) <= 1e-12 * h &&
+           std::fabs(xyz[3 * nx + 2] - xyz[2]) <= 1e-12 * h)
+        ++nx;
+    int64_t layer = 0;
+    while (layer < n_nodes && std::fabs(xyz[3 * layer + 2] - xyz[2]) <= 1e-12 * h) ++layer;
+    if (nx < 3 || layer % nx || n_nodes % layer) return;
+    const int64_t ny = layer / nx, nz = n_nodes / layer;
+    if (ny < 3 || nz < 3 || nx > (1 << 20) || ny > (1 << 20) || nz > (1 << 20)) return;
+    const double tol = 1e-9 * h;
+    for (int64_t i = 0; i < n_nodes; ++i) {
+        const int64_t x = i % nx, y = (i / nx) % ny, z = i / layer;
+        if (std::fabs(xyz[3 * i] - (xyz[0] + x * h)) > tol || std::fabs(xyz[3 * i + 1] - (xyz[1] + y * h)) > tol ||
+            std::fabs(xyz[3 * i + 2] - (xyz[2] + z * h)) > tol)
+            return;
+    }
+    if (std::fabs(box[0] - nx * h) > tol || std::fabs(box[1] - ny * h) > tol) return;
+    const bool pz = (flags & FELBM_PERIODIC_Z) != 0;
+    if (pz && std::fabs(box[2] - nz * h) > tol) return;
+    if (!pz) {
+        if (!tag) return;
+        for (int64_t i = 0; i < n_nodes; ++i) {
+            const int64_t z = i / layer;
+            if (tag[i] != (z == 0 ? 5 : (z == nz - 1 ? 6 : 0))) return;
+        }
+    } else if (tag) {
+        for (int64_t i = 0; i < n_nodes; ++i)
+            if (tag[i]) return;
+    }
+    bool have[3] = {false, false, false};
+    int count[3] = {0, 0, 0};
+    double c[3][14][9] = {};
+    double cmax = 0.0;
+    for (double v : H.coef) cmax = std::max(cmax, std::fabs(v));
+    const size_t nnz = H.col.size();
+    for (int32_t k = 0; k < H.n; ++k) {
+        const int64_t ci = H.perm[k];
+        const int64_t x = ci % nx, y = (ci / nx) % ny, z = ci / layer;
+        const int kind = pz ? 0 : (z == 0 ? 1 : (z == nz - 1 ? 2 : 0));
+        const int deg = H.rowptr[k + 1] - H.rowptr[k];
+        double row[14][9] = {};
+        bool seen[14] = {};
+        for (int32_t p = H.rowptr[k]; p < H.rowptr[k + 1]; ++p) {
+            const int64_t cj = H.perm[H.col[p]];
+            int64_t dx = cj % nx - x, dy = (cj / nx) % ny - y, dz = cj / layer - z;
+            if (dx > 1) dx -= nx;
+            if (dx < -1) dx += nx;
+            if (dy > 1) dy -= ny;
+            if (dy < -1) dy += ny;
+            if (pz && dz > 1) dz -= nz;
+            if (pz && dz < -1) dz += nz;
+            const int o = offset_index3((int)dx, (int)dy, (int)dz);
+            if (o < 0 || seen[o]) return;
+            seen[o] = true;
+            for (int q = 0; q < 9; ++q) row[o][q] = H.coef[(size_t)q * nnz + p];
+        }
+        if (!have[kind]) {
+            have[kind] = true;
+            count[kind] = deg;
+            for (int o = 0; o < 14; ++o)
+                for (int q = 0; q < 9; ++q) c[kind][o][q] = row[o][q];
+        } else {
+            if (deg != count[kind]) return;
+            for (int o = 0; o < 14; ++o)
+                for (int q = 0; q < 9; ++q)
+                    if (std::fabs(row[o][q] - c[kind][o][q]) > 1e-12 * cmax) return;
+        }
+    }
+    info.nx = (int32_t)nx;
+    info.ny = (int32_t)ny;
+    info.nz = (int32_t)nz;
+    info.walls = !pz;
+    for (int k = 0; k < 3; ++k)
+        for (int o = 0; o < 14; ++o)
+            for (int q = 0; q < 9; ++q) info.c[k][o][q] = c[k][o][q];
+    info.ok = true;
+}
+
+}  // namespace felbm

@@ -224,6 +224,8 @@ class Mesh:
         if self.dim == 3:
             f = sum(bit for bit, L in zip((FELBM_PERIODIC_X, FELBM_PERIODIC_Y, FELBM_PERIODIC_Z), box)
                     if L > 0)
+            if general:
+                f |= FELBM_MESH_GENERAL
             st, h = felbm_mesh_create_tet(xy, tri, box, f, node_tag, stream)
             _check(st, "felbm_mesh_create_tet")
         else:

@@ -39,10 +39,12 @@ def channel(nz=17):
     return xyz, tet, box, tag, rho0, u, p0, params
 
 
-def run_gpu(case, precision, steps, export=False):
+def run_gpu(case, precision, steps, export=False, general=False):
     xyz, tet, box, tag, rho0, u0, p0, params = case
-    mesh = felbm.Mesh(xyz, tet, box, tag)
-    assert mesh.info()["kind"] == 2
+    mesh = felbm.Mesh(xyz, tet, box, tag, general=general)
+    # the Kuhn lattice runs on the lattice kernels (kind 3) unless the CSR
+    # path is forced (kind 2)
+    assert mesh.info()["kind"] == (2 if general else 3)
     st = felbm.State(mesh, felbm.make_params(precision=precision, **params), rho0, u0, p0)
     st.step(steps)
     m = st.moments()
@@ -65,9 +67,10 @@ def errors(m, o):
             "u": rel_l2(m["u"], o.u), "p": rel_l2(m["p"], o.p)}
 
 
-def test_fp64_droplet_matches_oracle():
+@pytest.mark.parametrize("general", [False, True])
+def test_fp64_droplet_matches_oracle(general):
     case = droplet()
-    m, (h, g) = run_gpu(case, "fp64", 40, export=True)
+    m, (h, g) = run_gpu(case, "fp64", 40, export=True, general=general)
     o = run_oracle(case, 40)
     e = errors(m, o)
     assert max(e.values()) <= 1e-12, e
@@ -75,9 +78,10 @@ def test_fp64_droplet_matches_oracle():
     assert rel_l2(h.ravel(), o.h.ravel()) <= 1e-12 and rel_l2(g.ravel(), o.g.ravel()) <= 1e-12
 
 
-def test_fp64_walled_channel_matches_oracle():
+@pytest.mark.parametrize("general", [False, True])
+def test_fp64_walled_channel_matches_oracle(general):
     case = channel()
-    m, _ = run_gpu(case, "fp64", 300)
+    m, _ = run_gpu(case, "fp64", 300, general=general)
     o = run_oracle(case, 300)
     e = errors(m, o)
     assert max(e["rho"], e["C"], e["u"]) <= 1e-12, e
@@ -99,11 +103,50 @@ def test_fp64_totals_conserved():
     mesh.close()
 
 
-def test_fp32_droplet_1000_steps():
+@pytest.mark.parametrize("general", [False, True])
+def test_fp32_droplet_1000_steps(general):
     case = droplet(n=12, R=3.5, u0=(0.0, 0.0, 0.0))
-    m, _ = run_gpu(case, "fp32", 1000)
+    m, _ = run_gpu(case, "fp32", 1000, general=general)
     o = run_oracle(case, 1000)
     e = errors(m, o)
     print("3-D fp32 1000 steps", e)
     # measured: rho 1.8e-7, C 2.9e-7, u 1.5e-6, p 5.7e-6
     assert e["rho"] <= 1e-6 and e["C"] <= 1e-6 and e["u"] <= 1e-5 and e["p"] <= 2e-5, e
+
+
+def test_lattice_detection():
+    """Only the exact Kuhn lattice takes the lattice kernels; a moved node,
+    a tag off the wall layers or a forced CSR path keep the general kernels."""
+    xyz, tet, box, _ = inputs.structured_tet_mesh(5, 4, 6)
+    assert felbm.Mesh(xyz, tet, box).info()["kind"] == 3
+    assert felbm.Mesh(xyz, tet, box, general=True).info()["kind"] == 2
+    moved = xyz.copy()
+    moved[7] += (0.05, -0.03, 0.02)
+    assert felbm.Mesh(moved, tet, box).info()["kind"] == 2
+    xyz, tet, box, tag = inputs.structured_tet_mesh(4, 5, 7, periodic_z=False)
+    assert felbm.Mesh(xyz, tet, box, tag).info()["kind"] == 3
+    tag2 = tag.copy()
+    tag2[len(tag2) // 2] = 5
+    assert felbm.Mesh(xyz, tet, box, tag2).info()["kind"] == 2
+    assert felbm.Mesh(xyz, tet, box, tag).info()["device_bytes"] < \
+        felbm.Mesh(xyz, tet, box, tag, general=True).info()["device_bytes"]
+
+
+def test_lattice_matches_csr_fp32():
+    """Both topologies of the same walled lattice agree to FP32 rounding."""
+    xyz, tet, box, tag = inputs.structured_tet_mesh(8, 6, 21, periodic_z=False)
+    rho0, u, p0 = inputs.slab_fields3(xyz, 5.0, 15.0, 1.0, 0.1, 3.0)
+    params = dict(rho_l=1.0, rho_v=0.1, sigma=0.01, xi=3.0, tau_l=0.8, tau_v=0.5, dt=0.5,
+                  gravity=(1e-5, 2e-6, -1e-6))
+    out = []
+    for general in (False, True):
+        mesh = felbm.Mesh(xyz, tet, box, tag, general=general)
+        st = felbm.State(mesh, felbm.make_params(precision="fp32", **params), rho0, u, p0)
+        st.step(200)
+        out.append(st.moments())
+        st.close()
+        mesh.close()
+    for k in ("rho", "C", "u"):
+        assert rel_l2(out[0][k], out[1][k]) <= 2e-6, (k, rel_l2(out[0][k], out[1][k]))
+    # p is O(1e-5) here: compare it on the c_s^2 scale
+    assert np.abs(out[0]["p"] - out[1]["p"]).max() <= 1e-8 / 3.0
