@@ -124,7 +124,8 @@ int felbm_mesh_create(const double *xy, int64_t n_nodes, const int32_t *tri, int
  *             image of the periodic box, have a positive determinant.
  *   box       host, 3 doubles: periods, read for the flagged directions
  *             (every element edge shorter than half the period).
- *   flags     FELBM_PERIODIC_X | FELBM_PERIODIC_Y | FELBM_PERIODIC_Z.
+ *   flags     FELBM_PERIODIC_X | FELBM_PERIODIC_Y | FELBM_PERIODIC_Z |
+ *             FELBM_MESH_GENERAL.
  *   node_tag  host, n_nodes uint8 or NULL: 0 = fluid; k in 1..18 = no-slip
  *             wall node whose inward normal is the D3Q19 direction e_k of
  *             the order (0,0,0), (+-1,0,0), (0,+-1,0), (0,0,+-1), (1,1,0),
@@ -133,7 +134,15 @@ int felbm_mesh_create(const double *xy, int64_t n_nodes, const int32_t *tri, int
  *             directions are neighbours).
  *   stream    as for felbm_mesh_create.
  * The mesh has kind 2 (felbm_mesh_info) and is stepped by the general
- * kernels in D3Q19.  On states of such meshes u has 3 components (u0 and u
+ * kernels in D3Q19, except the Kuhn-split cube lattice: node i at
+ * (i mod nx, (i div nx) mod ny, i div (nx ny)) h, each cube cut into the six
+ * tetrahedra around its (0,0,0)-(1,1,1) diagonal, periodic in x and y,
+ * periodic in z or walled with tags 5 on the bottom layer and 6 on the top
+ * layer (nx, ny, nz >= 3).  Unless FELBM_MESH_GENERAL is set, that lattice
+ * has kind 3: the kernels compute its neighbours from the node position and
+ * take its coefficients from the kernel parameters (no assembled arrays on
+ * the device); the results agree with kind 2 to rounding.
+ * On states of tetrahedral meshes u has 3 components (u0 and u
  * are n_nodes x 3 doubles), totals has 4 entries (mass and the three
  * momentum components), and the checkpoint arrays hold 19 x n_nodes
  * doubles each.  Errors: as felbm_mesh_create (n_nodes < 4, n_tet < 1). */
@@ -142,8 +151,8 @@ int felbm_mesh_create_tet(const double *xyz, int64_t n_nodes, const int32_t *tet
                           void *stream, felbm_mesh **out);
 
 /* Mesh facts.  Any output pointer may be NULL.  kind: 0 = general
- * (unstructured CSR kernels), 1 = structured lattice, 2 = tetrahedral
- * (n_tri then counts tetrahedra).  device_bytes: device memory held by the
+ * (unstructured CSR kernels), 1 = structured lattice, 2 = tetrahedral,
+ * 3 = Kuhn tetrahedral lattice (n_tri then counts tetrahedra).  device_bytes: device memory held by the
  * mesh. */
 int felbm_mesh_info(const felbm_mesh *mesh, int64_t *n_nodes, int64_t *n_tri, int32_t *kind,
                     int64_t *device_bytes);

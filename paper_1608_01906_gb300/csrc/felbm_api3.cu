@@ -82,12 +82,13 @@ static Phys3<T> phys3_of(const felbm_params &p) {
     return P;
 }
 
-// Scratch layout (8 N): rho, grad rho (3), mu, K (3).
+// Scratch layout (19 Np + 8 N): streamed h*, rho, grad rho (3), mu, K (3).
 template <typename T>
 static Fields3<T> fields3_of(felbm_state *s) {
     const size_t n = (size_t)s->mesh->n_nodes;
-    T *b = reinterpret_cast<T *>(s->scratch);
     Fields3<T> F;
+    F.hs = reinterpret_cast<T *>(s->scratch);
+    T *b = F.hs + 19 * pad4(n);
     F.rho = b;
     for (int k = 0; k < 3; ++k) F.dr[k] = b + (1 + k) * n;
     F.mu = b + 4 * n;
@@ -137,7 +138,7 @@ static void step3(felbm_state *s, const Topo &d, const Fields3<T> &F, const Phys
     const T *fin = reinterpret_cast<const T *>(s->f[s->cur]);
     T *fout = reinterpret_cast<T *>(s->f[s->cur ^ 1]);
     int sl = prof_begin(s, 0);
-    k_rho3<T, Topo><<<nblocks3(m->n_nodes, 256), 256, 0, m->stream>>>(d, fin, P.dt, F.rho);
+    k_rho3<T, Topo><<<nblocks3(m->n_nodes, 256), 256, 0, m->stream>>>(d, fin, P.dt, F.rho, F.hs);
     prof_end(s, sl);
     chain3<T>(s, d, F, P);
     Collide3Args<T, Topo> A;
@@ -188,7 +189,7 @@ int state_init3(const felbm_mesh *mesh, const felbm_params *params, const double
     };
     alloc(&s->f[0], 38 * pad4(N) * es);
     alloc(&s->f[1], 38 * pad4(N) * es);
-    alloc(&s->scratch, 8 * N * es);
+    alloc(&s->scratch, (19 * pad4(N) + 8 * N) * es);
     alloc(&s->mom, 5 * N * es);
     alloc((void **)&s->d_out, (6 * N + 4 * (kTotalsBlocks + 1)) * sizeof(double));
     alloc((void **)&s->d_flag, sizeof(int));

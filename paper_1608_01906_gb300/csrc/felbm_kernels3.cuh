@@ -3,12 +3,13 @@
 // Kuhn-split cube lattice (DevLattice3).  Same four dependent passes as the
 // two-dimensional general path (felbm_kernels.cuh):
 //   k_rho3      Taylor-Galerkin streaming of the 19 h populations (Sec.
-//               2.2.1, lumped mass), wall bounce-back, rho = sum_a h_a;
+//               2.2.1, lumped mass), wall bounce-back, rho = sum_a h_a; the
+//               streamed h* is kept for the collision;
 //   k_grad3     recovered grad rho (Sec. 2.3);
 //   k_mu3       Laplacian of rho, the stress force
 //               K_i = kappa [d_i |grad rho|^2 - d_j (d_i rho d_j rho)] and
 //               mu = mu_phi(rho) - kappa lap rho (Sec. 2.1);
-//   k_collide3  recovered grad mu, streaming of all 38 populations,
+//   k_collide3  recovered grad mu, streaming of the 19 g populations,
 //               bounce-back, moments (Eqs. velocity, pressure) and the
 //               post- and next pre-streaming collision (Sec. 2.2).
 // D3Q19 directions are ordered so that 2q+1 and 2q+2 are opposite (q =
@@ -184,10 +185,13 @@ __device__ __forceinline__ void by_kind(const Topo &m, int32_t i, Fn &&fn) {
 }
 #endif
 
-// Scalar fields of one time level (N each): rho, grad rho, mu, K.
+// Scalar fields of one time level (N each): rho, grad rho, mu, K; and the
+// streamed, bounced-back h* of k_rho3 (19 values per node, population
+// layout: rest at [0, Np), pair q at Np + 2 Np q).
 template <typename T>
 struct Fields3 {
     T *rho, *dr[3], *mu, *k[3];
+    T *hs;
 };
 
 // Streamed values of the 9 pairs of h (G = 0) or h and g (G = 1) of node i:
@@ -245,7 +249,7 @@ __device__ __forceinline__ void bounce_back3(int k, T *psi) {
 
 template <typename T, typename Topo>
 __global__ void __launch_bounds__(256) k_rho3(const __grid_constant__ Topo m, const T *__restrict__ f, T dt,
-                                              T *__restrict__ rho) {
+                                              T *__restrict__ rho, T *__restrict__ hs) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m.n) return;
     const size_t np = pad4((size_t)m.n);
@@ -259,6 +263,10 @@ __global__ void __launch_bounds__(256) k_rho3(const __grid_constant__ Topo m, co
 #pragma unroll
     for (int a = 0; a < 19; ++a) r += h[a];
     rho[i] = r;
+    V2<T> *hb = reinterpret_cast<V2<T> *>(hs + np);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) hb[q * np + i] = vset(h[2 * q + 1], h[2 * q + 2]);
+    hs[i] = h[0];
 }
 
 // Recovered gradient of a scalar field (3 components).
@@ -409,7 +417,7 @@ struct Collide3Args {
 };
 
 template <typename T, typename Topo>
-__global__ void __launch_bounds__(128) k_collide3(const __grid_constant__ Collide3Args<T, Topo> A) {
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 5 : 1) k_collide3(const __grid_constant__ Collide3Args<T, Topo> A) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     const Topo &m = A.m;
     if (i >= m.n) return;
@@ -417,19 +425,24 @@ __global__ void __launch_bounds__(128) k_collide3(const __grid_constant__ Collid
     T dm[3];
     T hs[19], gs[19];
     {
-        V2<T> hp[9], gp[9];
+        // g: streamed here (the h code on the g half of the state)
+        V2<T> gp[9];
         by_kind(m, i, [&](auto K) {
             recover3<T, decltype(K)::value>(m, A.F.mu, i, dm);
-            stream_pairs3<T, true, decltype(K)::value>(m, A.fin, np, i, A.P.dt, hp, gp);
+            stream_pairs3<T, false, decltype(K)::value>(m, A.fin + 19 * np, np, i, A.P.dt, gp, gp);
         });
-        unpack3<T>(A.fin[i], hp, hs);
         unpack3<T>(A.fin[19 * np + i], gp, gs);
     }
-    const int k = m.tag_of(i);
-    if (k) {
-        bounce_back3<T>(k, hs);
-        bounce_back3<T>(k, gs);
+    {
+        // h: streamed and bounced back by k_rho3
+        const V2<T> *hb = reinterpret_cast<const V2<T> *>(A.F.hs + np);
+        V2<T> hp[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) hp[q] = hb[q * np + i];
+        unpack3<T>(A.F.hs[i], hp, hs);
     }
+    const int k = m.tag_of(i);
+    if (k) bounce_back3<T>(k, gs);
     // moments of g: first moments from the differences of opposite pairs
     T sg = gs[0], mg[3] = {T(0), T(0), T(0)};
 #pragma unroll

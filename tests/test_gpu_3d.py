@@ -114,6 +114,18 @@ def test_fp32_droplet_1000_steps(general):
     assert e["rho"] <= 1e-6 and e["C"] <= 1e-6 and e["u"] <= 1e-5 and e["p"] <= 2e-5, e
 
 
+def test_fp64_box_lattice_matches_oracle():
+    """A lattice of unequal sides (16 x 8 x 12), off-centre drop."""
+    xyz, tet, box, tag = inputs.structured_tet_mesh(16, 8, 12)
+    rho0, u, p0 = inputs.droplet_fields3(xyz, box, (8.0, 4.0, 6.0), 3.0, 1.0, 0.2, 3.0,
+                                         u0=(0.01, 0.02, -0.01))
+    params = dict(rho_l=1.0, rho_v=0.2, sigma=0.01, xi=3.0, tau_l=0.6, tau_v=0.5, dt=0.5,
+                  gravity=(0.0, 0.0, 0.0))
+    m, _ = run_gpu((xyz, tet, box, None, rho0, u, p0, params), "fp64", 30)
+    e = errors(m, run_oracle((xyz, tet, box, None, rho0, u, p0, params), 30))
+    assert max(e.values()) <= 1e-12, e
+
+
 def test_lattice_detection():
     """Only the exact Kuhn lattice takes the lattice kernels; a moved node,
     a tag off the wall layers or a forced CSR path keep the general kernels."""
