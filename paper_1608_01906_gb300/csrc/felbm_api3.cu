@@ -82,17 +82,18 @@ static Phys3<T> phys3_of(const felbm_params &p) {
     return P;
 }
 
-// Scratch layout (19 Np + 8 N): streamed h*, rho, grad rho (3), mu, K (3).
+// Scratch layout (19 Np + 9 N): streamed h*, grad rho (4 N interleaved,
+// 16-byte aligned since Np is a multiple of 4), rho, mu, K (3).
 template <typename T>
 static Fields3<T> fields3_of(felbm_state *s) {
     const size_t n = (size_t)s->mesh->n_nodes;
     Fields3<T> F;
     F.hs = reinterpret_cast<T *>(s->scratch);
-    T *b = F.hs + 19 * pad4(n);
+    F.dr4 = F.hs + 19 * pad4(n);
+    T *b = F.dr4 + 4 * n;
     F.rho = b;
-    for (int k = 0; k < 3; ++k) F.dr[k] = b + (1 + k) * n;
-    F.mu = b + 4 * n;
-    for (int k = 0; k < 3; ++k) F.k[k] = b + (5 + k) * n;
+    F.mu = b + n;
+    for (int k = 0; k < 3; ++k) F.k[k] = b + (2 + k) * n;
     return F;
 }
 
@@ -189,7 +190,7 @@ int state_init3(const felbm_mesh *mesh, const felbm_params *params, const double
     };
     alloc(&s->f[0], 38 * pad4(N) * es);
     alloc(&s->f[1], 38 * pad4(N) * es);
-    alloc(&s->scratch, (19 * pad4(N) + 8 * N) * es);
+    alloc(&s->scratch, (19 * pad4(N) + 9 * N) * es);
     alloc(&s->mom, 5 * N * es);
     alloc((void **)&s->d_out, (6 * N + 4 * (kTotalsBlocks + 1)) * sizeof(double));
     alloc((void **)&s->d_flag, sizeof(int));

@@ -185,14 +185,45 @@ __device__ __forceinline__ void by_kind(const Topo &m, int32_t i, Fn &&fn) {
 }
 #endif
 
-// Scalar fields of one time level (N each): rho, grad rho, mu, K; and the
-// streamed, bounced-back h* of k_rho3 (19 values per node, population
-// layout: rest at [0, Np), pair q at Np + 2 Np q).
+// Fields of one time level: rho, mu, K (N each); grad rho interleaved as
+// (x, y, z, unused) per node (4 N, 16-byte aligned), so that one gather
+// reads a neighbour's gradient; and the streamed, bounced-back h* of k_rho3
+// (19 values per node, population layout: rest at [0, Np), pair q at
+// Np + 2 Np q).
 template <typename T>
 struct Fields3 {
-    T *rho, *dr[3], *mu, *k[3];
+    T *rho, *dr4, *mu, *k[3];
     T *hs;
 };
+
+#ifdef __CUDACC__
+template <typename T>
+__device__ __forceinline__ void load_grad3(const T *__restrict__ dr4, int32_t j, T *g) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(dr4) + j);
+        g[0] = v.x;
+        g[1] = v.y;
+        g[2] = v.z;
+    } else {
+        const double2 *p = reinterpret_cast<const double2 *>(dr4) + 2 * (size_t)j;
+        const double2 a = __ldg(p), b = __ldg(p + 1);
+        g[0] = a.x;
+        g[1] = a.y;
+        g[2] = b.x;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void store_grad3(T *__restrict__ dr4, int32_t i, const T *g) {
+    if constexpr (sizeof(T) == 4) {
+        reinterpret_cast<float4 *>(dr4)[i] = make_float4(g[0], g[1], g[2], 0.0f);
+    } else {
+        double2 *p = reinterpret_cast<double2 *>(dr4) + 2 * (size_t)i;
+        p[0] = make_double2(g[0], g[1]);
+        p[1] = make_double2(g[2], 0.0);
+    }
+}
+#endif
 
 // Streamed values of the 9 pairs of h (G = 0) or h and g (G = 1) of node i:
 // psi* = psi - dt sum_j (e.a_ij + dt/2 e.b_ij.e) (psi_j - psi_i).
@@ -292,7 +323,7 @@ __global__ void __launch_bounds__(256) k_grad3(const __grid_constant__ Topo m, F
     T g[3];
     by_kind(m, i, [&](auto K) { recover3<T, decltype(K)::value>(m, F.rho, i, g); });
 #pragma unroll
-    for (int c = 0; c < 3; ++c) F.dr[c][i] = g[c];
+    store_grad3<T>(F.dr4, i, g);
 }
 
 // lap rho = sum_c R_c(d_c rho);
@@ -304,9 +335,9 @@ __device__ __forceinline__ void mu_sums3(const Topo &m, const Fields3<T> &F, int
                                          T *K3) {
     m.template for_each<K>(i, [&](int32_t j, const T *cf) {
         T gj[3], d[3];
+        load_grad3<T>(F.dr4, j, gj);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            gj[c] = __ldg(F.dr[c] + j);
             d[c] = gj[c] - gi[c];
             lap += cf[c] * d[c];
         }
@@ -333,7 +364,7 @@ __global__ void __launch_bounds__(256) k_mu3(const __grid_constant__ Topo m, Fie
     if (i >= m.n) return;
     T gi[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) gi[c] = F.dr[c][i];
+    load_grad3<T>(F.dr4, i, gi);
     T lap = T(0), K[3] = {T(0), T(0), T(0)};
     by_kind(m, i, [&](auto KD) { mu_sums3<T, decltype(KD)::value>(m, F, i, gi, lap, K); });
     F.mu[i] = mu_bulk3<T>(P, F.rho[i]) - P.kappa * lap;
@@ -456,11 +487,9 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 5 : 1) k_collide3(const 
     }
     const T r = A.F.rho[i];
     T dr[3], K[3];
+    load_grad3<T>(A.F.dr4, i, dr);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        dr[c] = A.F.dr[c][i];
-        K[c] = A.F.k[c][i];
-    }
+    for (int c = 0; c < 3; ++c) K[c] = A.F.k[c][i];
     const Prep3<T> c = prep3<T>(A.P, sg, mg, r, dr, dm, K);
     T hout[19], gout[19];
     T dsum = T(0);
@@ -502,11 +531,9 @@ __global__ void __launch_bounds__(128) k_init3(const __grid_constant__ Topo m, T
     const size_t n = (size_t)m.n, np = pad4(n);
     T dm[3], dr[3], K[3];
     by_kind(m, i, [&](auto KD) { recover3<T, decltype(KD)::value>(m, F.mu, i, dm); });
+    load_grad3<T>(F.dr4, i, dr);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        dr[c] = F.dr[c][i];
-        K[c] = F.k[c][i];
-    }
+    for (int c = 0; c < 3; ++c) K[c] = F.k[c][i];
     const T r = mom[i];
     Prep3<T> c;
     constexpr T cs2 = T(1) / T(3);
