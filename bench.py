@@ -34,7 +34,8 @@ UNIT = "MNUPS"
 ALGO_BYTES_PER_NODE = {"fp32": 144, "fp64": 288}  # 18 populations read + 18 written
 FALLBACK_HBM_GBS = 6800.0
 # FP64 runs are bound by the FP64 pipe (about 85% busy), not by HBM.  Peak:
-# the nominal dense FP64 rate of the part.  Algorithmic flops per node update
+# the FP64 FMA rate measured on the device (felbm_alu_peak), else the nominal
+# dense FP64 rate of the part.  Algorithmic flops per node update
 # in FP64: the 1251 flops ncu counts per node (2 DFMA + DADD + DMUL) less the
 # halo recompute of the tile step (h streaming on the depth-3 halo, 1.08x
 # extra; grad rho 0.69x; mu 0.33x; about 220 flops)
@@ -402,6 +403,13 @@ def main():
         dom_name = "+".join(per_step)
         dom_avg_ms = sum(v[0] / max(v[1], 1) for v in per_step.values())
     peak, peak_kind = hbm_peak()
+    # measured ALU ceilings (after the timed region: a few ms of FMA streams)
+    alu = {}
+    for key, kind in (("fp32", felbm.ALU_FP32), ("fp32x2", felbm.ALU_FP32X2), ("fp64", felbm.ALU_FP64)):
+        try:
+            alu[key] = felbm.alu_peak(kind) / 1e12
+        except Exception:  # noqa: BLE001
+            alu[key] = None
     dim = int(np.shape(prob.xy)[1])
     # 2 x Q populations per node, read once and written once
     algo = ALGO_BYTES_PER_NODE[args.precision] * (19 if dim == 3 else 9) // 9 * prob.n_nodes
@@ -427,9 +435,12 @@ def main():
         roofline["largest_launch"] = {"kernel": dom_single, "share": dom_share}
     if args.precision == "fp64" and not multi:
         tf = FP64_ALGO_FLOPS_PER_NODE * prob.n_nodes / (dom_avg_ms * 1e-3) / 1e12
-        roofline = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": tf / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": dom_name,
-                    "kernel_ms": dom_avg_ms, "peak_source": "nominal dense FP64 rate",
+        p64 = alu.get("fp64") or FP64_PEAK_TFLOPS
+        roofline = {"bound": "alu", "achieved": tf, "peak": p64, "unit": "TFLOP/s",
+                    "frac": tf / p64, "traffic": traffic, "kernel": dom_name,
+                    "kernel_ms": dom_avg_ms,
+                    "peak_source": ("measured FP64 FMA streams (felbm_alu_peak)" if alu.get("fp64")
+                                    else "nominal dense FP64 rate"),
                     "hbm_gbs": achieved, "hbm_frac": achieved / peak,
                     "kernel_share": dom_ms / max(sum(v[0] for v in prof.values()), 1e-12)}
 
@@ -488,7 +499,8 @@ def main():
                 "gpu_launches": launches * world, "clocks": clocks,
                 "kernels": {k: {"ms": v[0], "timed": v[1], "launches": v[2]}
                             for k, v in prof.items() if v[2]},
-                "mass": float(mom["totals"][0]), "batched": batched, "serving": serving}
+                "mass": float(mom["totals"][0]), "alu_peaks_tflops": alu,
+                "batched": batched, "serving": serving}
         print(json.dumps(line), flush=True)
     st.close()
     mesh.close()

@@ -288,6 +288,15 @@ const char *felbm_profile_kind_name(int k);
 int felbm_totals_nalloc(const void *rho, const void *ux, const void *uy, const double *weight,
                         int64_t n, int32_t precision, double *totals, void *stream);
 
+/* Measured arithmetic peak of the current device, in flop/s (an FMA counts
+ * as 2): one full-occupancy launch of independent FMA chains per thread,
+ * timed with CUDA events on the legacy default stream (best of three after a
+ * warm-up launch).  kind: 0 = FP32 FMA, 1 = FP32 packed two-wide FMA
+ * (FFMA2), 2 = FP64 FMA.  These are the ALU ceilings of the step kernels.
+ * Synchronises the default stream; allocates 16 bytes of device memory for
+ * the call.  Errors: INVALID_ARG (NULL pointer, kind out of range), CUDA. */
+int felbm_alu_peak(int kind, double *flops_per_s);
+
 /* Short static description of a status code. */
 const char *felbm_status_string(int status);
 

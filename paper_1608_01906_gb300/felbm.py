@@ -37,7 +37,7 @@ EXPORTED = [
     "felbm_state_import", "felbm_state_destroy", "felbm_status_string",
     "felbm_profile_enable", "felbm_profile_read", "felbm_profile_kind_name",
     "felbm_batch_create", "felbm_batch_step", "felbm_batch_sync", "felbm_batch_info",
-    "felbm_batch_destroy", "felbm_totals_nalloc",
+    "felbm_batch_destroy", "felbm_totals_nalloc", "felbm_alu_peak",
 ]
 FELBM_BATCH_AUTOTUNE = 0x1
 FELBM_PROFILE_KINDS = 8
@@ -127,6 +127,8 @@ def _declare_extra(lib):
     if hasattr(lib, "felbm_totals_nalloc"):
         lib.felbm_totals_nalloc.restype = C.c_int
         lib.felbm_totals_nalloc.argtypes = [vp, vp, vp, vp, i64, i32, vp, vp]
+    lib.felbm_alu_peak.restype = C.c_int
+    lib.felbm_alu_peak.argtypes = [C.c_int, vp]
 
 
 def _p(a):
@@ -199,6 +201,23 @@ def felbm_state_export(state, hbar, gbar):
 
 def felbm_state_import(state, hbar, gbar):
     return load().felbm_state_import(state, _p(hbar), _p(gbar))
+
+
+def felbm_alu_peak(kind):
+    v = C.c_double()
+    st = load().felbm_alu_peak(kind, C.byref(v))
+    return st, v.value
+
+
+ALU_FP32, ALU_FP32X2, ALU_FP64 = 0, 1, 2
+
+
+def alu_peak(kind):
+    """Measured flop/s of the current device: ALU_FP32, ALU_FP32X2 (packed
+    two-wide FMA) or ALU_FP64."""
+    st, v = felbm_alu_peak(kind)
+    _check(st, "felbm_alu_peak")
+    return v
 
 
 # ---- owning wrappers ------------------------------------------------------
