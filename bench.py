@@ -405,9 +405,10 @@ def main():
     peak, peak_kind = hbm_peak()
     # measured ALU ceilings (after the timed region: a few ms of FMA streams)
     alu = {}
-    for key, kind in (("fp32", felbm.ALU_FP32), ("fp32x2", felbm.ALU_FP32X2), ("fp64", felbm.ALU_FP64)):
+    for key, alu_kind in (("fp32", felbm.ALU_FP32), ("fp32x2", felbm.ALU_FP32X2),
+                          ("fp64", felbm.ALU_FP64)):
         try:
-            alu[key] = felbm.alu_peak(kind) / 1e12
+            alu[key] = felbm.alu_peak(alu_kind) / 1e12
         except Exception:  # noqa: BLE001
             alu[key] = None
     dim = int(np.shape(prob.xy)[1])

@@ -88,11 +88,18 @@ static Phys<T> phys_of(const felbm_params &p) {
     return P;
 }
 
+// Scratch: on general meshes the streamed h* (9 Np, population layout)
+// first, then 6 N fields (rho, grad rho, mu, K).
+static size_t hstar_elems(const felbm_mesh *m) { return m->kind == 0 ? 9 * pad4(pop_slots(m)) : 0; }
+
 template <typename T>
 static Fields<T> fields_of(felbm_state *s) {
     const size_t n = (size_t)s->mesh->n_nodes;
-    T *b = reinterpret_cast<T *>(s->scratch);
+    T *base = reinterpret_cast<T *>(s->scratch);
+    const size_t nh = hstar_elems(s->mesh);
+    T *b = base + nh;
     Fields<T> F;
+    F.hs = nh ? base : nullptr;
     F.rho = b;
     F.drx = b + n;
     F.dry = b + 2 * n;
@@ -161,7 +168,7 @@ static void step_topo(felbm_state *s, const Topo &d, bool write_mom) {
     const T *fin = reinterpret_cast<const T *>(s->f[s->cur]);
     T *fout = reinterpret_cast<T *>(s->f[s->cur ^ 1]);
     int sl = prof_begin(s, 0);
-    k_rho<T, Topo><<<g, 256, 0, m->stream>>>(d, fin, P.dt, F.rho);
+    k_rho<T, Topo><<<g, 256, 0, m->stream>>>(d, fin, P.dt, F.rho, F.hs);
     prof_end(s, sl);
     launch_chain<T, Topo>(s, d);
     CollideArgs<T, Topo> A;
@@ -471,7 +478,7 @@ int felbm_state_init(const felbm_mesh *mesh, const felbm_params *params, const d
     };
     alloc(&s->f[0], 18 * pad4(pop_slots(mesh)) * es);
     alloc(&s->f[1], 18 * pad4(pop_slots(mesh)) * es);
-    alloc(&s->scratch, 6 * N * es);
+    alloc(&s->scratch, (hstar_elems(mesh) + 6 * N) * es);
     alloc(&s->mom, 4 * N * es);
     alloc((void **)&s->d_out, (5 * N + 3 * (kTotalsBlocks + 1)) * sizeof(double));
     alloc((void **)&s->d_flag, sizeof(int));

@@ -233,6 +233,9 @@ inline size_t pop_index(int a, size_t i, size_t n) {
 template <typename T>
 struct Fields {
     T *rho, *drx, *dry, *mu, *kx, *ky;  // N each
+    // general meshes: the streamed, bounced-back h* of k_rho (population
+    // layout: rest at [0, Np), pair q at Np + 2 Np q); nullptr otherwise
+    T *hs;
 };
 
 }  // namespace felbm

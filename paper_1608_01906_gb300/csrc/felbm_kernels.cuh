@@ -158,7 +158,7 @@ __device__ __forceinline__ void bounce_back(int k, T *psi) {
 
 template <typename T, typename Topo>
 __global__ void __launch_bounds__(256) k_rho(Topo m, const T *__restrict__ f, T dt,
-                                             T *__restrict__ rho) {
+                                             T *__restrict__ rho, T *__restrict__ hs) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m.n) return;
     const size_t np = pad4(m.slots());
@@ -174,6 +174,11 @@ __global__ void __launch_bounds__(256) k_rho(Topo m, const T *__restrict__ f, T 
 #pragma unroll
     for (int a = 0; a < 9; ++a) r += h[a];
     rho[i] = r;
+    const size_t si = m.slot(i);
+    V2<T> *hb = reinterpret_cast<V2<T> *>(hs + np);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) hb[q * np + si] = vset(h[pair_dir(q, 0)], h[pair_dir(q, 1)]);
+    hs[si] = h[0];
 }
 
 // Recovered gradient of a scalar field.
@@ -385,17 +390,19 @@ __global__ void __launch_bounds__(256) k_collide(CollideArgs<T, Topo> A) {
     const size_t np = pad4(m.slots()), si = m.slot(i);
     T hs[9], gs[9];
     {
-        V2<T> hp[4], gp[4];
-        stream_pairs<T, true>(m, A.fin, np, i, A.P.dt, hp, gp);
-        unpack_pairs<T>(A.fin[si], hp, hs);
+        // g streamed here (the h code on the g half of the state); h* was
+        // streamed and bounced back by k_rho
+        V2<T> gp[4], hp[4];
+        stream_pairs<T, false>(m, A.fin + 9 * np, np, i, A.P.dt, gp, gp);
         unpack_pairs<T>(A.fin[9 * np + si], gp, gs);
+        const V2<T> *hsb = reinterpret_cast<const V2<T> *>(A.F.hs + np);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) hp[q] = hsb[q * np + si];
+        unpack_pairs<T>(A.F.hs[si], hp, hs);
     }
     {
         const int k = m.tag_of(i);
-        if (k) {
-            bounce_back<T>(k, hs);
-            bounce_back<T>(k, gs);
-        }
+        if (k) bounce_back<T>(k, gs);
     }
     const T r = A.F.rho[i];
     T hout[9], gout[9], ux, uy, p;

@@ -278,6 +278,19 @@ __device__ __forceinline__ void bounce_back3(int k, T *psi) {
         if (e3x(a) * kx + e3y(a) * ky + e3z(a) * kz > 0) psi[a] = psi[a % 2 ? a + 1 : a - 1];
 }
 
+// Bounce-back of pair q = (a, a+1), a = 2q+1, at a wall node with inward
+// normal e_k: the member with e . e_k > 0 takes the value of the other
+// (bounce_back3 on one pair).
+template <typename T>
+__device__ __forceinline__ void bounce_pair3(int k, int q, V2<T> &p) {
+    const int a = 2 * q + 1;
+    const int d = e3x(a) * e3x(k) + e3y(a) * e3y(k) + e3z(a) * e3z(k);
+    if (d > 0)
+        p.x = p.y;
+    else if (d < 0)
+        p.y = p.x;
+}
+
 template <typename T, typename Topo>
 __global__ void __launch_bounds__(256) k_rho3(const __grid_constant__ Topo m, const T *__restrict__ f, T dt,
                                               T *__restrict__ rho, T *__restrict__ hs) {
@@ -436,6 +449,39 @@ __device__ __forceinline__ void collide_pop3(const Prep3<T> &c, int a, T hs, T g
     gout = gs + (c.omw * dg + c.opw * (Ga + Ba));
 }
 
+// Collision of the opposite pair q = (a, a+1), a = 2q+1, in packed
+// two-wide arithmetic: e_(a+1) = -e_a and equal weights, so the odd parts
+// (e.u, e.X, e.grad rho, e.K, e.du) flip sign between the lanes and the even
+// parts are shared (collide_pop3 on both members).
+template <typename T>
+__device__ __forceinline__ void collide_pair3(const Prep3<T> &c, int q, V2<T> hs, V2<T> gs, V2<T> &ho,
+                                              V2<T> &go) {
+    const int a = 2 * q + 1;
+    const T ex = T(e3x(a)), ey = T(e3y(a)), ez = T(e3z(a));
+    const T wa = w3<T>(a);
+    const T eu = ex * c.u[0] + ey * c.u[1] + ez * c.u[2];
+    const T eX = ex * c.X[0] + ey * c.X[1] + ez * c.X[2];
+    const T eD = ex * c.dr[0] + ey * c.dr[1] + ez * c.dr[2];
+    const T eK = ex * c.K[0] + ey * c.K[1] + ez * c.K[2];
+    const T edu = ex * c.du[0] + ey * c.du[1] + ez * c.du[2];
+    const T even = T(4.5) * eu * eu - T(1.5) * c.uu;
+    const V2<T> gmw = vfma(vset(T(3) * wa, T(3) * wa), vset(eu, -eu), vset(wa * even, wa * even));  // Gamma - w
+    const V2<T> gam = vadd(gmw, vset(wa, wa));
+    const T h3 = c.hdt * T(3);
+    const V2<T> Fa = vmul(vset(h3 * (eX - c.uX), h3 * (-eX - c.uX)), gam);
+    const V2<T> Ga = vfma(vset(c.hdt * (eD - c.uD), c.hdt * (-eD - c.uD)), gmw,
+                          vmul(vset(h3 * (eK - c.uK), h3 * (-eK - c.uK)), gam));
+    const T bev = T(4.5) * edu * (T(2) * eu + edu) - T(1.5) * c.udu;
+    const T hrw = T(0.5) * c.r * wa;
+    const V2<T> Sg = vfma(vset(hrw, hrw), vset(T(3) * edu + bev, bev - T(3) * edu), Ga);  // G + B
+    const V2<T> rg = vmul(vset(c.r, c.r), gmw);
+    const V2<T> dh = vadd(vfma(vset(c.r, c.r), vset(wa, wa), vset(-hs.x, -hs.y)), rg);  // h_eq - h*
+    const T p3 = wa * T(3) * c.p;
+    const V2<T> dg = vadd(vset(p3 - gs.x, p3 - gs.y), rg);  // g_eq - g*
+    ho = vadd(hs, vfma(vset(c.omw, c.omw), dh, vmul(vset(c.opw, c.opw), Fa)));
+    go = vadd(gs, vfma(vset(c.omw, c.omw), dg, vmul(vset(c.opw, c.opw), Sg)));
+}
+
 template <typename T, typename Topo>
 struct Collide3Args {
     Topo m;
@@ -454,33 +500,32 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 5 : 1) k_collide3(const 
     if (i >= m.n) return;
     const size_t n = (size_t)m.n, np = pad4(n);
     T dm[3];
-    T hs[19], gs[19];
-    {
-        // g: streamed here (the h code on the g half of the state)
-        V2<T> gp[9];
-        by_kind(m, i, [&](auto K) {
-            recover3<T, decltype(K)::value>(m, A.F.mu, i, dm);
-            stream_pairs3<T, false, decltype(K)::value>(m, A.fin + 19 * np, np, i, A.P.dt, gp, gp);
-        });
-        unpack3<T>(A.fin[19 * np + i], gp, gs);
-    }
+    V2<T> hp[9], gp[9];  // h* (from k_rho3) and the streamed g, as opposite pairs
+    // g: streamed here (the h code on the g half of the state)
+    by_kind(m, i, [&](auto K) {
+        recover3<T, decltype(K)::value>(m, A.F.mu, i, dm);
+        stream_pairs3<T, false, decltype(K)::value>(m, A.fin + 19 * np, np, i, A.P.dt, gp, gp);
+    });
+    const T g0 = A.fin[19 * np + i];
     {
         // h: streamed and bounced back by k_rho3
         const V2<T> *hb = reinterpret_cast<const V2<T> *>(A.F.hs + np);
-        V2<T> hp[9];
 #pragma unroll
         for (int q = 0; q < 9; ++q) hp[q] = hb[q * np + i];
-        unpack3<T>(A.F.hs[i], hp, hs);
     }
+    const T h0 = A.F.hs[i];
     const int k = m.tag_of(i);
-    if (k) bounce_back3<T>(k, gs);
+    if (k) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) bounce_pair3<T>(k, q, gp[q]);
+    }
     // moments of g: first moments from the differences of opposite pairs
-    T sg = gs[0], mg[3] = {T(0), T(0), T(0)};
+    T sg = g0, mg[3] = {T(0), T(0), T(0)};
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
         const int a = 2 * q + 1;
-        const T d = gs[a] - gs[a + 1];
-        sg += gs[a] + gs[a + 1];
+        const T d = gp[q].x - gp[q].y;
+        sg += gp[q].x + gp[q].y;
         mg[0] += T(e3x(a)) * d;
         mg[1] += T(e3y(a)) * d;
         mg[2] += T(e3z(a)) * d;
@@ -491,25 +536,22 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 5 : 1) k_collide3(const 
 #pragma unroll
     for (int c = 0; c < 3; ++c) K[c] = A.F.k[c][i];
     const Prep3<T> c = prep3<T>(A.P, sg, mg, r, dr, dm, K);
-    T hout[19], gout[19];
-    T dsum = T(0);
-#pragma unroll
-    for (int a = 1; a < 19; ++a) {
-        collide_pop3<T>(c, a, hs[a], gs[a], hout[a], gout[a]);
-        dsum += hout[a] - hs[a];
-    }
-    collide_pop3<T>(c, 0, hs[0], gs[0], hout[0], gout[0]);
-    dsum += hout[0] - hs[0];
-    hout[0] -= dsum;  // local mass: sum_a hbar_a = sum_a h*_a up to one rounding
     V2<T> *hb = reinterpret_cast<V2<T> *>(A.fout + np);
     V2<T> *gb = reinterpret_cast<V2<T> *>(A.fout + 20 * np);
+    T dsum = T(0);
 #pragma unroll
     for (int q = 0; q < 9; ++q) {
-        hb[q * np + i] = vset(hout[2 * q + 1], hout[2 * q + 2]);
-        gb[q * np + i] = vset(gout[2 * q + 1], gout[2 * q + 2]);
+        V2<T> ho, go;
+        collide_pair3<T>(c, q, hp[q], gp[q], ho, go);
+        dsum += (ho.x - hp[q].x) + (ho.y - hp[q].y);
+        hb[q * np + i] = ho;
+        gb[q * np + i] = go;
     }
-    A.fout[i] = hout[0];
-    A.fout[19 * np + i] = gout[0];
+    T hout0, gout0;
+    collide_pop3<T>(c, 0, h0, g0, hout0, gout0);
+    dsum += hout0 - h0;
+    A.fout[i] = hout0 - dsum;  // local mass: sum_a hbar_a = sum_a h*_a up to one rounding
+    A.fout[19 * np + i] = gout0;
     if (!(finite_val(r) && finite_val(c.u[0]) && finite_val(c.u[1]) && finite_val(c.u[2]) &&
           finite_val(c.p)))
         atomicOr(A.flag, 1);
