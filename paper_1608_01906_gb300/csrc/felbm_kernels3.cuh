@@ -225,37 +225,37 @@ __device__ __forceinline__ void store_grad3(T *__restrict__ dr4, int32_t i, cons
 }
 #endif
 
-// Streamed values of the 9 pairs of h (G = 0) or h and g (G = 1) of node i:
+// Streamed values of pairs Q0 .. Q0+NQ-1 of one distribution of node i
+// (base: its rest values; pair q at base + Np + 2 Np q):
 // psi* = psi - dt sum_j (e.a_ij + dt/2 e.b_ij.e) (psi_j - psi_i).
-template <typename T, bool G, int K, typename Topo>
-__device__ __forceinline__ void stream_pairs3(const Topo &m, const T *__restrict__ f, size_t np, int32_t i,
-                                              T dt, V2<T> *hp, V2<T> *gp) {
-    const V2<T> *hb = reinterpret_cast<const V2<T> *>(f + np);
-    const V2<T> *gb = reinterpret_cast<const V2<T> *>(f + 20 * np);
+template <typename T, int Q0, int NQ, int K, typename Topo>
+__device__ __forceinline__ void stream_range3(const Topo &m, const T *__restrict__ base, size_t np, int32_t i,
+                                              T dt, V2<T> *out) {
+    const V2<T> *pb = reinterpret_cast<const V2<T> *>(base + np);
     const V2<T> m1 = vset(T(-1), T(-1));
-    V2<T> hs[9], ha[9], gs[9], ga[9];
+    V2<T> own[NQ], acc[NQ];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) {
-        hs[q] = hb[q * np + i];
-        ha[q] = vset(T(0), T(0));
-        if (G) {
-            gs[q] = gb[q * np + i];
-            ga[q] = vset(T(0), T(0));
-        }
+    for (int r = 0; r < NQ; ++r) {
+        own[r] = pb[(Q0 + r) * np + i];
+        acc[r] = vset(T(0), T(0));
     }
     m.template for_each_pair<K>(i, T(0.5) * dt, [&](int32_t j, const V2<T> *c) {
 #pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            ha[q] = vfma(c[q], vfma(hs[q], m1, __ldg(hb + q * np + j)), ha[q]);
-            if (G) ga[q] = vfma(c[q], vfma(gs[q], m1, __ldg(gb + q * np + j)), ga[q]);
-        }
+        for (int r = 0; r < NQ; ++r)
+            acc[r] = vfma(c[Q0 + r], vfma(own[r], m1, __ldg(pb + (Q0 + r) * np + j)), acc[r]);
     });
     const V2<T> mdt = vset(-dt, -dt);
 #pragma unroll
-    for (int q = 0; q < 9; ++q) {
-        hp[q] = vfma(mdt, ha[q], hs[q]);
-        if (G) gp[q] = vfma(mdt, ga[q], gs[q]);
-    }
+    for (int r = 0; r < NQ; ++r) out[r] = vfma(mdt, acc[r], own[r]);
+}
+
+// The 9 streamed pairs in two passes over the neighbours (5 + 4 pairs):
+// fewer live registers per thread, more threads per SM.
+template <typename T, int K, typename Topo>
+__device__ __forceinline__ void stream_all3(const Topo &m, const T *__restrict__ base, size_t np, int32_t i,
+                                            T dt, V2<T> *out) {
+    stream_range3<T, 0, 5, K>(m, base, np, i, dt, out);
+    stream_range3<T, 5, 4, K>(m, base, np, i, dt, out + 5);
 }
 
 template <typename T>
@@ -292,13 +292,13 @@ __device__ __forceinline__ void bounce_pair3(int k, int q, V2<T> &p) {
 }
 
 template <typename T, typename Topo>
-__global__ void __launch_bounds__(256) k_rho3(const __grid_constant__ Topo m, const T *__restrict__ f, T dt,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 1) k_rho3(const __grid_constant__ Topo m, const T *__restrict__ f, T dt,
                                               T *__restrict__ rho, T *__restrict__ hs) {
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m.n) return;
     const size_t np = pad4((size_t)m.n);
     V2<T> hp[9];
-    by_kind(m, i, [&](auto K) { stream_pairs3<T, false, decltype(K)::value>(m, f, np, i, dt, hp, hp); });
+    by_kind(m, i, [&](auto K) { stream_all3<T, decltype(K)::value>(m, f, np, i, dt, hp); });
     T h[19];
     unpack3<T>(f[i], hp, h);
     const int k = m.tag_of(i);
@@ -504,7 +504,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 5 : 1) k_collide3(const 
     // g: streamed here (the h code on the g half of the state)
     by_kind(m, i, [&](auto K) {
         recover3<T, decltype(K)::value>(m, A.F.mu, i, dm);
-        stream_pairs3<T, false, decltype(K)::value>(m, A.fin + 19 * np, np, i, A.P.dt, gp, gp);
+        stream_all3<T, decltype(K)::value>(m, A.fin + 19 * np, np, i, A.P.dt, gp);
     });
     const T g0 = A.fin[19 * np + i];
     {
