@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(256) k_grad3(const __grid_constant__ Topo m, F
     if (i >= m.n) return;
     T g[3];
     by_kind(m, i, [&](auto K) { recover3<T, decltype(K)::value>(m, F.rho, i, g); });
-store_grad3<T>(F.dr4, i, g);
+    store_grad3<T>(F.dr4, i, g);
 }
 
 // lap rho = sum_c R_c(d_c rho);
@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(256) k_mu3(const __grid_constant__ Topo m, Fie
     const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m.n) return;
     T gi[3];
-load_grad3<T>(F.dr4, i, gi);
+    load_grad3<T>(F.dr4, i, gi);
     T lap = T(0), K[3] = {T(0), T(0), T(0)};
     by_kind(m, i, [&](auto KD) { mu_sums3<T, decltype(KD)::value>(m, F, i, gi, lap, K); });
     F.mu[i] = mu_bulk3<T>(P, F.rho[i]) - P.kappa * lap;
