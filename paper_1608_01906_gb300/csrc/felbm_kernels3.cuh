@@ -356,17 +356,13 @@ __device__ __forceinline__ void mu_sums3(const Topo &m, const Fields3<T> &F, int
         T sq[3];  // differences of (d_c rho)^2
 #pragma unroll
         for (int c = 0; c < 3; ++c) sq[c] = d[c] * (gj[c] + gi[c]);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            T acc = T(0);
-#pragma unroll
-            for (int b = 0; b < 3; ++b) {
-                if (b == a) continue;
-                const T dab = gj[a] * d[b] + gi[b] * d[a];  // difference of d_a rho d_b rho
-                acc += cf[a] * sq[b] - cf[b] * dab;
-            }
-            K3[a] += acc;
-        }
+        // differences of d_a rho d_b rho (a < b), each formed once
+        const T pxy = gj[0] * d[1] + gi[1] * d[0];
+        const T pxz = gj[0] * d[2] + gi[2] * d[0];
+        const T pyz = gj[1] * d[2] + gi[2] * d[1];
+        K3[0] += cf[0] * (sq[1] + sq[2]) - (cf[1] * pxy + cf[2] * pxz);
+        K3[1] += cf[1] * (sq[0] + sq[2]) - (cf[0] * pxy + cf[2] * pyz);
+        K3[2] += cf[2] * (sq[0] + sq[1]) - (cf[0] * pxz + cf[1] * pyz);
     });
 }
 
