@@ -126,6 +126,21 @@ def test_fp64_box_lattice_matches_oracle():
     assert max(e.values()) <= 1e-12, e
 
 
+def test_fp64_walled_slab_lattice_matches_oracle():
+    """32 x 8 x 16 with z walls, a liquid slab under oblique gravity: blocks
+    of the lattice kernels hold wall-layer and interior nodes together."""
+    xyz, tet, box, tag = inputs.structured_tet_mesh(32, 8, 16, periodic_z=False)
+    rho0, u, p0 = inputs.slab_fields3(xyz, 4.0, 11.0, 1.0, 0.1, 3.0)
+    params = dict(rho_l=1.0, rho_v=0.1, sigma=0.01, xi=3.0, tau_l=0.7, tau_v=0.5, dt=0.5,
+                  gravity=(2e-5, -1e-5, 0.0))
+    case = (xyz, tet, box, tag, rho0, u, p0, params)
+    m, _ = run_gpu(case, "fp64", 40)
+    e = errors(m, run_oracle(case, 40))
+    assert max(e["rho"], e["C"], e["u"]) <= 1e-12, e
+    o = run_oracle(case, 40)
+    assert np.abs(m["p"] - o.p).max() <= 1e-13 / 3.0
+
+
 def test_lattice_detection():
     """Only the exact Kuhn lattice takes the lattice kernels; a moved node,
     a tag off the wall layers or a forced CSR path keep the general kernels."""
