@@ -75,14 +75,25 @@ def dist_env():
     return world, rank, local
 
 
-def csrc_hash():
+# Sources that determine a kernel's code (its ncu counters stay valid while
+# these are unchanged); kernels not listed depend on every source.
+KERNEL_SOURCES = {
+    "k_lattice_step": ["csrc/felbm_lattice.cuh", "csrc/felbm_kernels.cuh", "csrc/felbm_internal.h",
+                       "csrc/felbm_api.cu", "csrc/felbm_tmap.cu", "../include/felbm.h"],
+}
+
+
+def csrc_hash(kernel=None):
     import hashlib
 
-    d = os.path.join(ROOT, "paper_1608_01906_gb300", "csrc")
+    pkg = os.path.join(ROOT, "paper_1608_01906_gb300")
+    files = KERNEL_SOURCES.get(kernel)
+    if files is None:
+        files = ["csrc/" + f for f in sorted(os.listdir(os.path.join(pkg, "csrc")))]
     h = hashlib.sha256()
-    for f in sorted(os.listdir(d)):
+    for f in files:
         h.update(f.encode())
-        with open(os.path.join(d, f), "rb") as fh:
+        with open(os.path.join(pkg, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
@@ -422,7 +433,7 @@ def main():
             tr = json.load(f)
         ent = tr.get(dom_name + ":" + args.precision)
         # counters are valid only for the kernel sources they were taken on
-        if ent and ent.get("csrc_sha256_16") == csrc_hash():
+        if ent and ent.get("csrc_sha256_16") == csrc_hash(dom_name):
             traffic = ent["bytes_per_launch"]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "kernel": dom_name,
