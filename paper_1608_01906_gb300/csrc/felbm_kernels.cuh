@@ -30,6 +30,26 @@ __host__ __device__ constexpr int kOpp(int a) { return a == 0 ? 0 : (a <= 4 ? ((
 template <typename T>
 __host__ __device__ constexpr T kW(int a) { return a == 0 ? T(4) / T(9) : (a <= 4 ? T(1) / T(9) : T(1) / T(36)); }
 
+// 1/12 rounded to a multiple of 2^-25 (FP32) or 2^-54 (FP64): the base of the
+// 3 w_a constants below, chosen so that they are exact in T.
+template <typename T>
+__host__ __device__ constexpr T kTwelfth() {
+    return sizeof(T) == 4 ? T(2796203.0 / 33554432.0) : T(1501199875790165.0 / 18014398509481984.0);
+}
+
+// 3 w_a in the working precision, with the moment identities of the
+// equilibria exact in T: sum_a 3 w_a = 3 (w3_0 + 4 w3_1 + 4 w3_5) and
+// sum_a 3 w_a e_ax^2 = 1 (2 w3_1 + 4 w3_5), from e ~ 1/12: w3_5 = e,
+// w3_1 = (1 - 4 e)/2, w3_0 = 1 + 4 e.  The nearest values to 4/3, 1/3, 1/12
+// miss both identities by about one rounding; through the pressure and the
+// momentum of g that bias is a gain on p and u applied every step, which a
+// near-steady FP32 run accumulates (1.3e-5 in u after 1000 steps of a
+// droplet, against 1.3e-6 with these constants).
+template <typename T>
+__host__ __device__ constexpr T kW3(int a) {
+    return a == 0 ? T(1) + T(4) * kTwelfth<T>() : (a <= 4 ? (T(1) - T(4) * kTwelfth<T>()) / T(2) : kTwelfth<T>());
+}
+
 template <typename T>
 __device__ __forceinline__ bool finite_val(T v) { return isfinite(v); }
 
@@ -269,7 +289,9 @@ __device__ __forceinline__ CollidePrep<T> collide_prep(const Phys<T> &P, T sg, T
     c.r = r;
     c.ux = (mx + c.hdt * kx + c.hdt * r * P.gx) * inv_r;
     c.uy = (my + c.hdt * ky + c.hdt * r * P.gy) * inv_r;
-    c.p = cs2 * (sg + c.hdt * (c.ux * drx + c.uy * dry));
+    // p = c_s^2 (...) as a division by 3: a rounded 1/3 would be a gain on p
+    // every step (see kW3)
+    c.p = (sg + c.hdt * (c.ux * drx + c.uy * dry)) / T(3);
     T C = (r - P.rho_v) * P.inv_drho;
     C = C < T(0) ? T(0) : (C > T(1) ? T(1) : C);
     // 1/tau = C/tau_l + (1-C)/tau_v; w = (2 tau - 1)/(2 tau + 1) gives, with
@@ -297,23 +319,23 @@ __device__ __forceinline__ CollidePrep<T> collide_prep(const Phys<T> &P, T sg, T
 template <typename T, int A>
 __device__ __forceinline__ void collide_pop(const CollidePrep<T> &c, T hs, T gs, T &hout, T &gout) {
     constexpr int ex = kEx(A), ey = kEy(A);
-    constexpr T wa = kW<T>(A);
+    constexpr T wa = kW<T>(A), w3 = kW3<T>(A);
     const T eu = T(ex) * c.ux + T(ey) * c.uy;
     // Gamma - w formed directly: forming Gamma ~ w first and subtracting w
     // would cancel away the momentum part rho w 3 e.u in FP32.
-    const T gmw = wa * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * c.uu);
-    const T gam = wa + gmw;
+    const T gmw = w3 * (eu + T(1.5) * eu * eu - T(0.5) * c.uu);
+    const T gam3 = w3 + T(3) * gmw;  // 3 Gamma
     const T eX = T(ex) * c.Xx + T(ey) * c.Xy;
     const T eD = T(ex) * c.drx + T(ey) * c.dry;
     const T eK = T(ex) * c.kx + T(ey) * c.ky;
     const T edu = T(ex) * c.dux + T(ey) * c.duy;
-    const T Fa = c.hdt * T(3) * (eX - c.uX) * gam;
-    const T Ga = c.hdt * (eD - c.uD) * gmw + c.hdt * T(3) * (eK - c.uK) * gam;
+    const T Fa = c.hdt * (eX - c.uX) * gam3;
+    const T Ga = c.hdt * (eD - c.uD) * gmw + c.hdt * (eK - c.uK) * gam3;
     // 1/2 [g_eq(u + du) - g_eq(u)] = rho/2 [Gamma(u + du) - Gamma(u)]
-    const T Ba = T(0.5) * c.r * wa * (T(3) * edu + T(4.5) * edu * (T(2) * eu + edu) - T(1.5) * c.udu);
+    const T Ba = T(0.5) * c.r * w3 * (edu + T(1.5) * edu * (T(2) * eu + edu) - T(0.5) * c.udu);
     const T Sg = Ga + Ba;
-    const T dh = fma(c.r, wa, -hs) + c.r * gmw;           // h_eq - h*
-    const T dg = fma(wa * T(3), c.p, -gs) + c.r * gmw;    // g_eq - g*
+    const T dh = fma(c.r, wa, -hs) + c.r * gmw;  // h_eq - h*
+    const T dg = fma(w3, c.p, -gs) + c.r * gmw;  // g_eq - g*
     hout = hs + (c.omw * dh + c.opw * Fa);
     gout = gs + (c.omw * dg + c.opw * Sg);
 }
@@ -447,19 +469,19 @@ __global__ void __launch_bounds__(256) k_init(Topo m, T *__restrict__ fout, Fiel
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
         const int ex = kEx(a), ey = kEy(a);
-        const T wa = kW<T>(a);
+        const T wa = kW<T>(a), w3 = kW3<T>(a);
         const T eu = T(ex) * ux + T(ey) * uy;
-        const T gmw = wa * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * uu);  // Gamma - w
-        const T gam = wa + gmw;
+        const T gmw = w3 * (eu + T(1.5) * eu * eu - T(0.5) * uu);  // Gamma - w
+        const T gam3 = w3 + T(3) * gmw;                             // 3 Gamma
         const T eX = T(ex) * Xx + T(ey) * Xy;
         const T eD = T(ex) * drx + T(ey) * dry;
         const T eK = T(ex) * kx + T(ey) * ky;
         const T edu = T(ex) * dux + T(ey) * duy;
-        const T Fa = hdt * T(3) * (eX - uX) * gam;
-        const T Ga = hdt * (eD - uD) * gmw + hdt * T(3) * (eK - uK) * gam;
-        const T Ba = T(0.5) * r * wa * (T(3) * edu + T(4.5) * edu * (T(2) * eu + edu) - T(1.5) * udu);
-        fout[pop_index(a, m.slot(i), m.slots())] = r * gam + Fa;
-        fout[pop_index(9 + a, m.slot(i), m.slots())] = wa * T(3) * p + r * gmw + Ga + Ba;
+        const T Fa = hdt * (eX - uX) * gam3;
+        const T Ga = hdt * (eD - uD) * gmw + hdt * (eK - uK) * gam3;
+        const T Ba = T(0.5) * r * w3 * (edu + T(1.5) * edu * (T(2) * eu + edu) - T(0.5) * udu);
+        fout[pop_index(a, m.slot(i), m.slots())] = (r * wa + r * gmw) + Fa;
+        fout[pop_index(9 + a, m.slot(i), m.slots())] = w3 * p + r * gmw + Ga + Ba;
     }
 }
 

@@ -42,6 +42,15 @@ __host__ __device__ constexpr T w3(int a) {
     return a == 0 ? T(1) / T(3) : (a <= 6 ? T(1) / T(18) : T(1) / T(36));
 }
 
+// 3 w_a of D3Q19 in the working precision with the moment identities exact
+// in T (see kW3): sum_a 3 w_a = 3 (w3_0 + 6 w3_1 + 12 w3_7) and
+// sum_a 3 w_a e_ax^2 = 1 (2 w3_1 + 8 w3_7), from e ~ 1/12 (kTwelfth):
+// w3_7 = e, w3_1 = (1 - 8 e)/2, w3_0 = 12 e.
+template <typename T>
+__host__ __device__ constexpr T w3x3(int a) {
+    return a == 0 ? T(12) * kTwelfth<T>() : (a <= 6 ? (T(1) - T(8) * kTwelfth<T>()) / T(2) : kTwelfth<T>());
+}
+
 // Model constants of one state (Sec. 2.1) with three-component gravity.
 template <typename T>
 struct Phys3 {
@@ -399,7 +408,7 @@ __device__ __forceinline__ Prep3<T> prep3(const Phys3<T> &P, T sg, const T *mg, 
         c.u[k] = (mg[k] + c.hdt * K[k] + c.hdt * r * P.g[k]) * inv_r;
         ud += c.u[k] * dr[k];
     }
-    c.p = cs2 * (sg + c.hdt * ud);
+    c.p = (sg + c.hdt * ud) / T(3);  // a division: a rounded 1/3 is a gain on p (see kW3)
     T C = (r - P.rho_v) * P.inv_drho;
     C = C < T(0) ? T(0) : (C > T(1) ? T(1) : C);
     const T s = C * P.inv_tau_l + (T(1) - C) * P.inv_tau_v;  // 1/tau
@@ -426,19 +435,19 @@ __device__ __forceinline__ Prep3<T> prep3(const Phys3<T> &P, T sg, const T *mg, 
 template <typename T>
 __device__ __forceinline__ void collide_pop3(const Prep3<T> &c, int a, T hs, T gs, T &hout, T &gout) {
     const T ex = T(e3x(a)), ey = T(e3y(a)), ez = T(e3z(a));
-    const T wa = w3<T>(a);
+    const T wa = w3<T>(a), w3a = w3x3<T>(a);
     const T eu = ex * c.u[0] + ey * c.u[1] + ez * c.u[2];
-    const T gmw = wa * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * c.uu);  // Gamma - w
-    const T gam = wa + gmw;
+    const T gmw = w3a * (eu + T(1.5) * eu * eu - T(0.5) * c.uu);  // Gamma - w
+    const T gam3 = w3a + T(3) * gmw;                             // 3 Gamma
     const T eX = ex * c.X[0] + ey * c.X[1] + ez * c.X[2];
     const T eD = ex * c.dr[0] + ey * c.dr[1] + ez * c.dr[2];
     const T eK = ex * c.K[0] + ey * c.K[1] + ez * c.K[2];
     const T edu = ex * c.du[0] + ey * c.du[1] + ez * c.du[2];
-    const T Fa = c.hdt * T(3) * (eX - c.uX) * gam;
-    const T Ga = c.hdt * (eD - c.uD) * gmw + c.hdt * T(3) * (eK - c.uK) * gam;
-    const T Ba = T(0.5) * c.r * wa * (T(3) * edu + T(4.5) * edu * (T(2) * eu + edu) - T(1.5) * c.udu);
+    const T Fa = c.hdt * (eX - c.uX) * gam3;
+    const T Ga = c.hdt * (eD - c.uD) * gmw + c.hdt * (eK - c.uK) * gam3;
+    const T Ba = T(0.5) * c.r * w3a * (edu + T(1.5) * edu * (T(2) * eu + edu) - T(0.5) * c.udu);
     const T dh = fma(c.r, wa, -hs) + c.r * gmw;
-    const T dg = fma(wa * T(3), c.p, -gs) + c.r * gmw;
+    const T dg = fma(w3a, c.p, -gs) + c.r * gmw;
     hout = hs + (c.omw * dh + c.opw * Fa);
     gout = gs + (c.omw * dg + c.opw * (Ga + Ba));
 }
@@ -452,26 +461,24 @@ __device__ __forceinline__ void collide_pair3(const Prep3<T> &c, int q, V2<T> hs
                                               V2<T> &go) {
     const int a = 2 * q + 1;
     const T ex = T(e3x(a)), ey = T(e3y(a)), ez = T(e3z(a));
-    const T wa = w3<T>(a);
+    const T wa = w3<T>(a), w3a = w3x3<T>(a);
     const T eu = ex * c.u[0] + ey * c.u[1] + ez * c.u[2];
     const T eX = ex * c.X[0] + ey * c.X[1] + ez * c.X[2];
     const T eD = ex * c.dr[0] + ey * c.dr[1] + ez * c.dr[2];
     const T eK = ex * c.K[0] + ey * c.K[1] + ez * c.K[2];
     const T edu = ex * c.du[0] + ey * c.du[1] + ez * c.du[2];
-    const T even = T(4.5) * eu * eu - T(1.5) * c.uu;
-    const V2<T> gmw = vfma(vset(T(3) * wa, T(3) * wa), vset(eu, -eu), vset(wa * even, wa * even));  // Gamma - w
-    const V2<T> gam = vadd(gmw, vset(wa, wa));
-    const T h3 = c.hdt * T(3);
-    const V2<T> Fa = vmul(vset(h3 * (eX - c.uX), h3 * (-eX - c.uX)), gam);
+    const T even = T(1.5) * eu * eu - T(0.5) * c.uu;
+    const V2<T> gmw = vfma(vset(w3a, w3a), vset(eu, -eu), vset(w3a * even, w3a * even));  // Gamma - w
+    const V2<T> gam3 = vfma(vset(T(3), T(3)), gmw, vset(w3a, w3a));                       // 3 Gamma
+    const V2<T> Fa = vmul(vset(c.hdt * (eX - c.uX), c.hdt * (-eX - c.uX)), gam3);
     const V2<T> Ga = vfma(vset(c.hdt * (eD - c.uD), c.hdt * (-eD - c.uD)), gmw,
-                          vmul(vset(h3 * (eK - c.uK), h3 * (-eK - c.uK)), gam));
-    const T bev = T(4.5) * edu * (T(2) * eu + edu) - T(1.5) * c.udu;
-    const T hrw = T(0.5) * c.r * wa;
-    const V2<T> Sg = vfma(vset(hrw, hrw), vset(T(3) * edu + bev, bev - T(3) * edu), Ga);  // G + B
+                          vmul(vset(c.hdt * (eK - c.uK), c.hdt * (-eK - c.uK)), gam3));
+    const T bev = T(1.5) * edu * (T(2) * eu + edu) - T(0.5) * c.udu;
+    const T hrw = T(0.5) * c.r * w3a;
+    const V2<T> Sg = vfma(vset(hrw, hrw), vset(edu + bev, bev - edu), Ga);  // G + B
     const V2<T> rg = vmul(vset(c.r, c.r), gmw);
-    const V2<T> dh = vadd(vfma(vset(c.r, c.r), vset(wa, wa), vset(-hs.x, -hs.y)), rg);  // h_eq - h*
-    const T p3 = wa * T(3) * c.p;
-    const V2<T> dg = vadd(vset(p3 - gs.x, p3 - gs.y), rg);  // g_eq - g*
+    const V2<T> dh = vadd(vfma(vset(c.r, c.r), vset(wa, wa), vset(-hs.x, -hs.y)), rg);   // h_eq - h*
+    const V2<T> dg = vadd(vfma(vset(w3a, w3a), vset(c.p, c.p), vset(-gs.x, -gs.y)), rg);  // g_eq - g*
     ho = vadd(hs, vfma(vset(c.omw, c.omw), dh, vmul(vset(c.opw, c.opw), Fa)));
     go = vadd(gs, vfma(vset(c.omw, c.omw), dg, vmul(vset(c.opw, c.opw), Sg)));
 }

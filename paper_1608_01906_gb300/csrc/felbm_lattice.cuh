@@ -273,29 +273,27 @@ __device__ __forceinline__ void collide_pair(const CollidePrep<T> &c, V2<T> hs, 
                                              V2<T> &go) {
     constexpr int A = pair_dir(Q, 0);
     constexpr int ex = kEx(A), ey = kEy(A);
-    constexpr T wa = kW<T>(A);
+    constexpr T wa = kW<T>(A), w3 = kW3<T>(A);
     const T eu = T(ex) * c.ux + T(ey) * c.uy;
     const T eX = T(ex) * c.Xx + T(ey) * c.Xy;
     const T eD = T(ex) * c.drx + T(ey) * c.dry;
     const T eK = T(ex) * c.kx + T(ey) * c.ky;
     const T edu = T(ex) * c.dux + T(ey) * c.duy;
-    // Gamma - w = w (3 e.u + 4.5 (e.u)^2 - 1.5 u.u), formed without the w
-    // offset (FP32: keeps the momentum part)
-    const T even = T(4.5) * eu * eu - T(1.5) * c.uu;
-    const V2<T> gmw = vfma(vset(T(3) * wa, T(3) * wa), vset(eu, -eu), vset(wa * even, wa * even));
-    const V2<T> gam = vadd(gmw, vset(wa, wa));
-    const T h3 = c.hdt * T(3);
-    const V2<T> Fa = vmul(vset(h3 * (eX - c.uX), h3 * (-eX - c.uX)), gam);
+    // Gamma - w = 3w (e.u + 1.5 (e.u)^2 - 0.5 u.u), formed without the w
+    // offset (FP32: keeps the momentum part); 3w from kW3
+    const T even = T(1.5) * eu * eu - T(0.5) * c.uu;
+    const V2<T> gmw = vfma(vset(w3, w3), vset(eu, -eu), vset(w3 * even, w3 * even));
+    const V2<T> gam3 = vfma(vset(T(3), T(3)), gmw, vset(w3, w3));  // 3 Gamma
+    const V2<T> Fa = vmul(vset(c.hdt * (eX - c.uX), c.hdt * (-eX - c.uX)), gam3);
     const V2<T> Ga = vfma(vset(c.hdt * (eD - c.uD), c.hdt * (-eD - c.uD)), gmw,
-                          vmul(vset(h3 * (eK - c.uK), h3 * (-eK - c.uK)), gam));
+                          vmul(vset(c.hdt * (eK - c.uK), c.hdt * (-eK - c.uK)), gam3));
     // 1/2 [g_eq(u + du) - g_eq(u)] = rho/2 [Gamma(u + du) - Gamma(u)]
-    const T bev = T(4.5) * edu * (T(2) * eu + edu) - T(1.5) * c.udu;
-    const T hrw = T(0.5) * c.r * wa;
-    const V2<T> Sg = vfma(vset(hrw, hrw), vset(T(3) * edu + bev, bev - T(3) * edu), Ga);
+    const T bev = T(1.5) * edu * (T(2) * eu + edu) - T(0.5) * c.udu;
+    const T hrw = T(0.5) * c.r * w3;
+    const V2<T> Sg = vfma(vset(hrw, hrw), vset(edu + bev, bev - edu), Ga);
     const V2<T> rg = vmul(vset(c.r, c.r), gmw);
     const V2<T> dh = vadd(vfma(vset(c.r, c.r), vset(wa, wa), vset(-hs.x, -hs.y)), rg);  // h_eq - h*
-    const T p3 = wa * T(3) * c.p;
-    const V2<T> dg = vadd(vset(p3 - gs.x, p3 - gs.y), rg);  // g_eq - g*
+    const V2<T> dg = vadd(vfma(vset(w3, w3), vset(c.p, c.p), vset(-gs.x, -gs.y)), rg);  // g_eq - g*
     ho = vadd(hs, vfma(vset(c.omw, c.omw), dh, vmul(vset(c.opw, c.opw), Fa)));
     go = vadd(gs, vfma(vset(c.omw, c.omw), dg, vmul(vset(c.opw, c.opw), Sg)));
 }

@@ -2,11 +2,13 @@
 
 Tolerances (relative L2 over all nodes, per field):
 * FP64 GPU run: <= 1e-12 (reordered sums only).
-* FP32 GPU run after 1000 steps: the target is 1e-5 in velocity and C.  C
-  holds it with a wide margin (1.3e-7 at density ratio 10, 1.6e-7 at ratio
-  1000: the collision is formed as an increment and keeps each node's mass
-  to one rounding).  Velocity does not: 1.3e-5 at ratio 10 and 6.3e-5 at
-  ratio 1000.  These tests hold the measured levels as regression bounds.
+* FP32 GPU run after 1000 steps: <= 1e-5 in velocity and C.  Measured: C
+  1.3e-7 (ratio 10) and 9.4e-8 (ratio 1000), u 1.2e-6 to 1.5e-6 (ratio 10)
+  and 5.5e-6 (ratio 1000).  The collision keeps each node's mass to one
+  rounding, and its 3 w_a constants satisfy the equilibrium moment
+  identities exactly in FP32 (p by a division by 3): with the nearest
+  rounded weights and c_s^2 the pressure and momentum of g gain about 1e-8
+  per step, 1.3e-5 and 6.3e-5 in u after 1000 steps.
 """
 import numpy as np
 import pytest
@@ -145,15 +147,15 @@ def test_fp64_layered_channel_walls():
 def test_fp32_layered_channel_steady_profile():
     # 20,000 FP32 steps to the steady profile against the FP64 oracle.  The
     # bulk densities drift slowly towards the discrete equilibrium over the
-    # run, and FP32 rounding of that drift leaves rho 7.3e-6, C 1.7e-5 and u
-    # 1.05e-4 relative L2 (measured); held as regression bounds
+    # run, and FP32 rounding of that drift leaves rho 7.2e-6, C 1.7e-5 and u
+    # 5.5e-6 relative L2 (measured); held as regression bounds
     prob = _layered_channel()
     m, kind = run_gpu(prob, "fp32", 20000)
     o = run_oracle(prob, 20000)
     e = errors(m, o)
     dp = np.abs(m["p"] - o.p).max() / (1.0 / 3.0)
     print("channel fp32 errors", e, "max|dp| / c_s^2", dp)
-    assert e["rho"] <= 2e-5 and e["C"] <= 5e-5 and e["u"] <= 3e-4 and dp <= 1e-6, (e, dp)
+    assert e["rho"] <= 2e-5 and e["C"] <= 5e-5 and e["u"] <= 2e-5 and dp <= 1e-6, (e, dp)
 
 
 def test_fp64_mass_momentum_conserved_gpu():
@@ -174,7 +176,7 @@ def test_fp32_droplet_1000_steps(general):
     o = run_oracle(prob, 1000)
     e = errors(m, o)
     print("fp32 1000-step errors", e)
-    assert e["C"] <= 1e-6 and e["u"] <= 2e-5, e
+    assert e["C"] <= 1e-6 and e["u"] <= 1e-5, e
 
 
 @pytest.mark.parametrize("nx,ny", [(40, 40), (38, 30)])
@@ -247,4 +249,4 @@ def test_fullsize_unstructured_fp32_1000_steps():
     o = run_oracle(prob, 1000)
     e = errors(m, o)
     print("c2 1000-step fp32 errors", e)
-    assert e["C"] <= 1e-6 and e["u"] <= 1e-4, e
+    assert e["C"] <= 1e-6 and e["u"] <= 1e-5, e
