@@ -110,7 +110,7 @@ def test_fp32_droplet_1000_steps(general):
     o = run_oracle(case, 1000)
     e = errors(m, o)
     print("3-D fp32 1000 steps", e)
-    # measured: rho 1.8e-7, C 2.9e-7, u 1.5e-6, p 5.7e-6
+    # measured: rho 2.1e-7, C 3.4e-7, u 1.2e-6, p 1.7e-6 (lattice kernels)
     assert e["rho"] <= 1e-6 and e["C"] <= 1e-6 and e["u"] <= 1e-5 and e["p"] <= 2e-5, e
 
 
