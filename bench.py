@@ -75,6 +75,25 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(x, dist=None, device="cpu"):
+    """The largest per-rank value of x over all ranks (every rank gets it):
+    the slowest rank sets the job's time.  dist: torch.distributed with an
+    initialised process group, or None for one process."""
+    if dist is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, nodes, steps, seconds):
+    """Whole-job MNUPS: the node updates of all ranks (each runs its own
+    replica of nodes x steps) over the slowest rank's time."""
+    return world * nodes * steps / seconds / 1e6
+
+
 # Sources that determine a kernel's code (its ncu counters stay valid while
 # these are unchanged); kernels not listed depend on every source.
 KERNEL_SOURCES = {
@@ -394,11 +413,9 @@ def main():
     prof = st.profile_read()
     st.sync()
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+        ms = max_over_ranks(ms, dist, "cuda")
         dist.barrier()
-    value = world * prob.n_nodes * args.steps / (ms * 1e-3) / 1e6
+    value = job_rate(world, prob.n_nodes, args.steps, ms * 1e-3)
     launches = int(sum(v[2] for v in prof.values()))
 
     # ---- dominant kernel roofline (event-timed launches of the region).  A
@@ -464,11 +481,8 @@ def main():
     mom = st2.moments()
     t1 = time.perf_counter()
     st2.close()
-    e2e_val = world * prob.n_nodes * args.steps / (t1 - t0) / 1e6
-    if dist:
-        t = torch.tensor([t1 - t0], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_val = world * prob.n_nodes * args.steps / float(t.item()) / 1e6
+    e2e_val = job_rate(world, prob.n_nodes, args.steps,
+                       max_over_ranks(t1 - t0, dist, "cuda") if dist else t1 - t0)
     n = prob.n_nodes
     h2d = (n * 8 + dim * n * 8 + n * 8) / args.steps          # rho0, u0, p0
     d2h = ((3 + dim) * n * 8 + (1 + dim) * 8) / args.steps  # rho, C, u, p, totals
