@@ -28,3 +28,37 @@ def test_status_strings_need_no_gpu():
     felbm.load()
     assert felbm.status_string(0) == "ok"
     assert "mesh" in felbm.status_string(felbm.FELBM_ERR_INVALID_MESH)
+
+
+def test_tet_mesh_validation_needs_no_gpu():
+    """felbm_mesh_create_tet rejects bad arguments and mis-oriented
+    tetrahedra on the host, before any device work."""
+    import numpy as np
+
+    from paper_1608_01906_gb300 import inputs
+
+    felbm.load()
+    xyz, tet, box, _ = inputs.structured_tet_mesh(4, 4, 4)
+    flags = felbm.FELBM_PERIODIC_X | felbm.FELBM_PERIODIC_Y | felbm.FELBM_PERIODIC_Z
+    bad = tet.copy()
+    bad[5] = bad[5][[1, 0, 2, 3]]  # two vertices swapped: negative volume
+    st, _ = felbm.felbm_mesh_create_tet(xyz, bad, box, flags)
+    assert st == felbm.FELBM_ERR_INVALID_MESH
+    out_of_range = tet.copy()
+    out_of_range[0, 0] = len(xyz)
+    st, _ = felbm.felbm_mesh_create_tet(xyz, out_of_range, box, flags)
+    assert st == felbm.FELBM_ERR_INVALID_MESH
+    repeated = tet.copy()
+    repeated[0, 1] = repeated[0, 0]
+    st, _ = felbm.felbm_mesh_create_tet(xyz, repeated, box, flags)
+    assert st == felbm.FELBM_ERR_INVALID_MESH
+    st, _ = felbm.felbm_mesh_create_tet(xyz, tet, np.array([4.0, 4.0, 0.0]), flags)  # flagged period 0
+    assert st == felbm.FELBM_ERR_INVALID_ARG
+    st, _ = felbm.felbm_mesh_create_tet(xyz, tet, box, flags | 0x100)  # unknown flag bit
+    assert st == felbm.FELBM_ERR_INVALID_ARG
+    st, _ = felbm.felbm_mesh_create_tet(xyz[:3], tet[:0], box, flags)  # n_nodes < 4, no elements
+    assert st == felbm.FELBM_ERR_INVALID_ARG
+    nan = xyz.copy()
+    nan[2, 1] = np.nan
+    st, _ = felbm.felbm_mesh_create_tet(nan, tet, box, flags)
+    assert st == felbm.FELBM_ERR_INVALID_MESH

@@ -177,3 +177,31 @@ def test_lattice_matches_csr_fp32():
         assert rel_l2(out[0][k], out[1][k]) <= 2e-6, (k, rel_l2(out[0][k], out[1][k]))
     # p is O(1e-5) here: compare it on the c_s^2 scale
     assert np.abs(out[0]["p"] - out[1]["p"]).max() <= 1e-8 / 3.0
+
+
+@pytest.mark.parametrize("general", [False, True])
+def test_nonfinite_detected_3d(general):
+    """An unstable time step blows the 3-D state up to inf/nan without a
+    fault; the step's flag reports it."""
+    xyz, tet, box, _ = inputs.structured_tet_mesh(8, 8, 8)
+    rho0, u, p0 = inputs.droplet_fields3(xyz, box, (4.0, 4.0, 4.0), 2.5, 1.0, 0.25, 2.0)
+    mesh = felbm.Mesh(xyz, tet, box, general=general)
+    st = felbm.State(mesh, felbm.make_params(1.0, 0.25, 0.01, 2.0, 0.5, 0.5, 3.0, precision="fp32"),
+                     rho0, u, p0)
+    st.step(2000)
+    assert felbm.felbm_state_sync(st.handle) == felbm.FELBM_ERR_NONFINITE
+    st.close()
+    mesh.close()
+
+
+def test_batch_rejects_tetrahedral_states():
+    xyz, tet, box, _ = inputs.structured_tet_mesh(6, 6, 6)
+    rho0, u, p0 = inputs.droplet_fields3(xyz, box, (3.0, 3.0, 3.0), 2.0, 1.0, 0.5, 2.0)
+    mesh = felbm.Mesh(xyz, tet, box)
+    st = felbm.State(mesh, felbm.make_params(1.0, 0.5, 0.01, 2.0, 0.5, 0.5, 0.5, precision="fp32"),
+                     rho0, u, p0)
+    with pytest.raises(felbm.FelbmError) as exc:
+        felbm.Batch([st])
+    assert exc.value.status == felbm.FELBM_ERR_UNSUPPORTED
+    st.close()
+    mesh.close()
