@@ -45,6 +45,9 @@ struct BatchArgs {
     unsigned *ctr;  // 2 tile counters, by parity
     int parity;
     int write_mom;
+    // the coefficient tables of every mesh when they are all the same (same
+    // lattice spacing and dt): read as kernel parameters by the SC kernels
+    LatCoef<T> c;
 };
 
 template <typename T>
@@ -68,8 +71,19 @@ __device__ __forceinline__ void load_mesh(const BatchArgs<T> &B, int m, LatArgs<
     cur = m;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kNT, (sizeof(T) == 4 ? 768 : 512) / kNT) k_batch_step(BatchArgs<T> B) {
+// SC: all meshes share B.c (interior tiles then read the coefficients as
+// constant operands, as the single-mesh step does), else each mesh's own
+// tables from its shared-memory descriptor.
+template <typename T, bool SC>
+__device__ __forceinline__ const LatCoef<T> &batch_coef(const BatchArgs<T> &B, const LatArgs<T> &sA) {
+    if constexpr (SC)
+        return B.c;
+    else
+        return sA.c;
+}
+
+template <typename T, bool SC>
+__global__ void __launch_bounds__(kNT, (sizeof(T) == 4 ? 768 : 512) / kNT) k_batch_step(const __grid_constant__ BatchArgs<T> B) {
     __shared__ StepSmem<T> S;
     __shared__ __align__(16) LatArgs<T> sA;
     extern __shared__ __align__(128) unsigned char bdsm[];
@@ -97,7 +111,7 @@ __global__ void __launch_bounds__(kNT, (sizeof(T) == 4 ? 768 : 512) / kNT) k_bat
                 next.tma = rn.mesh == r.mesh && tile_tma(sA, rn.bx, rn.by, bdsm);
             }
         }
-        if (!lat_tile<T>(sA, r.bx, r.by, S, bdsm, pp, next)) return;
+        if (!lat_tile<T>(sA, batch_coef<T, SC>(B, sA), r.bx, r.by, S, bdsm, pp, next)) return;
         if (!take_next(S, pp)) return;
         t = S.nt[0];
     }
@@ -106,8 +120,8 @@ __global__ void __launch_bounds__(kNT, (sizeof(T) == 4 ? 768 : 512) / kNT) k_bat
 // One block per tile of the batch's tile list, at the register budget of
 // the single-mesh step (4 blocks per SM in FP32).  Zeroes both tile counters,
 // so that a walking launch after it starts from zero.
-template <typename T>
-__global__ void __launch_bounds__(kNT, (sizeof(T) == 4 ? 1024 : 512) / kNT) k_batch_tile(BatchArgs<T> B) {
+template <typename T, bool SC>
+__global__ void __launch_bounds__(kNT, (sizeof(T) == 4 ? 1024 : 512) / kNT) k_batch_tile(const __grid_constant__ BatchArgs<T> B) {
     __shared__ StepSmem<T> S;
     __shared__ __align__(16) LatArgs<T> sA;
     extern __shared__ __align__(128) unsigned char bdsm[];
@@ -121,7 +135,7 @@ __global__ void __launch_bounds__(kNT, (sizeof(T) == 4 ? 1024 : 512) / kNT) k_ba
     load_mesh<T>(B, r.mesh, sA, cur);
     TilePipe pp;
     const NextTile none{0, 0, 0, false, false};
-    lat_tile<T>(sA, r.bx, r.by, S, bdsm, pp, none);
+    lat_tile<T>(sA, batch_coef<T, SC>(B, sA), r.bx, r.by, S, bdsm, pp, none);
 }
 
 template <typename T>
@@ -187,6 +201,8 @@ struct felbm_batch {
     int64_t launches = 0;
     std::vector<TileRef> tiles_mesh_major, tiles_interleaved;
     std::vector<int> c0;  // each state's current buffer when descriptors were built
+    bool shared_coef = false;          // every mesh has the same coefficient tables
+    std::vector<unsigned char> coef;   // those tables (LatCoef of the batch's precision)
 };
 
 static int b_status(cudaError_t e) {
@@ -211,12 +227,22 @@ static cudaError_t batch_launch(felbm_batch *b, int parity, int write_mom) {
     B.ctr = b->d_ctr;
     B.parity = parity;
     B.write_mom = write_mom;
+    std::memset(&B.c, 0, sizeof(B.c));
+    if (b->shared_coef) std::memcpy(&B.c, b->coef.data(), sizeof(B.c));
     b->launches++;
-    if (b->bps > 0)
-        k_batch_step<T><<<(unsigned)(b->bps * b->sm_count), dim3(kLTX, kLTY), batch_smem(sizeof(T)),
-                          b->stream>>>(B);
-    else
-        k_batch_tile<T><<<(unsigned)b->ntiles, dim3(kLTX, kLTY), batch_smem(sizeof(T)), b->stream>>>(B);
+    const dim3 blk(kLTX, kLTY);
+    const size_t sm = batch_smem(sizeof(T));
+    if (b->bps > 0) {
+        const unsigned grid = (unsigned)(b->bps * b->sm_count);
+        if (b->shared_coef)
+            k_batch_step<T, true><<<grid, blk, sm, b->stream>>>(B);
+        else
+            k_batch_step<T, false><<<grid, blk, sm, b->stream>>>(B);
+    } else if (b->shared_coef) {
+        k_batch_tile<T, true><<<(unsigned)b->ntiles, blk, sm, b->stream>>>(B);
+    } else {
+        k_batch_tile<T, false><<<(unsigned)b->ntiles, blk, sm, b->stream>>>(B);
+    }
     return cudaGetLastError();
 }
 
@@ -283,19 +309,29 @@ static int setup_meshes(felbm_batch *b) {
         bm.c0 = s->cur;
         b->c0[k] = s->cur;
     }
+    b->shared_coef = true;
+    for (size_t k = 1; k < n; ++k)
+        if (std::memcmp(&hm[k].a.c, &hm[0].a.c, sizeof(LatCoef<T>)) != 0) b->shared_coef = false;
+    if (n) {
+        const unsigned char *c = reinterpret_cast<const unsigned char *>(&hm[0].a.c);
+        b->coef.assign(c, c + sizeof(LatCoef<T>));
+    }
     return b_status(cudaMemcpy(b->d_meshes, hm.data(), n * sizeof(BatchMesh<T>), cudaMemcpyHostToDevice));
 }
 
 template <typename T>
 static int occupancy(felbm_batch *b) {
     int bps = 0;
-    cudaError_t e = cudaFuncSetAttribute(k_batch_tile<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)batch_smem(sizeof(T)));
+    const int sm = (int)batch_smem(sizeof(T));
+    cudaError_t e = cudaFuncSetAttribute(k_batch_tile<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_batch_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)batch_smem(sizeof(T)));
+        e = cudaFuncSetAttribute(k_batch_tile<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_batch_step<T>, kLTX * kLTY,
+        e = cudaFuncSetAttribute(k_batch_step<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_batch_step<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_batch_step<T, false>, kLTX * kLTY,
                                                           batch_smem(sizeof(T)));
     if (e != cudaSuccess) return b_status(e);
     b->max_bps = std::max(1, bps);

@@ -377,7 +377,8 @@ __device__ __forceinline__ bool tile_unwrapped(int x0, int y0, int nx, int ny) {
 // Collision of one node: the g pairs are streamed here from their depth-1
 // tiles, the h pairs were streamed by the density stage.
 template <typename T>
-__device__ __forceinline__ void lat_node(const LatArgs<T> &A, int k, int lx, int ly, int tid, int32_t i,
+__device__ __forceinline__ void lat_node(const LatArgs<T> &A, const LatCoef<T> &C, int k, int lx, int ly,
+                                         int tid, int32_t i,
                                          size_t ip, size_t n, size_t np, T h0, T g0, T r0, T drx, T dry,
                                          T dmx, T dmy, T kx, T ky, const V2<T> *gT,
                                          const V2<T> (*s_psi)[kNT]) {
@@ -387,7 +388,7 @@ __device__ __forceinline__ void lat_node(const LatArgs<T> &A, int k, int lx, int
     V2<T> gq[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q)
-        gq[q] = bounce_pair<T>(k, q, stream_pair<T, PG::W>(A.c, k, q, gT + q * PG::N, c, P.dt));
+        gq[q] = bounce_pair<T>(k, q, stream_pair<T, PG::W>(C, k, q, gT + q * PG::N, c, P.dt));
     T sg, mx, my;
     // g_1 = q0.x, g_3 = q0.y, g_2 = q1.x, g_4 = q1.y, g_5 = q2.x, g_7 = q2.y, g_6 = q3.x, g_8 = q3.y
     g_moments<T>(g0, gq[0].x, gq[1].x, gq[0].y, gq[1].y, gq[2].x, gq[3].x, gq[2].y, gq[3].y, sg, mx, my);
@@ -484,11 +485,14 @@ __device__ __noinline__ bool tma_gave_up(const LatArgs<T> &A, StepSmem<T> &S, co
 
 // One time step of tile (bx, by).  TMA: the halo windows come as TMA boxes
 // (tile_unwrapped, interior tiles) completing on S.bar, else as cp.async
-// fills.  Returns false (all threads alike) when a bounded wait for a TMA
-// load gave up; the flag then carries bit 2.
+// fills.  C: the mesh's coefficient tables (kernel parameters where they
+// can be, so that interior tiles read them as constant operands).  Returns
+// false (all threads alike) when a bounded wait for a TMA load gave up; the
+// flag then carries bit 2.
 template <typename T, bool INTERIOR, bool TMA>
-__device__ __forceinline__ bool lat_tile_impl(const LatArgs<T> &A, int bx, int by, StepSmem<T> &S,
-                                              unsigned char *dsm, TilePipe &pp, const NextTile &next) {
+__device__ __forceinline__ bool lat_tile_impl(const LatArgs<T> &A, const LatCoef<T> &C, int bx, int by,
+                                              StepSmem<T> &S, unsigned char *dsm, TilePipe &pp,
+                                              const NextTile &next) {
     using L = LatSmem<T>;
     using PH = PairTile<T, kHD>;
     auto &s_rho = S.s_rho;
@@ -560,7 +564,7 @@ __device__ __forceinline__ bool lat_tile_impl(const LatArgs<T> &A, int bx, int b
             r = s_h0[ry][rx + 1];
 #pragma unroll
             for (int p = 0; p < 4; ++p) {
-                const V2<T> v = bounce_pair<T>(k, p, stream_pair<T, PH::W>(A.c, k, p, hT + p * PH::N, c, dt));
+                const V2<T> v = bounce_pair<T>(k, p, stream_pair<T, PH::W>(C, k, p, hT + p * PH::N, c, dt));
                 r += v.x + v.y;
                 if (own) s_psi[p][o] = v;
             }
@@ -578,7 +582,7 @@ __device__ __forceinline__ bool lat_tile_impl(const LatArgs<T> &A, int bx, int b
         S.nt[2] = next.by;
         S.nt[3] = (next.valid ? 1 : 0) | (next.tma ? 2 : 0);
     }
-    const auto &rc = A.c.r;  // recovery coefficients
+    const auto &rc = C.r;  // recovery coefficients
     // 2. recovered grad rho on the depth-2 region
     for (int q = tid; q < kGW * kGH; q += kNT) {
         const int ly = q / kGW, lx = q - ly * kGW;
@@ -649,7 +653,7 @@ __device__ __forceinline__ bool lat_tile_impl(const LatArgs<T> &A, int bx, int b
         __syncthreads();
     }
     if (valid)
-        lat_node<T>(A, k, lx, ly, tid, i, ip, n, np, h0, g0, r0, drx, dry, dmx, dmy, kx, ky, gT, s_psi);
+        lat_node<T>(A, C, k, lx, ly, tid, i, ip, n, np, h0, g0, r0, drx, dry, dmx, dmy, kx, ky, gT, s_psi);
     __syncthreads();  // the caller may reuse shared memory for the next tile
     return true;
 }
@@ -677,12 +681,12 @@ __device__ __forceinline__ bool tile_tma(const LatArgs<T> &A, int bx, int by, co
 // this tile's h group was already requested; next is the block's next tile).
 // False when a bounded wait gave up.
 template <typename T>
-__device__ __forceinline__ bool lat_tile(const LatArgs<T> &A, int bx, int by, StepSmem<T> &S,
+__device__ __forceinline__ bool lat_tile(const LatArgs<T> &A, const LatCoef<T> &C, int bx, int by, StepSmem<T> &S,
                                          unsigned char *dsm, TilePipe &pp, const NextTile &next) {
-    if (tile_tma(A, bx, by, dsm)) return lat_tile_impl<T, true, true>(A, bx, by, S, dsm, pp, next);
+    if (tile_tma(A, bx, by, dsm)) return lat_tile_impl<T, true, true>(A, C, bx, by, S, dsm, pp, next);
     if (tile_interior(bx * kLTX, by * kLTY, A.nx, A.ny, A.walls))
-        return lat_tile_impl<T, true, false>(A, bx, by, S, dsm, pp, next);
-    return lat_tile_impl<T, false, false>(A, bx, by, S, dsm, pp, next);
+        return lat_tile_impl<T, true, false>(A, C, bx, by, S, dsm, pp, next);
+    return lat_tile_impl<T, false, false>(A, C, bx, by, S, dsm, pp, next);
 }
 
 // After a tile: the published next tile (false: none), and whether its h
@@ -705,7 +709,7 @@ __global__ void __launch_bounds__(kNT, (sizeof(T) == 4 ? 1024 : 512) / kNT) k_la
     lat_block_init<T>(S);
     TilePipe pp;
     const NextTile none{0, 0, 0, false, false};
-    lat_tile<T>(A, blockIdx.x, blockIdx.y, S, lat_dsm, pp, none);
+    lat_tile<T>(A, A.c, blockIdx.x, blockIdx.y, S, lat_dsm, pp, none);
 }
 
 }  // namespace felbm
