@@ -38,9 +38,19 @@ def make_state(prob, precision):
     return mesh, st
 
 
+def periodic_problems():
+    # periodic unit lattices with one dt: every mesh has the same coefficient
+    # tables, which the batched kernels then take as kernel parameters
+    return [configs.droplet_structured(40, 10.0, 10.0, xi=4.0),
+            configs.droplet_structured(64, 20.0, 300.0, xi=configs.DROPLET_XI, tau_l=0.1, tau_v=0.1),
+            configs.droplet_structured(33, 9.0, 1000.0, xi=configs.DROPLET_XI, tau_l=0.1, tau_v=0.1),
+            configs.droplet_structured(97, 30.0, 50.0, xi=configs.DROPLET_XI, tau_l=0.2, tau_v=0.1)]
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
-def test_batch_equals_standalone_bitwise(precision):
-    probs = mixed_problems()
+@pytest.mark.parametrize("which", ["mixed", "periodic"])
+def test_batch_equals_standalone_bitwise(precision, which):
+    probs = mixed_problems() if which == "mixed" else periodic_problems()
     alone = []
     for p in probs:
         mesh, st = make_state(p, precision)
