@@ -145,17 +145,23 @@ static DevLattice<T> dev_lattice(const felbm_mesh *m) {
 
 // Derivative chain shared by init and step: rho (already in F.rho) ->
 // grad rho -> lap rho, K, mu.
+// Threads per block of the general path's node kernels (one node per
+// thread).  On the 256 x 256 Delaunay mesh (65,536 nodes, fewer blocks than
+// two per SM) blocks of 128 and 64 threads spread the mesh more evenly but
+// ran 3-7% slower than 256.
+constexpr int kGenBlock = 256;
+
 template <typename T, typename Topo>
 static void launch_chain(felbm_state *s, const Topo &d) {
     const felbm_mesh *m = s->mesh;
     const Fields<T> F = fields_of<T>(s);
     const Phys<T> P = phys_of<T>(s->params);
-    const unsigned g = nblocks(m->n_nodes, 256);
+    const unsigned g = nblocks(m->n_nodes, kGenBlock);
     int sl = prof_begin(s, 1);
-    k_grad<T, Topo><<<g, 256, 0, m->stream>>>(d, F);
+    k_grad<T, Topo><<<g, kGenBlock, 0, m->stream>>>(d, F);
     prof_end(s, sl);
     sl = prof_begin(s, 2);
-    k_mu<T, Topo><<<g, 256, 0, m->stream>>>(d, F, P);
+    k_mu<T, Topo><<<g, kGenBlock, 0, m->stream>>>(d, F, P);
     prof_end(s, sl);
 }
 
@@ -164,11 +170,11 @@ static void step_topo(felbm_state *s, const Topo &d, bool write_mom) {
     const felbm_mesh *m = s->mesh;
     const Fields<T> F = fields_of<T>(s);
     const Phys<T> P = phys_of<T>(s->params);
-    const unsigned g = nblocks(m->n_nodes, 256);
+    const unsigned g = nblocks(m->n_nodes, kGenBlock);
     const T *fin = reinterpret_cast<const T *>(s->f[s->cur]);
     T *fout = reinterpret_cast<T *>(s->f[s->cur ^ 1]);
     int sl = prof_begin(s, 0);
-    k_rho<T, Topo><<<g, 256, 0, m->stream>>>(d, fin, P.dt, F.rho, F.hs);
+    k_rho<T, Topo><<<g, kGenBlock, 0, m->stream>>>(d, fin, P.dt, F.rho, F.hs);
     prof_end(s, sl);
     launch_chain<T, Topo>(s, d);
     CollideArgs<T, Topo> A;
@@ -180,7 +186,7 @@ static void step_topo(felbm_state *s, const Topo &d, bool write_mom) {
     A.mom = write_mom ? reinterpret_cast<T *>(s->mom) : nullptr;
     A.flag = s->d_flag;
     sl = prof_begin(s, 3);
-    k_collide<T, Topo><<<g, 256, 0, m->stream>>>(A);
+    k_collide<T, Topo><<<g, kGenBlock, 0, m->stream>>>(A);
     prof_end(s, sl);
     s->cur ^= 1;
 }
@@ -194,8 +200,8 @@ static void init_topo(felbm_state *s, const Topo &d) {
     cudaMemcpyAsync(F.rho, s->mom, (size_t)m->n_nodes * sizeof(T), cudaMemcpyDeviceToDevice,
                     m->stream);
     launch_chain<T, Topo>(s, d);
-    const unsigned g = nblocks(m->n_nodes, 256);
-    k_init<T, Topo><<<g, 256, 0, m->stream>>>(d, reinterpret_cast<T *>(s->f[s->cur]), F, P,
+    const unsigned g = nblocks(m->n_nodes, kGenBlock);
+    k_init<T, Topo><<<g, kGenBlock, 0, m->stream>>>(d, reinterpret_cast<T *>(s->f[s->cur]), F, P,
                                               reinterpret_cast<const T *>(s->mom));
 }
 
