@@ -1,5 +1,6 @@
 // C ABI of the FE-LBM library: handle management, uploads, launches.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -244,16 +245,28 @@ static void step_lattice(felbm_state *s, LatArgs<T> &A, bool write_mom) {
     s->cur ^= 1;
 }
 
+// The dynamic shared memory of k_lat_step is above the default limit: set
+// the function attribute once per device (bit d of done; devices from 64 on
+// set it at every call).
+template <typename T>
+static void lat_smem_attr() {
+    static std::atomic<uint64_t> done{0};
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        dev = -1;
+    }
+    const uint64_t bit = (dev >= 0 && dev < 64) ? (uint64_t(1) << dev) : 0;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return;
+    cudaFuncSetAttribute(k_lat_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lat_smem<T>());
+    if (bit) done.fetch_or(bit, std::memory_order_release);
+}
+
 template <typename T>
 static void do_steps(felbm_state *s, int64_t n) {
     const felbm_mesh *m = s->mesh;
     if (m->kind == 1) {
-        static bool attr_set = false;  // once per instantiation (per process)
-        if (!attr_set) {
-            cudaFuncSetAttribute(k_lat_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)lat_smem<T>());
-            attr_set = true;
-        }
+        lat_smem_attr<T>();
         LatArgs<T> A;
         A.nx = m->sinfo.nx;
         A.ny = m->sinfo.ny;
