@@ -62,3 +62,33 @@ def test_tet_mesh_validation_needs_no_gpu():
     nan[2, 1] = np.nan
     st, _ = felbm.felbm_mesh_create_tet(nan, tet, box, flags)
     assert st == felbm.FELBM_ERR_INVALID_MESH
+
+
+def test_size_limits_and_null_pointers_need_no_gpu():
+    """Sizes above 2^31 - 1 and NULL pointers are rejected before any array
+    is read (the arrays passed here are far smaller than the sizes claimed)."""
+    import ctypes as C
+
+    import numpy as np
+
+    lib = felbm.load()
+    xy = np.zeros((4, 3))
+    tri = np.zeros((2, 4), dtype=np.int32)
+    box = np.ones(3)
+    out = C.c_void_p()
+    p = lambda a: a.ctypes.data_as(C.c_void_p)
+    flags = felbm.FELBM_PERIODIC_X | felbm.FELBM_PERIODIC_Y
+    big = 1 << 31
+    assert lib.felbm_mesh_create(p(xy), big, p(tri), 1, p(box), flags, None, None,
+                                 C.byref(out)) == felbm.FELBM_ERR_INVALID_ARG
+    assert lib.felbm_mesh_create(p(xy), 3, p(tri), big, p(box), flags, None, None,
+                                 C.byref(out)) == felbm.FELBM_ERR_INVALID_ARG
+    assert lib.felbm_mesh_create(None, 3, p(tri), 1, p(box), flags, None, None,
+                                 C.byref(out)) == felbm.FELBM_ERR_INVALID_ARG
+    assert lib.felbm_mesh_create_tet(p(xy), big, p(tri), 1, p(box), flags, None, None,
+                                     C.byref(out)) == felbm.FELBM_ERR_INVALID_ARG
+    assert lib.felbm_mesh_create_tet(p(xy), 4, p(tri), 1, p(box), flags, None, None,
+                                     None) == felbm.FELBM_ERR_INVALID_ARG
+    v = C.c_double()
+    assert lib.felbm_alu_peak(0, None) == felbm.FELBM_ERR_INVALID_ARG
+    assert lib.felbm_alu_peak(-1, C.byref(v)) == felbm.FELBM_ERR_INVALID_ARG
