@@ -216,12 +216,15 @@ void felbm_state_destroy(felbm_state *state);
  * times real steps under each candidate (a persistent grid of 1 to the
  * co-resident maximum blocks per SM, or one block per tile, reported as 0;
  * tile order mesh-major or interleaved) and keeps the fastest; those steps
- * count toward n_steps.
+ * count toward n_steps.  When every member has the same coefficient tables
+ * (same lattice spacing and dt, and the same walls), the launch carries them
+ * once as kernel parameters; otherwise each tile reads its mesh's tables.
+ * Results are the same either way.
  *   states   n_states distinct states, same precision, meshes on the same
  *            stream; the batch borrows them (they must outlive it).
  * Stepping a member state on its own between batch steps is allowed; the
  * next felbm_batch_step then waits for the stream and rebuilds its tables.
- * Errors: INVALID_ARG, UNSUPPORTED (a general mesh), OOM, CUDA; NONFINITE
+ * Errors: INVALID_ARG, UNSUPPORTED (a general or tetrahedral mesh), OOM, CUDA; NONFINITE
  * (or TIMEOUT) from felbm_batch_sync as a member's felbm_state_sync reports
  * it. */
 #define FELBM_BATCH_AUTOTUNE 0x1u
