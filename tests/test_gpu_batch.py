@@ -47,10 +47,17 @@ def periodic_problems():
             configs.droplet_structured(97, 30.0, 50.0, xi=configs.DROPLET_XI, tau_l=0.2, tau_v=0.1)]
 
 
+def walled_problems():
+    # Rayleigh-Taylor layers of different sizes with one dt: shared tables
+    # whose wall-row kinds are read at run time
+    return [configs.c3_rayleigh_taylor(nx=48, ny=100), configs.c3_rayleigh_taylor(nx=48, ny=64),
+            configs.c3_rayleigh_taylor(nx=48, ny=41)]
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
-@pytest.mark.parametrize("which", ["mixed", "periodic"])
+@pytest.mark.parametrize("which", ["mixed", "periodic", "walled"])
 def test_batch_equals_standalone_bitwise(precision, which):
-    probs = mixed_problems() if which == "mixed" else periodic_problems()
+    probs = {"mixed": mixed_problems, "periodic": periodic_problems, "walled": walled_problems}[which]()
     alone = []
     for p in probs:
         mesh, st = make_state(p, precision)
