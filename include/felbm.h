@@ -169,7 +169,8 @@ void felbm_mesh_destroy(felbm_mesh *mesh);
  *   p0    host, n_nodes doubles or NULL for zero pressure.
  * Device memory: 2 x 18 n_nodes values of the chosen precision plus scratch
  * (2 x 38 n_nodes on tetrahedral meshes)
- * (structured meshes with nx % 4 == 0: also 768 bytes of TMA tensor maps).
+ * (structured meshes: also 768 bytes of TMA tensor maps; rows are padded to
+ * a multiple of 4 slots, so every width qualifies).
  * Errors: INVALID_ARG, OOM, CUDA. */
 int felbm_state_init(const felbm_mesh *mesh, const felbm_params *params, const double *rho0,
                      const double *u0, const double *p0, felbm_state **out);
@@ -280,8 +281,10 @@ const char *felbm_profile_kind_name(int k);
  *   stream       cudaStream_t (as void*) the work is issued on; NULL = the
  *                legacy default stream.  The call returns after enqueueing.
  * The first call on a device, with that device current, looks up the device
- * address of the scratch array; make that first call before any stream
- * capture.  All calls on a device share the one scratch array and leave
+ * address of the scratch array and keeps it for the life of the process;
+ * make that first call before any stream capture, and do not use this entry
+ * point on a device after cudaDeviceReset (the device image is reloaded and
+ * the kept address no longer names the array).  All calls on a device share the one scratch array and leave
  * their partial sums in it (each call writes every slot it reads, so nothing
  * needs clearing); calls whose work overlaps on the GPU -- on different
  * streams, or from different host threads without ordering -- race on it.

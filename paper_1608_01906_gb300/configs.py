@@ -102,12 +102,14 @@ def rt_params(width=512, Re=3000.0, uref=0.08, dt=0.5):
     return g, nu, tau
 
 
-def c3_rayleigh_taylor(nx=512, ny=2048, steps=20000, Re=3000.0, uref=0.08):
+def c3_rayleigh_taylor(nx=512, ny=2048, steps=20000, Re=3000.0, uref=0.08, ref_width=None):
     """512x2048 structured split, walls top/bottom, periodic x, At = 0.5,
-    amplitude 0.1 W, Re 3000, gravity body force, FP32."""
+    amplitude 0.1 W, Re 3000, gravity body force, FP32.  ref_width: the
+    width g, nu and tau are derived from (default nx); a smaller mesh with
+    ref_width=512 runs the physics of the 512-wide workload."""
     xy, tri, box, tag = inputs.structured_mesh(nx, ny, periodic_y=False)
     rho_h, rho_lt = 1.0, 1.0 / 3.0
-    g, nu, tau = rt_params(nx, Re, uref)
+    g, nu, tau = rt_params(ref_width or nx, Re, uref)
     rho0, u0, p0 = inputs.rayleigh_taylor_fields(xy, nx, ny, rho_h, rho_lt, 4.0, 0.1 * nx, g)
     return Problem("c3_rayleigh_taylor_%dx%d" % (nx, ny), xy, tri, box, tag, rho0, u0, p0,
                    params(rho_h, rho_lt, 1e-4, 4.0, tau, tau, 0.5, (0.0, -g)), steps, "fp32",

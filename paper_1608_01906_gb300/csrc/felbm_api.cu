@@ -246,10 +246,11 @@ static void step_lattice(felbm_state *s, LatArgs<T> &A, bool write_mom) {
 }
 
 // The dynamic shared memory of k_lat_step is above the default limit: set
-// the function attribute once per device (bit d of done; devices from 64 on
-// set it at every call).
+// the function attribute once per device (bit d of done, set only once the
+// call succeeded; devices from 64 on set it at every call).  A refusal is
+// returned to the caller of felbm_step.
 template <typename T>
-static void lat_smem_attr() {
+static cudaError_t lat_smem_attr() {
     static std::atomic<uint64_t> done{0};
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -257,16 +258,23 @@ static void lat_smem_attr() {
         dev = -1;
     }
     const uint64_t bit = (dev >= 0 && dev < 64) ? (uint64_t(1) << dev) : 0;
-    if (bit && (done.load(std::memory_order_acquire) & bit)) return;
-    cudaFuncSetAttribute(k_lat_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lat_smem<T>());
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_lat_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lat_smem<T>());
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e;
+    }
     if (bit) done.fetch_or(bit, std::memory_order_release);
+    return cudaSuccess;
 }
 
 template <typename T>
-static void do_steps(felbm_state *s, int64_t n) {
+static int do_steps(felbm_state *s, int64_t n) {
     const felbm_mesh *m = s->mesh;
     if (m->kind == 1) {
-        lat_smem_attr<T>();
+        const cudaError_t ea = lat_smem_attr<T>();
+        if (ea != cudaSuccess) return cuda_status(ea);
         LatArgs<T> A;
         A.nx = m->sinfo.nx;
         A.ny = m->sinfo.ny;
@@ -281,6 +289,7 @@ static void do_steps(felbm_state *s, int64_t n) {
         const DevCSR<T> d = dev_csr<T>(m);
         for (int64_t k = 0; k < n; ++k) step_topo<T>(s, d, k == n - 1);
     }
+    return FELBM_OK;
 }
 
 template <typename T>
@@ -551,12 +560,12 @@ int felbm_state_init(const felbm_mesh *mesh, const felbm_params *params, const d
 int felbm_step(felbm_state *s, int64_t n_steps) {
     if (!s || n_steps < 0) return FELBM_ERR_INVALID_ARG;
     if (n_steps == 0) return FELBM_OK;
-    if (s->mesh->kind >= 2)
+    if (s->mesh->kind >= 2) {
         steps3(s, n_steps);
-    else if (s->esize == 8)
-        do_steps<double>(s, n_steps);
-    else
-        do_steps<float>(s, n_steps);
+    } else {
+        const int st = s->esize == 8 ? do_steps<double>(s, n_steps) : do_steps<float>(s, n_steps);
+        if (st != FELBM_OK) return st;
+    }
     s->steps_done += n_steps;
     s->have_moments = true;
     return cuda_status(cudaGetLastError());

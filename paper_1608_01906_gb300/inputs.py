@@ -274,6 +274,23 @@ def structured_tet_mesh(nx, ny, nz, h=1.0, periodic_z=True):
     return xyz, tet, box, tag
 
 
+def jittered_tet_mesh(nx, ny, nz, jitter=0.15, seed=1608, h=1.0):
+    """The periodic Kuhn-split lattice of :func:`structured_tet_mesh` with
+    every node moved by independent uniform offsets in ``+-jitter*h`` drawn
+    from ``numpy.random.default_rng(seed)``, coordinates wrapped into the
+    box.  Same tetrahedra (the orientation under the minimum-image rule holds
+    for ``jitter <= 0.15``); element volumes and lumped masses then differ
+    from node to node.  Returns ``(xyz, tet, box, tag)``."""
+    if not (0.0 <= jitter <= 0.15):
+        raise ValueError("jitter must lie in [0, 0.15]")
+    xyz, tet, box, tag = structured_tet_mesh(nx, ny, nz, h, True)
+    rng = np.random.default_rng(seed)
+    xyz = xyz + rng.uniform(-jitter * h, jitter * h, size=xyz.shape)
+    for c in range(3):
+        xyz[:, c] %= box[c]
+    return xyz, tet, box, tag
+
+
 def droplet_fields3(xyz, box, center, radius, rho_l, rho_v, xi, u0=(0.0, 0.0, 0.0)):
     """Spherical liquid drop of radius ``radius`` in vapour: the tanh
     profile of ``droplet_fields`` in the minimum-image distance to

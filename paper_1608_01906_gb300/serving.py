@@ -85,6 +85,26 @@ def state_bytes(side, precision="fp32"):
     return n * (36 * es + 6 * es + 4 * es + 5 * 8)
 
 
+def mesh_bytes(side):
+    """Device bytes of a structured side x side mesh before it exists: the
+    FP64 lumped mass (structured meshes hold no assembled arrays).  Once the
+    mesh is created its own count (felbm_mesh_info) replaces this."""
+    return side * side * 8
+
+
+# Batch memory outside the states and meshes: per run a share of the tile
+# list (one 16-byte record per 32 x 8 tile), its descriptor and its 768
+# bytes of tensor maps; per batch the launch counters and the autotuner's
+# buffers.
+BATCH_RUN_BYTES = 4096
+BATCH_FIXED_BYTES = 1 << 20
+
+
+def run_bytes(side, precision="fp32"):
+    """Device bytes a run adds to a batch besides its mesh."""
+    return state_bytes(side, precision) + (side * side // 256 + 1) * 16 + BATCH_RUN_BYTES
+
+
 def problem_for(req: Request):
     return configs.droplet_structured(req.side, req.radius_frac * req.side, req.ratio,
                                       configs.DROPLET_XI, 0.01,
@@ -103,6 +123,7 @@ class Server:
         self.meshes = {}   # side -> (Mesh, users)
         self.active = []   # dicts: req, state, done, admitted
         self.used = 0
+        self.fixed_held = False
         self.batch = None
         self.dirty = True
         self.results = []
@@ -115,8 +136,9 @@ class Server:
         if ent is None:
             prob = problem_for(req)
             m = felbm.Mesh(prob.xy, prob.tri, prob.box, prob.tag, stream=self.stream)
-            ent = [m, 0]
+            ent = [m, 0, int(m.info()["device_bytes"])]
             self.meshes[req.side] = ent
+            self.used += ent[2]
         ent[1] += 1
         return ent[0]
 
@@ -125,17 +147,38 @@ class Server:
         ent[1] -= 1
         if ent[1] == 0:
             ent[0].close()
+            self.used -= ent[2]
             del self.meshes[side]
 
+    def need(self, req):
+        """Device bytes admitting req would add: the run, its mesh when no
+        active run shares that side, and the batch's fixed part when the
+        batch is empty."""
+        b = run_bytes(req.side, self.precision)
+        if req.side not in self.meshes:
+            b += mesh_bytes(req.side)
+        if not self.fixed_held:
+            b += BATCH_FIXED_BYTES
+        return b
+
+    def _release_fixed(self):
+        # the batch's fixed part goes with its last run
+        if self.fixed_held and not self.active:
+            self.used -= BATCH_FIXED_BYTES
+            self.fixed_held = False
+
     def fits(self, req):
-        return self.used + state_bytes(req.side, self.precision) <= self.budget
+        return self.used + self.need(req) <= self.budget
 
     def admit(self, req, now):
         prob = problem_for(req)
+        if not self.fixed_held:
+            self.used += BATCH_FIXED_BYTES
+            self.fixed_held = True
         mesh = self._mesh(req)
         st = felbm.State(mesh, felbm.make_params(precision=self.precision, **prob.params),
                          prob.rho0, prob.u0, prob.p0)
-        self.used += state_bytes(req.side, self.precision)
+        self.used += run_bytes(req.side, self.precision)
         self.active.append({"req": req, "state": st, "done": 0, "admitted": now})
         self.dirty = True
 
@@ -146,7 +189,7 @@ class Server:
                                    req.nodes, m, status))
         slot["state"].close()
         self._release_mesh(req.side)
-        self.used -= state_bytes(req.side, self.precision)
+        self.used -= run_bytes(req.side, self.precision)
         self.dirty = True
 
     # ---- stepping -----------------------------------------------------
@@ -179,6 +222,7 @@ class Server:
             for s in diverged:
                 self._retire(s, now, "diverged")
             self.active = [s for s in self.active if all(s is not d for d in diverged)]
+            self._release_fixed()
         return n
 
     def retire_finished(self, now):
@@ -189,6 +233,7 @@ class Server:
             else:
                 keep.append(s)
         self.active = keep
+        self._release_fixed()
 
     def close(self):
         if self.batch is not None:

@@ -169,6 +169,67 @@ def test_fp64_mass_momentum_conserved_gpu():
     assert abs(t1[1]) / t0[0] <= 1e-13 and abs(t1[2]) / t0[0] <= 1e-13
 
 
+def test_fp64_totals_match_oracle_on_delaunay_mesh():
+    # FP64 mass and momentum totals sum_i m_i rho_i, sum_i m_i rho_i u_i with
+    # the lumped mass m_i = sum_{T contains i} |T|/3 (Sec. 2.2.1): on a
+    # jittered Delaunay mesh the masses differ from node to node (0.6-1.4),
+    # so unit weights or any other wrong weighting fails.  A drop carried by
+    # a uniform velocity gives non-zero momentum totals.
+    xy, tri, box, tag = inputs.jittered_delaunay_mesh(40, 36, 0.25, seed=21)
+    rho0, u0, p0 = inputs.droplet_fields(xy, box, (20, 18), 10.0, 1.0, 0.1, 4.0,
+                                         u0=(0.012, -0.007))
+    prob = configs.Problem("u", xy, tri, box, tag, rho0, u0, p0, configs.params(dt=0.4), 0,
+                           "fp64")
+    o = Oracle(prob.xy, prob.tri, prob.box, prob.tag, Params(**prob.params))
+    assert o.mass.min() < 0.8 and o.mass.max() > 1.2
+    mesh = felbm.Mesh(prob.xy, prob.tri, prob.box, prob.tag)
+    st = felbm.State(mesh, felbm.make_params(precision="fp64", **prob.params), prob.rho0,
+                     prob.u0, prob.p0)
+    o.init(prob.rho0, prob.u0, prob.p0)
+    for steps in (1, 49):
+        st.step(steps)
+        o.step(steps)
+        got = np.asarray(st.moments()["totals"])
+        want = np.asarray(o.totals())
+        assert np.all(np.abs(got - want) <= 1e-12 * np.abs(want)), (steps, got, want)
+        # the same sums from the returned fields (caller order) and the
+        # oracle's lumped mass
+        m = st.moments()
+        mr = o.mass * m["rho"]
+        direct = np.array([mr.sum(), (mr * m["u"][:, 0]).sum(), (mr * m["u"][:, 1]).sum()])
+        assert np.all(np.abs(got - direct) <= 1e-12 * np.abs(direct)), (got, direct)
+    st.close()
+    mesh.close()
+
+
+def test_fp32_walled_rayleigh_taylor_1000_steps():
+    # Rayleigh-Taylor physics of the 512 x 2048 workload (walls, gravity,
+    # At 0.5, Re 3000 at the reference width) on a 128 x 512 mesh, 1000 FP32
+    # steps against the FP64 oracle: <= 1e-5 relative L2 in u and C.  The
+    # flow is the gravity-driven start of the instability, so u is compared
+    # on the scale of the flow U = sqrt(lambda g) as well as in relative L2.
+    prob = configs.c3_rayleigh_taylor(nx=128, ny=512, steps=0, ref_width=512)
+    m, kind = run_gpu(prob, "fp32", 1000)
+    assert kind == 1
+    o = run_oracle(prob, 1000)
+    e = errors(m, o)
+    U = np.sqrt(512 * prob.meta["g"])  # sqrt(lambda g) of the 512-wide workload
+    du = np.abs(m["u"] - np.stack([o.ux, o.uy], 1)).max() / U
+    print("RT 128x512 fp32 1000 steps", e, "max|du|/U", du)
+    assert e["C"] <= 1e-5 and e["u"] <= 1e-5 and e["rho"] <= 1e-5 and du <= 1e-5, (e, du)
+
+
+def test_fp32_layered_channel_1000_steps():
+    # the walled two-phase channel of the 20,000-step test at the 1000-step
+    # horizon of the FP32 tolerance: <= 1e-5 in u and C
+    prob = _layered_channel()
+    m, _ = run_gpu(prob, "fp32", 1000)
+    o = run_oracle(prob, 1000)
+    e = errors(m, o)
+    print("channel fp32 1000 steps", e)
+    assert e["C"] <= 1e-5 and e["u"] <= 1e-5, e
+
+
 @pytest.mark.parametrize("general", [False, True])
 def test_fp32_droplet_1000_steps(general):
     prob = configs.droplet_structured(64, 16.0, 10.0, steps=1000, precision="fp32")

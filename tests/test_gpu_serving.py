@@ -19,7 +19,7 @@ def _lib():
 def test_served_runs_equal_standalone_runs():
     reqs = serving.poisson_stream(7, rate=40.0, seed=5, side=(32, 96), steps=(40, 260))
     # room for about three of the runs at a time: later arrivals queue
-    budget = 3 * serving.state_bytes(96)
+    budget = 3 * (serving.run_bytes(96) + serving.mesh_bytes(96)) + serving.BATCH_FIXED_BYTES
     results, stats = serving.serve(reqs, budget, chunk=37)
     assert stats["completed"] == len(reqs)
     assert stats["p50_s"] is not None and stats["p99_s"] >= stats["p50_s"]

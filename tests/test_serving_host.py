@@ -29,7 +29,8 @@ class FakeState:
 
 
 class FakeMesh(FakeState):
-    pass
+    def info(self):
+        return {"device_bytes": serving.mesh_bytes(64)}
 
 
 class FakeBatch:
@@ -59,7 +60,9 @@ def test_scheduler_budget_chunks_and_retirement(monkeypatch):
                                          "gravity": (0.0, 0.0)}})())
     FakeBatch.log = []
     reqs = [serving.Request(k, 0.0, 64, 10.0, 0.3, s) for k, s in enumerate([100, 250, 60, 300])]
-    budget = 2 * serving.state_bytes(64)  # two runs at a time
+    # two runs at a time: their states and batch shares, the shared mesh and
+    # the batch's fixed part
+    budget = 2 * serving.run_bytes(64) + serving.mesh_bytes(64) + serving.BATCH_FIXED_BYTES
     results, stats = serving.serve(reqs, budget, chunk=80, autotune=False)
     assert stats["completed"] == 4
     # never more than two runs in a launch, chunk never above 80 nor past a finish
@@ -112,9 +115,33 @@ def test_diverged_run_is_retired_and_the_rest_finish(monkeypatch):
                                          "gravity": (0.0, 0.0)}})())
     FakeBatch.log = []
     reqs = [serving.Request(k, 0.0, 64, 10.0, 0.3, s) for k, s in enumerate([300, 400, 200])]
-    results, stats = serving.serve(reqs, 3 * serving.state_bytes(64), chunk=40, autotune=False)
+    budget = 3 * serving.run_bytes(64) + serving.mesh_bytes(64) + serving.BATCH_FIXED_BYTES
+    results, stats = serving.serve(reqs, budget, chunk=40, autotune=False)
     by = {r.rid: r for r in results}
     assert stats["completed"] == 2 and stats["diverged"] == 1
     assert by[1].status == "diverged" and by[1].steps == 120 and by[1].moments == {}
     assert by[0].status == "ok" and by[0].steps == 300
     assert by[2].status == "ok" and by[2].steps == 200
+
+
+def test_budget_counts_meshes_and_batch_memory(monkeypatch):
+    """Admission counts each mesh once per side (while a run uses it) and the
+    batch's own memory; the count returns to zero when every run retired."""
+    monkeypatch.setattr(serving.felbm, "Mesh", FakeMesh)
+    monkeypatch.setattr(serving.felbm, "State", FakeState)
+    monkeypatch.setattr(serving, "problem_for", lambda req: type(
+        "P", (), {"xy": None, "tri": None, "box": None, "tag": None, "rho0": None, "u0": None,
+                  "p0": None, "params": {"rho_l": 1.0, "rho_v": 0.1, "sigma": 0.01, "xi": 4.0,
+                                         "tau_l": 0.1, "tau_v": 0.1, "dt": 0.5,
+                                         "gravity": (0.0, 0.0)}})())
+    one = serving.run_bytes(64) + serving.mesh_bytes(64) + serving.BATCH_FIXED_BYTES
+    srv = serving.Server(one + serving.run_bytes(64) - 1, autotune=False)
+    a, b = (serving.Request(k, 0.0, 64, 10.0, 0.3, 100) for k in range(2))
+    assert srv.need(a) == one and srv.fits(a)
+    srv.admit(a, 0.0)
+    assert srv.used == one
+    # a second run on the same side shares the mesh and the batch: one byte short
+    assert srv.need(b) == serving.run_bytes(64) and not srv.fits(b)
+    srv.active[0]["done"] = 100
+    srv.retire_finished(1.0)
+    assert srv.used == 0 and not srv.meshes
