@@ -4,12 +4,14 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
 #include "felbm_internal.h"
 #include "felbm_kernels.cuh"
 #include "felbm_lattice.cuh"
+#include "felbm_march.cuh"
 
 using namespace felbm;
 
@@ -231,51 +233,77 @@ static LatCoef<T> lat_coef(const felbm_mesh *m, double dt) {
     return c;
 }
 
+// Launch facts of the march on the current device: SM count and resident
+// blocks per SM, with the dynamic shared-memory attribute of k_lat_march set
+// (above the default limit).  Computed once per device (ordinals below 64;
+// others at every call); a refusal is returned to the caller of felbm_step.
 template <typename T>
-static void step_lattice(felbm_state *s, LatArgs<T> &A, bool write_mom) {
-    const felbm_mesh *m = s->mesh;
-    A.fin = reinterpret_cast<const T *>(s->f[s->cur]);
-    A.fout = reinterpret_cast<T *>(s->f[s->cur ^ 1]);
-    A.mom = write_mom ? reinterpret_cast<T *>(s->mom) : nullptr;
-    A.tmap = s->d_tmap ? s->d_tmap + 3 * s->cur : nullptr;
-    const dim3 grd((A.nx + kLTX - 1) / kLTX, (A.ny + kLTY - 1) / kLTY);
-    const int sl = prof_begin(s, 4);
-    k_lat_step<T><<<grd, dim3(kLTX, kLTY), lat_smem<T>(), m->stream>>>(A);
-    prof_end(s, sl);
-    s->cur ^= 1;
-}
-
-// The dynamic shared memory of k_lat_step is above the default limit: set
-// the function attribute once per device (bit d of done, set only once the
-// call succeeded; devices from 64 on set it at every call).  A refusal is
-// returned to the caller of felbm_step.
-template <typename T>
-static cudaError_t lat_smem_attr() {
-    static std::atomic<uint64_t> done{0};
+static cudaError_t march_setup(int &sms, int &bps) {
+    static std::mutex mu;
+    static int cache[64][2];
     int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess) {
-        cudaGetLastError();
-        dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev >= 0 && dev < 64 && cache[dev][0] > 0) {
+        sms = cache[dev][0];
+        bps = cache[dev][1];
+        return cudaSuccess;
     }
-    const uint64_t bit = (dev >= 0 && dev < 64) ? (uint64_t(1) << dev) : 0;
-    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
-    const cudaError_t e =
-        cudaFuncSetAttribute(k_lat_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lat_smem<T>());
+    e = cudaFuncSetAttribute(k_lat_march<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)march_smem<T>());
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_lat_march<T>, kMT, march_smem<T>());
     if (e != cudaSuccess) {
         cudaGetLastError();
         return e;
     }
-    if (bit) done.fetch_or(bit, std::memory_order_release);
+    if (bps < 1) bps = 1;
+    if (dev >= 0 && dev < 64) {
+        cache[dev][0] = sms;
+        cache[dev][1] = bps;
+    }
     return cudaSuccess;
+}
+
+// Rows per segment of the march: as many segments per strip as keep every
+// block of the grid resident at once (one wave), each a whole number of
+// 8-row iterations; at least one iteration per segment.
+static int march_seg(int nx, int ny, int sms, int bps) {
+    const int nstrips = (nx + 31) / 32;
+    const int rows8 = (ny + kMR - 1) / kMR;
+    int nsegs = std::max(1, (sms * bps) / nstrips);
+    nsegs = std::min(nsegs, rows8);
+    return ((rows8 + nsegs - 1) / nsegs) * kMR;
+}
+
+template <typename T>
+static void step_lattice(felbm_state *s, MarchArgs<T> &M, bool write_mom) {
+    const felbm_mesh *m = s->mesh;
+    LatArgs<T> &A = M.a;
+    A.fin = reinterpret_cast<const T *>(s->f[s->cur]);
+    A.fout = reinterpret_cast<T *>(s->f[s->cur ^ 1]);
+    A.mom = write_mom ? reinterpret_cast<T *>(s->mom) : nullptr;
+    A.tmap = nullptr;
+    M.tmap = s->d_tmap ? s->d_tmap + 3 * s->cur : nullptr;
+    const dim3 grd((A.nx + 31) / 32, (A.ny + M.seg - 1) / M.seg);
+    const int sl = prof_begin(s, 4);
+    k_lat_march<T><<<grd, kMT, march_smem<T>(), m->stream>>>(M);
+    prof_end(s, sl);
+    s->cur ^= 1;
 }
 
 template <typename T>
 static int do_steps(felbm_state *s, int64_t n) {
     const felbm_mesh *m = s->mesh;
     if (m->kind == 1) {
-        const cudaError_t ea = lat_smem_attr<T>();
+        int sms = 0, bps = 0;
+        const cudaError_t ea = march_setup<T>(sms, bps);
         if (ea != cudaSuccess) return cuda_status(ea);
-        LatArgs<T> A;
+        MarchArgs<T> M;
+        M.seg = march_seg(m->sinfo.nx, m->sinfo.ny, sms, bps);
+        march_consts<T>(m->sinfo, s->params.dt, M);
+        LatArgs<T> &A = M.a;
         A.nx = m->sinfo.nx;
         A.ny = m->sinfo.ny;
         A.pitch = m->sinfo.pitch;
@@ -284,7 +312,7 @@ static int do_steps(felbm_state *s, int64_t n) {
         A.P = phys_of<T>(s->params);
         A.rho = fields_of<T>(s).rho;
         A.flag = s->d_flag;
-        for (int64_t k = 0; k < n; ++k) step_lattice<T>(s, A, k == n - 1);
+        for (int64_t k = 0; k < n; ++k) step_lattice<T>(s, M, k == n - 1);
     } else {
         const DevCSR<T> d = dev_csr<T>(m);
         for (int64_t k = 0; k < n; ++k) step_topo<T>(s, d, k == n - 1);
@@ -710,7 +738,7 @@ int felbm_profile_read(felbm_state *s, double *ms, int64_t *timed, int64_t *laun
 
 const char *felbm_profile_kind_name(int k) {
     static const char *names[FELBM_PROFILE_KINDS] = {
-        "k_rho", "k_grad", "k_mu", "k_collide", "k_lattice_step", "unused5", "unused6",
+        "k_rho", "k_grad", "k_mu", "k_collide", "k_lat_march", "unused5", "unused6",
         "unused7"};
     return (k >= 0 && k < FELBM_PROFILE_KINDS) ? names[k] : nullptr;
 }

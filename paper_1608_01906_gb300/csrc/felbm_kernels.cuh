@@ -278,6 +278,23 @@ struct CollidePrep {
     T r, ux, uy, p, omw, opw, hdt, Xx, Xy, uX, uD, uK, uu, dux, duy, udu, drx, dry, kx, ky;
 };
 
+// Correctly rounded reciprocal (the same value as T(1) / x).
+__device__ __forceinline__ float recip_rn(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip_rn(double x) { return __drcp_rn(x); }
+
+// x / 3 correctly rounded, by a product with the rounded 1/3 and one
+// correction with the exact remainder x - 3 q (the FMA form of
+// division by a constant of Markstein, IBM J. Res. Dev. 34 (1990)).  It
+// equals the rounded quotient for every normal FP32 mantissa and for all
+// FP64 operands sampled (checked with exact rational arithmetic).
+template <typename T>
+__device__ __forceinline__ T div3(T x) {
+    constexpr T c = T(1) / T(3);
+    const T q = x * c;
+    const T r = fma(T(-3), q, x);
+    return fma(r, c, q);
+}
+
 // sg = sum_a g*_a, mx, my = sum_a e_a g*_a of the streamed (and bounced) g.
 template <typename T>
 __device__ __forceinline__ CollidePrep<T> collide_prep(const Phys<T> &P, T sg, T mx, T my, T r,
@@ -285,19 +302,19 @@ __device__ __forceinline__ CollidePrep<T> collide_prep(const Phys<T> &P, T sg, T
     constexpr T cs2 = T(1) / T(3);
     CollidePrep<T> c;
     c.hdt = T(0.5) * P.dt;
-    const T inv_r = T(1) / r;
+    const T inv_r = recip_rn(r);
     c.r = r;
     c.ux = (mx + c.hdt * kx + c.hdt * r * P.gx) * inv_r;
     c.uy = (my + c.hdt * ky + c.hdt * r * P.gy) * inv_r;
     // p = c_s^2 (...) as a division by 3: a rounded 1/3 would be a gain on p
     // every step (see kW3)
-    c.p = (sg + c.hdt * (c.ux * drx + c.uy * dry)) / T(3);
+    c.p = div3(sg + c.hdt * (c.ux * drx + c.uy * dry));
     T C = (r - P.rho_v) * P.inv_drho;
     C = C < T(0) ? T(0) : (C > T(1) ? T(1) : C);
     // 1/tau = C/tau_l + (1-C)/tau_v; w = (2 tau - 1)/(2 tau + 1) gives, with
     // s = 1/tau, 1 - w = 2 s/(2 + s) and 1 + w = 4/(2 + s): one reciprocal
     const T s = C * P.inv_tau_l + (T(1) - C) * P.inv_tau_v;
-    const T d = T(1) / (T(2) + s);
+    const T d = recip_rn(T(2) + s);
     c.omw = T(2) * s * d;  // 1 - w
     c.opw = T(4) * d;      // 1 + w
     c.Xx = cs2 * drx - r * dmx;  // F: c_s^2 grad rho - rho grad mu

@@ -401,18 +401,18 @@ __device__ __forceinline__ Prep3<T> prep3(const Phys3<T> &P, T sg, const T *mg, 
     Prep3<T> c;
     c.hdt = T(0.5) * P.dt;
     c.r = r;
-    const T inv_r = T(1) / r;
+    const T inv_r = recip_rn(r);
     T ud = T(0);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         c.u[k] = (mg[k] + c.hdt * K[k] + c.hdt * r * P.g[k]) * inv_r;
         ud += c.u[k] * dr[k];
     }
-    c.p = (sg + c.hdt * ud) / T(3);  // a division: a rounded 1/3 is a gain on p (see kW3)
+    c.p = div3(sg + c.hdt * ud);  // correctly rounded: a rounded 1/3 is a gain on p (see kW3)
     T C = (r - P.rho_v) * P.inv_drho;
     C = C < T(0) ? T(0) : (C > T(1) ? T(1) : C);
     const T s = C * P.inv_tau_l + (T(1) - C) * P.inv_tau_v;  // 1/tau
-    const T d = T(1) / (T(2) + s);
+    const T d = recip_rn(T(2) + s);
     c.omw = T(2) * s * d;  // 1 - w
     c.opw = T(4) * d;      // 1 + w
     c.uX = c.uD = c.uK = c.uu = c.udu = T(0);

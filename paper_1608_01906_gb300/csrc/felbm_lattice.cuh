@@ -1,27 +1,15 @@
-// Structured-lattice step: one launch per time step, one 32 x 8 tile of
-// nodes per block (k_lat_step).
+// Building blocks of the structured-lattice step (felbm_march.cuh): the
+// coefficient tables and arguments of a lattice, halo windows filled with
+// cp.async or loaded by TMA (cp.async.bulk.tensor with mbarrier waits that
+// are bounded), the Taylor-Galerkin streaming of a pair of opposite
+// populations from a shared-memory window (Sec. 2.2.1), bounce-back at wall
+// rows (Sec. 3.3) and the collision of a pair (Sec. 2.2).
 //
-//   1. the 4 h pair tiles (halo depth 4) and the h rest tile are staged in
-//      shared memory; the h populations are streamed (Taylor-Galerkin,
-//      Sec. 2.2.1) and bounced back at walls on the tile's depth-3 halo, and
-//      rho = sum_a h_a there; the tile's own streamed h pairs are kept;
-//   2. grad rho (depth 2), lap rho and mu (depth 1), then grad mu and the
-//      stress force at the tile's nodes (Sec. 2.3 recovery, Sec. 2.1 mu,
-//      stress form);
-//   3. the g pairs are streamed from depth-1 tiles, the moments formed and
-//      all populations collided (Sec. 2.2); one write of the 18 populations.
-//
-// The density stage recomputes the streaming of h on the halo instead of a
-// separate density launch: neighbouring tiles share no data within a step.
 // Opposite directions (a, abar) are stored interleaved (pop_index): the
 // stencil of a pair reads one 8-byte (FP32) word per neighbour and runs in
 // packed two-wide arithmetic (FFMA2 on sm_103a), each lane with its own
 // coefficient.  Population rows are stored with a pitch of nx rounded up to
-// a multiple of 4 slots, so every row starts 16-byte aligned.  Halo windows
-// that need no periodic wrap arrive as TMA boxes, the others by cp.async
-// (16-byte chunks unless a chunk would straddle the wrap of a row whose
-// length is not a multiple of 4); all are requested when the block starts,
-// and the g tiles arrive while rho and the scalar chain are computed.
+// a multiple of 4 slots, so every row starts 16-byte aligned.
 //
 // Coefficient tables: for each row kind (interior, bottom wall row, top wall
 // row), offset o and pair q, the streaming coefficients of the pair's two
@@ -36,7 +24,7 @@
 
 namespace felbm {
 
-constexpr int kLTX = 32, kLTY = 8;  // tile of nodes per block
+constexpr int kLTX = 32, kLTY = 8;  // strip width and rows per iteration of the march
 
 template <int V>
 struct IntC {
@@ -231,20 +219,6 @@ struct PairTile {
     static constexpr int N = W * H;
 };
 
-// Request the depth-D halo tiles of the 4 pairs of h (G = 0) or g (G = 1).
-// VEC: 16-byte chunks (needs a window without x wrap, or nx % 4 == 0, so
-// that no chunk straddles the wrap).
-template <typename T, int G, int D, bool VEC>
-__device__ __forceinline__ void issue_pair_tiles(const LatArgs<T> &A, int tid, int x0, int y0,
-                                                 V2<T> *tiles, size_t np) {
-    using E = V2<T>;
-    using PT = PairTile<T, D>;
-    const E *src = reinterpret_cast<const E *>(A.fin + (G ? 10 : 1) * np);  // pair 0; pair q at + q np
-    const FillPlan f =
-        fill_plan<E, PT::W, PT::H, VEC>(tid, kLTX * kLTY, x0 - PT::XH, y0 - D, A.nx, A.pitch, A.ny, A.walls);
-    fill_issue<E, VEC, 4>(f, src, np, tiles, PT::N);
-}
-
 // Streamed values of pair q of the node whose element in the halo tile buf
 // (rows of W elements) is c, at row kind k:
 // psi* = psi - dt sum_o s_o (psi(node + o) - psi(node)), both directions in
@@ -307,409 +281,17 @@ __device__ __forceinline__ V2<T> bounce_pair(int k, int q, V2<T> v) {
     return k == 1 ? vset(v.y, v.y) : vset(v.x, v.x);
 }
 
-// ---- one step of a tile ---------------------------------------------------
+// ---- windows of the march ------------------------------------------
 
-constexpr int kHD = 4;                            // depth of the h pair tiles
-constexpr int kH0W = kLTX + 8, kH0H = kLTY + 6;   // h rest tile: from (x0 - 4, y0 - 3)
-constexpr int kQW = kLTX + 6, kQH = kLTY + 6;     // rho region: halo 3
-constexpr int kRW = kLTX + 8, kRH = kLTY + 6;     // rho: rows from x0 - 4 (column 0, 39 unused)
-constexpr int kGW = kLTX + 4, kGH = kLTY + 4;     // grad rho: halo 2
-constexpr int kMW = kLTX + 2, kMH = kLTY + 2;     // mu: halo 1
-constexpr int kNT = kLTX * kLTY;
-
-// Shared memory of one tile: the scalar chain (static) and the population
-// tiles (dynamic, lat_smem bytes).  The streamed g pairs stay in registers.
-template <typename T>
-struct __align__(16) StepSmem {
-    uint64_t bar[2];  // TMA completion: h tiles, g tiles
-    int nt[4];        // the block's next tile as claimed by thread 0: index, bx, by, flags
-    T s_rho[kRH][kRW];
-    T s_gx[kGH][kGW], s_gy[kGH][kGW];
-    T s_mu[kMH][kMW];
-};
+constexpr int kHD = 4;  // depth of the h windows in x (columns x0-4 .. x0+35)
 
 constexpr size_t align128(size_t b) { return (b + 127) / 128 * 128; }
 
-// Regions of the dynamic shared memory, each 128-byte aligned (TMA
-// destinations).  The byte sizes of the h tiles (pairs + rest) and of the g
-// tiles are what one TMA load group delivers.
-template <typename T>
-struct LatSmem {
-    using PH = PairTile<T, kHD>;
-    using PG = PairTile<T, 1>;
-    static constexpr unsigned hT_bytes = 4 * PH::N * sizeof(V2<T>);
-    static constexpr unsigned h0_bytes = kH0W * kH0H * sizeof(T);
-    static constexpr unsigned gT_bytes = 4 * PG::N * sizeof(V2<T>);
-    static constexpr size_t hT = 0;                             // 4 h pair tiles
-    static constexpr size_t h0 = align128(hT + hT_bytes);      // h rest tile
-    static constexpr size_t gT = align128(h0 + h0_bytes);      // 4 g pair tiles
-    static constexpr size_t psi = align128(gT + gT_bytes);     // streamed h pairs
-    static constexpr size_t bytes = psi + 4 * (size_t)kNT * sizeof(V2<T>);
-};
-
-template <typename T>
-constexpr size_t lat_smem() {
-    return LatSmem<T>::bytes;
-}
-
-// Whether the halo windows of a tile at x0 may be filled in 16-byte chunks:
-// rows are 16-byte aligned (pitch), so unless a window wraps around a row
-// whose length is not a multiple of 4.
+// Whether the halo windows of a strip at x0 may be filled in 16-byte
+// chunks: rows are 16-byte aligned (pitch), so unless a window wraps around
+// a row whose length is not a multiple of 4.
 __device__ __forceinline__ bool vec_fills(int x0, int nx) {
     return (nx % 4) == 0 || (x0 >= kHD && x0 + kLTX + kHD <= nx);
-}
-
-// Whether tile (x0, y0) is whole (no node outside the mesh), its rho region
-// and h tiles hold no wall row nor a row outside a walled domain, and rows
-// are 16-byte aligned: such tiles run with the row kind fixed at compile
-// time and vector fills only.
-__device__ __forceinline__ bool tile_interior(int x0, int y0, int nx, int ny, int walls) {
-    const bool yin = walls ? (y0 >= kHD && y0 + kLTY + kHD <= ny) : (y0 + kLTY <= ny);
-    return yin && x0 + kLTX <= nx && vec_fills(x0, nx);
-}
-
-// Whether the halo windows of tile (x0, y0) lie inside the mesh without a
-// periodic wrap: a TMA box then covers each of them.
-__device__ __forceinline__ bool tile_unwrapped(int x0, int y0, int nx, int ny) {
-    return x0 >= kHD && x0 + kLTX + kHD <= nx && y0 >= kHD && y0 + kLTY + kHD <= ny;
-}
-
-// Collision of one node: the g pairs are streamed here from their depth-1
-// tiles, the h pairs were streamed by the density stage.
-template <typename T>
-__device__ __forceinline__ void lat_node(const LatArgs<T> &A, const LatCoef<T> &C, int k, int lx, int ly,
-                                         int tid, int32_t i,
-                                         size_t ip, size_t n, size_t np, T h0, T g0, T r0, T drx, T dry,
-                                         T dmx, T dmy, T kx, T ky, const V2<T> *gT,
-                                         const V2<T> (*s_psi)[kNT]) {
-    using PG = PairTile<T, 1>;
-    const Phys<T> &P = A.P;
-    const int c = (ly + 1) * PG::W + lx + PG::XH;
-    V2<T> gq[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-        gq[q] = bounce_pair<T>(k, q, stream_pair<T, PG::W>(C, k, q, gT + q * PG::N, c, P.dt));
-    T sg, mx, my;
-    // g_1 = q0.x, g_3 = q0.y, g_2 = q1.x, g_4 = q1.y, g_5 = q2.x, g_7 = q2.y, g_6 = q3.x, g_8 = q3.y
-    g_moments<T>(g0, gq[0].x, gq[1].x, gq[0].y, gq[1].y, gq[2].x, gq[3].x, gq[2].y, gq[3].y, sg, mx, my);
-    const CollidePrep<T> cp = collide_prep<T>(P, sg, mx, my, r0, drx, dry, dmx, dmy, kx, ky);
-    const T r = cp.r, ux = cp.ux, uy = cp.uy, p = cp.p;
-    // pairs, then the rest population, which also takes the sum of the h
-    // increments (zero in exact arithmetic): the collision then keeps the
-    // node's mass to one rounding instead of accumulating the rounding of the
-    // nine source terms every step
-    T dsum = T(0);
-    V2<T> *hout = reinterpret_cast<V2<T> *>(A.fout + np);
-    V2<T> *gout = reinterpret_cast<V2<T> *>(A.fout + 10 * np);
-    auto pair_update = [&](auto qc) {
-        constexpr int q = decltype(qc)::value;
-        const V2<T> hs = s_psi[q][tid];
-        V2<T> ho, go;
-        collide_pair<T, q>(cp, hs, gq[q], ho, go);
-        dsum += (ho.x - hs.x) + (ho.y - hs.y);
-        hout[(size_t)q * np + ip] = ho;
-        gout[(size_t)q * np + ip] = go;
-    };
-    pair_update(IntC<0>{});
-    pair_update(IntC<1>{});
-    pair_update(IntC<2>{});
-    pair_update(IntC<3>{});
-    {
-        T ho, go;
-        collide_pop_rt<T>(cp, 0, h0, g0, ho, go);
-        dsum += ho - h0;
-        A.fout[ip] = ho - dsum;
-        A.fout[9 * np + ip] = go;
-    }
-    if (!(finite_val(r) && finite_val(ux) && finite_val(uy) && finite_val(p))) atomicOr(A.flag, 1);
-    if (A.mom) {
-        A.mom[i] = r;
-        A.mom[n + i] = ux;
-        A.mom[2 * n + i] = uy;
-        A.mom[3 * n + i] = p;
-    }
-}
-
-// TMA state of a block walking its tiles (same value in every thread).
-struct TilePipe {
-    unsigned ph[2] = {0u, 0u};  // parity of the next phase of bar[0] (h group), bar[1] (g group)
-    bool h_issued = false;      // the current tile's h group was requested during the previous tile
-};
-
-// The block's next tile (known to thread 0 only): its h group is requested
-// as soon as the current tile has formed rho (tma: it loads by TMA, from
-// the same mesh).  Thread 0 publishes it in S.nt (flags: bit 0 valid, bit 1
-// h group requested) for the whole block after the tile.
-struct NextTile {
-    int t, bx, by;
-    bool valid, tma;
-};
-
-// Request the h group (4 h pair tiles + the rest tile) of tile (x0, y0).
-template <typename T>
-__device__ __forceinline__ void issue_h_group(const LatArgs<T> &A, int x0, int y0, StepSmem<T> &S,
-                                              unsigned char *dsm) {
-    using L = LatSmem<T>;
-    using PH = PairTile<T, kHD>;
-    constexpr int WPN = (int)sizeof(V2<T>) / 4, SPN = (int)sizeof(T) / 4;  // 4-byte words per element
-    fence_proxy_async();
-    mbar_expect_tx(&S.bar[0], L::hT_bytes + L::h0_bytes);
-    tma_load_3d(dsm + L::hT, A.tmap + 0, (x0 - PH::XH) * WPN, y0 - kHD, 0, &S.bar[0]);
-    tma_load_2d(dsm + L::h0, A.tmap + 1, (x0 - 4) * SPN, y0 - 3, &S.bar[0]);
-}
-
-// Request the g group (4 g pair tiles) of tile (x0, y0).
-template <typename T>
-__device__ __forceinline__ void issue_g_group(const LatArgs<T> &A, int x0, int y0, StepSmem<T> &S,
-                                              unsigned char *dsm) {
-    using L = LatSmem<T>;
-    using PG = PairTile<T, 1>;
-    constexpr int WPN = (int)sizeof(V2<T>) / 4;
-    fence_proxy_async();
-    mbar_expect_tx(&S.bar[1], L::gT_bytes);
-    tma_load_3d(dsm + L::gT, A.tmap + 2, (x0 - PG::XH) * WPN, y0 - 1, 0, &S.bar[1]);
-}
-
-// A bounded wait for a TMA load ran out: record it, give the loads still in
-// flight one more bounded wait each, and stop (all threads alike).
-template <typename T>
-__device__ __noinline__ bool tma_gave_up(const LatArgs<T> &A, StepSmem<T> &S, const TilePipe &pp) {
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-        atomicOr(A.flag, 4);
-        mbar_wait(&S.bar[0], pp.ph[0]);
-        mbar_wait(&S.bar[1], pp.ph[1]);
-    }
-    __syncthreads();
-    return false;
-}
-
-// One time step of tile (bx, by).  TMA: the halo windows come as TMA boxes
-// (tile_unwrapped, interior tiles) completing on S.bar, else as cp.async
-// fills.  C: the mesh's coefficient tables (kernel parameters where they
-// can be, so that interior tiles read them as constant operands).  Returns
-// false (all threads alike) when a bounded wait for a TMA load gave up; the
-// flag then carries bit 2.
-template <typename T, bool INTERIOR, bool TMA>
-__device__ __forceinline__ bool lat_tile_impl(const LatArgs<T> &A, const LatCoef<T> &C, int bx, int by,
-                                              StepSmem<T> &S, unsigned char *dsm, TilePipe &pp,
-                                              const NextTile &next) {
-    using L = LatSmem<T>;
-    using PH = PairTile<T, kHD>;
-    auto &s_rho = S.s_rho;
-    auto &s_gx = S.s_gx;
-    auto &s_gy = S.s_gy;
-    auto &s_mu = S.s_mu;
-    V2<T> *hT = reinterpret_cast<V2<T> *>(dsm + L::hT);
-    T(*s_h0)[kH0W] = reinterpret_cast<T(*)[kH0W]>(dsm + L::h0);
-    V2<T> *gT = reinterpret_cast<V2<T> *>(dsm + L::gT);
-    V2<T>(*s_psi)[kNT] = reinterpret_cast<V2<T>(*)[kNT]>(dsm + L::psi);
-    const int nx = A.nx, ny = A.ny, walls = A.walls;
-    const int x0 = bx * kLTX, y0 = by * kLTY;
-    const int tid = threadIdx.y * kLTX + threadIdx.x;
-    const size_t n = (size_t)nx * ny, np = pad4((size_t)A.pitch * ny);
-    const T dt = A.P.dt;
-    // 0. request the h pair tiles (depth 4) and the h rest tile (depth 3) as
-    //    group 1, the g pair tiles (depth 1) as group 2; the g tiles arrive
-    //    while rho and the scalar chain are computed
-    if (TMA) {
-        if (tid == 0) {
-            if (!pp.h_issued) issue_h_group<T>(A, x0, y0, S, dsm);
-            issue_g_group<T>(A, x0, y0, S, dsm);
-        }
-    } else if (INTERIOR || vec_fills(x0, nx)) {
-        issue_pair_tiles<T, 0, kHD, true>(A, tid, x0, y0, hT, np);
-        fill_issue<T, true, 1>(fill_plan<T, kH0W, kH0H, true>(tid, kNT, x0 - 4, y0 - 3, nx, A.pitch, ny, walls),
-                               A.fin, 0, &s_h0[0][0], 0);
-        cp_async_commit();
-        issue_pair_tiles<T, 1, 1, true>(A, tid, x0, y0, gT, np);
-    } else {
-        issue_pair_tiles<T, 0, kHD, false>(A, tid, x0, y0, hT, np);
-        fill_issue<T, false, 1>(fill_plan<T, kH0W, kH0H, false>(tid, kNT, x0 - 4, y0 - 3, nx, A.pitch, ny, walls),
-                                A.fin, 0, &s_h0[0][0], 0);
-        cp_async_commit();
-        issue_pair_tiles<T, 1, 1, false>(A, tid, x0, y0, gT, np);
-    }
-    if (!TMA) cp_async_commit();
-    // the node's g rest population (not moved by streaming): requested now so
-    // that its latency overlaps the density stage and the scalar chain
-    const int x = x0 + (int)threadIdx.x, y = y0 + (int)threadIdx.y;
-    const bool valid = INTERIOR || (x < nx && y < ny);
-    const int32_t i = valid ? x + nx * y : 0;                        // node (moments)
-    const size_t ip = valid ? (size_t)x + (size_t)A.pitch * y : 0;  // population slot
-    const T g0 = valid ? __ldg(A.fin + 9 * np + ip) : T(0);
-    // rows of the rho region (y0 - 3 .. y0 + 10) all of kind 0 and inside
-    const bool rows_in = INTERIOR || !walls || (y0 >= kHD && y0 + kLTY + kHD <= ny);
-    if (TMA) {
-        if (!block_mbar_wait(&S.bar[0], pp.ph[0])) return tma_gave_up(A, S, pp);
-        pp.ph[0] ^= 1u;
-    } else {
-        cp_async_wait_group<1>();
-        __syncthreads();
-    }
-    // the node's own rest population, read before the h tiles are reused
-    const T h0 = s_h0[threadIdx.y + 3][threadIdx.x + 4];
-    // 1. rho = sum of the streamed, bounced-back h on the depth-3 region
-    //    (s_rho[r][c] = global (x0 - 4 + c, y0 - 3 + r); zero outside a walled
-    //    domain, where only zero coefficients meet it); the tile's own
-    //    streamed h pairs are kept for the collision
-    for (int q = tid; q < kQW * kQH; q += kNT) {
-        const int ry = q / kQW, rx = q - ry * kQW;
-        const int gy = y0 + ry - 3;
-        T r = T(0);
-        if (rows_in || (gy >= 0 && gy < ny)) {
-            const int k = rows_in ? 0 : lat_kind(walls, gy, ny);
-            const int c = (ry + 1) * PH::W + rx + (PH::XH - 3);
-            const bool own = (unsigned)(rx - 3) < (unsigned)kLTX && (unsigned)(ry - 3) < (unsigned)kLTY;
-            const int o = (ry - 3) * kLTX + (rx - 3);
-            r = s_h0[ry][rx + 1];
-#pragma unroll
-            for (int p = 0; p < 4; ++p) {
-                const V2<T> v = bounce_pair<T>(k, p, stream_pair<T, PH::W>(C, k, p, hT + p * PH::N, c, dt));
-                r += v.x + v.y;
-                if (own) s_psi[p][o] = v;
-            }
-        }
-        s_rho[ry][rx + 1] = r;
-    }
-    __syncthreads();
-    // the h pair tiles and the rest tile are dead (nothing below reads them):
-    // request the next tile's h group now, so that it arrives while this
-    // tile finishes
-    if (tid == 0) {
-        if (next.tma) issue_h_group<T>(A, next.bx * kLTX, next.by * kLTY, S, dsm);
-        S.nt[0] = next.t;
-        S.nt[1] = next.bx;
-        S.nt[2] = next.by;
-        S.nt[3] = (next.valid ? 1 : 0) | (next.tma ? 2 : 0);
-    }
-    const auto &rc = C.r;  // recovery coefficients
-    // 2. recovered grad rho on the depth-2 region
-    for (int q = tid; q < kGW * kGH; q += kNT) {
-        const int ly = q / kGW, lx = q - ly * kGW;
-        const int gy = y0 + ly - 2;
-        const int k = (!INTERIOR && walls && (gy == 0 || gy == ny - 1)) ? (gy == 0 ? 1 : 2) : 0;
-        const T c0 = s_rho[ly + 1][lx + 2];
-        T sx = T(0), sy = T(0);
-#pragma unroll
-        for (int o = 0; o < 6; ++o) {
-            const T d = s_rho[ly + 1 + lat_dy(o)][lx + 2 + lat_dx(o)] - c0;
-            sx += rc[k][o][0] * d;
-            sy += rc[k][o][1] * d;
-        }
-        s_gx[ly][lx] = sx;
-        s_gy[ly][lx] = sy;
-    }
-    __syncthreads();
-    // 3. lap rho and mu on the depth-1 region
-    const Phys<T> &P = A.P;
-    for (int q = tid; q < kMW * kMH; q += kNT) {
-        const int ly = q / kMW, lx = q - ly * kMW;
-        const int gy = y0 + ly - 1;
-        const int k = (!INTERIOR && walls && (gy == 0 || gy == ny - 1)) ? (gy == 0 ? 1 : 2) : 0;
-        const T gxc = s_gx[ly + 1][lx + 1], gyc = s_gy[ly + 1][lx + 1];
-        T lap = T(0);
-#pragma unroll
-        for (int o = 0; o < 6; ++o) {
-            lap += rc[k][o][0] * (s_gx[ly + 1 + lat_dy(o)][lx + 1 + lat_dx(o)] - gxc) +
-                   rc[k][o][1] * (s_gy[ly + 1 + lat_dy(o)][lx + 1 + lat_dx(o)] - gyc);
-        }
-        s_mu[ly][lx] = mu_bulk<T>(P, s_rho[ly + 2][lx + 3]) - P.kappa * lap;
-    }
-    __syncthreads();
-    // 4. per node: grad mu, stress force, then the collision.  Threads of a
-    //    ragged tile outside the mesh take part in every barrier.
-    const int lx = threadIdx.x, ly = threadIdx.y;
-    const int k = (rows_in || !valid) ? 0 : lat_kind(walls, y, ny);
-    T dmx, dmy, kx, ky;
-    {
-        T smx = T(0), smy = T(0), skx = T(0), sky = T(0);
-        const T mc = s_mu[ly + 1][lx + 1];
-        const T gxc = s_gx[ly + 2][lx + 2], gyc = s_gy[ly + 2][lx + 2];
-#pragma unroll
-        for (int o = 0; o < 6; ++o) {
-            const T ax = rc[k][o][0], ay = rc[k][o][1];
-            const T dm = s_mu[ly + 1 + lat_dy(o)][lx + 1 + lat_dx(o)] - mc;
-            smx += ax * dm;
-            smy += ay * dm;
-            const T gxj = s_gx[ly + 2 + lat_dy(o)][lx + 2 + lat_dx(o)];
-            const T gyj = s_gy[ly + 2 + lat_dy(o)][lx + 2 + lat_dx(o)];
-            const T ddx = gxj - gxc, ddy = gyj - gyc;  // product form, see k_mu
-            const T dxx = ddx * (gxj + gxc), dxy = gxj * ddy + gyc * ddx, dyy = ddy * (gyj + gyc);
-            skx += ax * dyy - ay * dxy;
-            sky += ay * dxx - ax * dxy;
-        }
-        dmx = smx;
-        dmy = smy;
-        kx = P.kappa * skx;
-        ky = P.kappa * sky;
-    }
-    const T r0 = s_rho[ly + 3][lx + 4];
-    const T drx = s_gx[ly + 2][lx + 2], dry = s_gy[ly + 2][lx + 2];
-    if (TMA) {
-        if (!block_mbar_wait(&S.bar[1], pp.ph[1])) return tma_gave_up(A, S, pp);
-        pp.ph[1] ^= 1u;
-    } else {
-        cp_async_wait_group<0>();
-        __syncthreads();
-    }
-    if (valid)
-        lat_node<T>(A, C, k, lx, ly, tid, i, ip, n, np, h0, g0, r0, drx, dry, dmx, dmy, kx, ky, gT, s_psi);
-    __syncthreads();  // the caller may reuse shared memory for the next tile
-    return true;
-}
-
-// Barriers of the TMA loads; once per block before its first tile.
-template <typename T>
-__device__ __forceinline__ void lat_block_init(StepSmem<T> &S) {
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-        mbar_init(&S.bar[0], 1);
-        mbar_init(&S.bar[1], 1);
-        mbar_fence_init();
-    }
-    __syncthreads();
-}
-
-// Whether tile (bx, by) loads its halo windows by TMA.
-template <typename T>
-__device__ __forceinline__ bool tile_tma(const LatArgs<T> &A, int bx, int by, const unsigned char *dsm) {
-    const int x0 = bx * kLTX, y0 = by * kLTY;
-    return A.tmap && tile_interior(x0, y0, A.nx, A.ny, A.walls) && tile_unwrapped(x0, y0, A.nx, A.ny) &&
-           (smem_u32(dsm) & 127u) == 0;
-}
-
-// One tile of a block's walk (pp carries the TMA barrier phases and whether
-// this tile's h group was already requested; next is the block's next tile).
-// False when a bounded wait gave up.
-template <typename T>
-__device__ __forceinline__ bool lat_tile(const LatArgs<T> &A, const LatCoef<T> &C, int bx, int by, StepSmem<T> &S,
-                                         unsigned char *dsm, TilePipe &pp, const NextTile &next) {
-    if (tile_tma(A, bx, by, dsm)) return lat_tile_impl<T, true, true>(A, C, bx, by, S, dsm, pp, next);
-    if (tile_interior(bx * kLTX, by * kLTY, A.nx, A.ny, A.walls))
-        return lat_tile_impl<T, true, false>(A, C, bx, by, S, dsm, pp, next);
-    return lat_tile_impl<T, false, false>(A, C, bx, by, S, dsm, pp, next);
-}
-
-// After a tile: the published next tile (false: none), and whether its h
-// group was requested.
-template <typename T>
-__device__ __forceinline__ bool take_next(const StepSmem<T> &S, TilePipe &pp) {
-    const int f = S.nt[3];
-    pp.h_issued = (f & 2) != 0;
-    return (f & 1) != 0;
-}
-
-// One tile per block (grid ntx x nty).  Halo windows of interior tiles come
-// by TMA; walking several tiles per block with the next tile's h group
-// requested early measured slower for a single mesh (more instructions per
-// node, no better issue rate), so that walk is left to the batched kernel.
-template <typename T>
-__global__ void __launch_bounds__(kNT, (sizeof(T) == 4 ? 1024 : 512) / kNT) k_lat_step(LatArgs<T> A) {
-    __shared__ StepSmem<T> S;
-    extern __shared__ __align__(128) unsigned char lat_dsm[];
-    lat_block_init<T>(S);
-    TilePipe pp;
-    const NextTile none{0, 0, 0, false, false};
-    lat_tile<T>(A, A.c, blockIdx.x, blockIdx.y, S, lat_dsm, pp, none);
 }
 
 }  // namespace felbm
