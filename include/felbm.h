@@ -169,7 +169,7 @@ void felbm_mesh_destroy(felbm_mesh *mesh);
  *   p0    host, n_nodes doubles or NULL for zero pressure.
  * Device memory: 2 x 18 n_nodes values of the chosen precision plus scratch
  * (2 x 38 n_nodes on tetrahedral meshes)
- * (structured meshes: also 768 bytes of TMA tensor maps; rows are padded to
+ * (structured meshes: also 1024 bytes of TMA tensor maps; rows are padded to
  * a multiple of 4 slots, so every width qualifies).
  * Errors: INVALID_ARG, OOM, CUDA. */
 int felbm_state_init(const felbm_mesh *mesh, const felbm_params *params, const double *rho0,

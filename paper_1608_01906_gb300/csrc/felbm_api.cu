@@ -137,6 +137,7 @@ static DevLattice<T> dev_lattice(const felbm_mesh *m) {
     d.ny = m->sinfo.ny;
     d.walls = m->sinfo.walls ? 1 : 0;
     d.pitch = m->sinfo.pitch;
+    d.gy = m->sinfo.gy;
     for (int k = 0; k < 3; ++k)
         for (int o = 0; o < 6; ++o) {
             d.c[k][o][0] = (T)m->sinfo.a[k][o][0];
@@ -285,7 +286,7 @@ static void step_lattice(felbm_state *s, MarchArgs<T> &M, bool write_mom) {
     A.fout = reinterpret_cast<T *>(s->f[s->cur ^ 1]);
     A.mom = write_mom ? reinterpret_cast<T *>(s->mom) : nullptr;
     A.tmap = nullptr;
-    M.tmap = s->d_tmap ? s->d_tmap + 3 * s->cur : nullptr;
+    M.tmap = s->d_tmap ? s->d_tmap + 4 * s->cur : nullptr;
     const dim3 grd((A.nx + 31) / 32, (A.ny + M.seg - 1) / M.seg);
     const int sl = prof_begin(s, 4);
     k_lat_march<T><<<grd, kMT, march_smem<T>(), m->stream>>>(M);
@@ -307,6 +308,8 @@ static int do_steps(felbm_state *s, int64_t n) {
         A.nx = m->sinfo.nx;
         A.ny = m->sinfo.ny;
         A.pitch = m->sinfo.pitch;
+        A.gy = m->sinfo.gy;
+        A.rows = m->sinfo.rows;
         A.walls = m->sinfo.walls ? 1 : 0;
         A.c = lat_coef<T>(m, s->params.dt);
         A.P = phys_of<T>(s->params);
@@ -320,12 +323,46 @@ static int do_steps(felbm_state *s, int64_t n) {
     return FELBM_OK;
 }
 
+// Copy each node's populations into its ghost slots (structured meshes:
+// the copies a window reads past a periodic edge).  After initialisation or
+// an import; the step keeps them current itself.
+template <typename T>
+__global__ void k_fill_ghosts(T *f, int nx, int ny, int pitch, int gy, int rows, size_t np) {
+    const size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= (size_t)pitch * rows) return;
+    const int x = (int)(s % pitch) - kGX, y = (int)(s / pitch) - gy;
+    if (x < -kGX || x >= nx + kGX || y < -gy || y >= ny + gy) return;  // padding
+    if (x >= 0 && x < nx && y >= 0 && y < ny) return;                 // a node's own slot
+    const int xs = (x + nx) % nx, ys = (y + ny) % ny;
+    const size_t src = (size_t)(xs + kGX) + (size_t)pitch * (ys + gy);
+    f[s] = f[src];
+    f[9 * np + s] = f[9 * np + src];
+    V2<T> *ph = reinterpret_cast<V2<T> *>(f + np), *pg = reinterpret_cast<V2<T> *>(f + 10 * np);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        ph[q * np + s] = ph[q * np + src];
+        pg[q * np + s] = pg[q * np + src];
+    }
+}
+
+template <typename T>
+static void fill_ghosts(felbm_state *s) {
+    const felbm_mesh *m = s->mesh;
+    if (m->kind != 1) return;
+    const StructuredInfo &si = m->sinfo;
+    const size_t slots = (size_t)si.pitch * si.rows;
+    k_fill_ghosts<T><<<nblocks((int64_t)slots, 256), 256, 0, m->stream>>>(
+        reinterpret_cast<T *>(s->f[s->cur]), si.nx, si.ny, si.pitch, si.gy, si.rows, pad4(slots));
+}
+
 template <typename T>
 static void init_any(felbm_state *s) {
-    if (s->mesh->kind == 1)
+    if (s->mesh->kind == 1) {
         init_topo<T>(s, dev_lattice<T>(s->mesh));
-    else
+        fill_ghosts<T>(s);
+    } else {
         init_topo<T>(s, dev_csr<T>(s->mesh));
+    }
 }
 
 template <typename T>
@@ -680,6 +717,13 @@ int felbm_state_import(felbm_state *s, const double *hbar, const double *gbar) {
         }
     cudaError_t e = cudaMemcpyAsync(s->f[s->cur], buf.data(), buf.size(), cudaMemcpyHostToDevice,
                                     s->mesh->stream);
+    if (e == cudaSuccess) {
+        if (es == 8)
+            fill_ghosts<double>(s);
+        else
+            fill_ghosts<float>(s);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(s->d_flag, 0, sizeof(int), s->mesh->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->mesh->stream);
     if (e != cudaSuccess) return cuda_status(e);

@@ -34,7 +34,7 @@ struct BatchMesh {
     MarchArgs<T> m;  // fin / fout / mom / tmap / seg are set per launch
     T *f[2];
     T *mom;
-    const TMap *tmap;  // the state's 2 x 3 tensor maps, or nullptr
+    const TMap *tmap;  // the state's 2 x 4 tensor maps, or nullptr
     int32_t c0;
 };
 
@@ -55,8 +55,8 @@ struct BatchArgs {
 // One block per work item.  SC: the wall rows read the shared tables B.c
 // (kernel parameters), else each mesh's own from its descriptor.
 template <typename T, bool SC>
-__global__ void __launch_bounds__(kMT, sizeof(T) == 4 ? 3 : 2) k_batch_march(const __grid_constant__ BatchArgs<T> B) {
-    __shared__ __align__(8) uint64_t bars[2];
+__global__ void __launch_bounds__(kMT, sizeof(T) == 4 ? 2 : 1) k_batch_march(const __grid_constant__ BatchArgs<T> B) {
+    __shared__ MarchBars bars;
     __shared__ __align__(16) MarchArgs<T> sM;
     extern __shared__ __align__(128) unsigned char bdsm[];
     const TileRef r = B.tiles[blockIdx.x];
@@ -73,27 +73,19 @@ __global__ void __launch_bounds__(kMT, sizeof(T) == 4 ? 3 : 2) k_batch_march(con
             sM.a.fout = bm.f[c ^ 1];
             sM.a.mom = B.write_mom ? bm.mom : nullptr;
             sM.a.tmap = nullptr;
-            sM.tmap = bm.tmap ? bm.tmap + 3 * c : nullptr;
+            sM.tmap = bm.tmap ? bm.tmap + 4 * c : nullptr;
             sM.seg = B.seg;
-            if (threadIdx.x == 0) {
-                mbar_init(&bars[0], 1);
-                mbar_init(&bars[1], 1);
-                mbar_fence_init();
-            }
+            march_bars_init(bars);
         }
         __syncthreads();
     }
     const int x0 = r.bx * 32;
     const int ya = r.by * B.seg;
     const int yend = min(ya + B.seg, sM.a.ny);
-    const int niter = (yend - ya + kMR - 1) / kMR;
-    const LatCoef<T> &C = SC ? B.c : sM.a.c;
-    const bool tma = sM.tmap && march_tma_rows(x0, ya, ya + (niter - 1) * kMR, sM.a.nx, sM.a.ny, sM.a.walls) &&
-                     (smem_u32(bdsm) & 127u) == 0;
-    if (tma)
-        march_block<T, true>(sM, C, x0, ya, yend, niter, bdsm, bars);
+    if (SC)
+        march_block<T>(sM, B.c, x0, ya, yend, bdsm, bars);
     else
-        march_block<T, false>(sM, C, x0, ya, yend, niter, bdsm, bars);
+        march_block<T>(sM, sM.a.c, x0, ya, yend, bdsm, bars);
 }
 
 template <typename T>
@@ -281,6 +273,8 @@ static int setup_meshes(felbm_batch *b) {
         a.nx = m->sinfo.nx;
         a.ny = m->sinfo.ny;
         a.pitch = m->sinfo.pitch;
+        a.gy = m->sinfo.gy;
+        a.rows = m->sinfo.rows;
         a.walls = m->sinfo.walls ? 1 : 0;
         a.c = lat_coef_b<T>(m, s->params.dt);
         a.P = phys_b<T>(s->params);

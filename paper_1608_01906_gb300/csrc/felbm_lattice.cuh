@@ -40,7 +40,9 @@ struct LatCoef {
 template <typename T>
 struct LatArgs {
     int32_t nx, ny, walls;
-    int32_t pitch;  // population row pitch (slots), nx rounded up to a multiple of 4
+    int32_t pitch;  // population row pitch (slots)
+    int32_t gy;     // ghost rows on each side (slot row of mesh row y: y + gy)
+    int32_t rows;   // slot rows: ny + 2 gy
     LatCoef<T> c;
     Phys<T> P;
     const T *fin;
@@ -106,6 +108,38 @@ __device__ __forceinline__ FillPlan fill_plan(int tid, int nthreads, int gx0, in
     return f;
 }
 
+// Fill plan of a window of H rows x W elements whose top-left element is
+// slot (sx0, sy0) of a storage with rows of `pitch` slots and `rows` slot
+// rows: the columns are inside by construction (ghost columns), rows outside
+// [0, rows) fill with zeros.
+template <typename E, int W, int H, bool VEC>
+__device__ __forceinline__ FillPlan fill_plan_slots(int tid, int nthreads, int sx0, int sy0, int pitch,
+                                                    int rows) {
+    constexpr int CE = 16 / (int)sizeof(E);
+    constexpr int PER_ROW = VEC ? W / CE : W;
+    constexpr int TOTAL = PER_ROW * H;
+    FillPlan f;
+    f.n = 0;
+#pragma unroll
+    for (int t = 0; t < kMaxSlots; ++t) {
+        const int q = tid + t * nthreads;
+        f.src[t] = 0;
+        f.dst[t] = 0;
+        f.ok[t] = 0;
+        if (q < TOTAL) {
+            const int r = q / PER_ROW, c = q - r * PER_ROW;
+            const int col = VEC ? c * CE : c;
+            const int sy = sy0 + r;
+            const bool inside = sy >= 0 && sy < rows;
+            f.src[t] = inside ? sx0 + col + pitch * sy : 0;
+            f.ok[t] = inside;
+            f.dst[t] = r * W + col;
+            f.n = t + 1;
+        }
+    }
+    return f;
+}
+
 // cp.async of one slot; a zero source size fills the destination with zeros.
 template <typename E, bool VEC>
 __device__ __forceinline__ void cp_async_zfill(E *smem, const E *gmem, bool ok) {
@@ -146,22 +180,38 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes) {
                  : "memory");
 }
 // Wait for the phase of the given parity to complete; each try_wait is
-// itself time-limited and the number of tries is bounded: false when the
-// bound ran out.
+// itself time-limited, and the wait gives up after kMbarTries tries or
+// limit_ns nanoseconds of the global timer, whichever comes first: false
+// when it gave up.
 constexpr unsigned kMbarTries = 1u << 20;
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
-    const unsigned a = smem_u32(bar);
+constexpr uint64_t kMbarLimitNs = 2000000000ull;  // 2 s
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ bool mbar_try(unsigned a, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+static __device__ __noinline__ bool mbar_wait_slow(unsigned a, unsigned parity, uint64_t limit_ns) {
+    const uint64_t t0 = global_ns();
     for (unsigned it = 0; it < kMbarTries; ++it) {
-        unsigned done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            " selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done) return true;
+        if (mbar_try(a, parity)) return true;
+        if ((it & 63u) == 63u && global_ns() - t0 > limit_ns) return false;
     }
     return false;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, uint64_t limit_ns = kMbarLimitNs) {
+    const unsigned a = smem_u32(bar);
+    if (mbar_try(a, parity)) return true;
+    return mbar_wait_slow(a, parity, limit_ns);
 }
 // Block-wide wait for a TMA load group: the first warp polls the barrier,
 // the others wait at the block barrier (no issue slots spent polling).
@@ -189,6 +239,17 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const TMap *map, int x, i
         " [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(smem_u32(dst)),
         "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
         : "memory");
+}
+
+// Bring a TMA box into L2 (no shared memory, no completion to wait for).
+__device__ __forceinline__ void tma_prefetch_2d(const TMap *map, int x, int y) {
+    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];\n" ::"l"(map), "r"(x), "r"(y)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_prefetch_3d(const TMap *map, int x, int y, int z) {
+    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];\n" ::"l"(map), "r"(x), "r"(y),
+                 "r"(z)
+                 : "memory");
 }
 
 // Request NF windows (src + f * src_stride -> dst + f * dst_stride).

@@ -1,15 +1,15 @@
 // TMA tensor maps of a state on a structured mesh.
 //
-// For each of the two population buffers c, three maps (3c + 0, 1, 2)
+// For each of the two population buffers c, four maps (4c + 0 .. 3)
 // describe the halo windows of one iteration of the march along y
-// (felbm_march.cuh): the 4 h pairs as a 3-D tensor (x in 4-byte words, y,
-// pair) with a box of 40 columns x 10 rows x 4 pairs; the h rest population
+// (felbm_march.cuh), over the slot arrays (ghost columns and rows included,
+// coordinates in slots): the 4 h pairs as a 3-D tensor (x in 4-byte words,
+// y, pair) with a box of 40 columns x 10 rows x 4 pairs; the h rest population
 // as a 2-D tensor with a box of 40 x 8; the 4 g pairs as a 3-D tensor with a
-// box of the g window (10 rows).  Coordinates outside the mesh load zeros
-// (walls); strips whose windows would wrap periodically use cp.async fills
-// instead.  The maps need rows of a multiple of 16 bytes (the row pitch, a
-// multiple of 4 slots) and the driver's encoder; without it the state keeps
-// d_tmap null and every window is filled by cp.async.
+// box of the g window (10 rows); the g rest population with a box of the
+// strip's own 32 x 8 nodes.  Rows outside the slot rows load zeros (outside
+// a walled domain).  The maps need the driver's encoder; without it the state
+// keeps d_tmap null and every window is filled by cp.async.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -58,16 +58,18 @@ static bool encode(PFN_cuTensorMapEncodeTiled_v12000 fn, TMap *out, void *base, 
 }
 
 template <typename T>
-static bool encode_state(PFN_cuTensorMapEncodeTiled_v12000 fn, const felbm_state *s, TMap maps[6]) {
+static bool encode_state(PFN_cuTensorMapEncodeTiled_v12000 fn, const felbm_state *s, TMap maps[8]) {
     using MS = MarchSmem<T>;
-    const uint64_t nx = (uint64_t)s->mesh->sinfo.nx, ny = (uint64_t)s->mesh->sinfo.ny;
-    const uint64_t pitch = (uint64_t)s->mesh->sinfo.pitch;
+    // the tensors are the slot arrays: pitch slots per row (ghost columns and
+    // padding included), rows slot rows (ghost rows included)
+    const uint64_t pitch = (uint64_t)s->mesh->sinfo.pitch, rows = (uint64_t)s->mesh->sinfo.rows;
+    const uint64_t nx = pitch, ny = rows;
     const uint64_t np = pad4(pop_slots(s->mesh));
     const uint64_t wpn = sizeof(T) * 2 / 4, spn = sizeof(T) / 4;  // words per pair, per scalar
     for (int c = 0; c < 2; ++c) {
         T *f = reinterpret_cast<T *>(s->f[c]);
         const uint64_t pair_rows = pitch * wpn * 4, pair_planes = 2 * np * sizeof(T);
-        TMap *mm = maps + 3 * c;
+        TMap *mm = maps + 4 * c;
         if (!encode(fn, &mm[0], f + np, 3, nx * wpn, ny, 4, pair_rows, pair_planes, (uint32_t)(kMX * wpn),
                     (uint32_t)kHWR, 4))
             return false;
@@ -76,6 +78,9 @@ static bool encode_state(PFN_cuTensorMapEncodeTiled_v12000 fn, const felbm_state
             return false;
         if (!encode(fn, &mm[2], f + 10 * np, 3, nx * wpn, ny, 4, pair_rows, pair_planes,
                     (uint32_t)(MS::GW * wpn), (uint32_t)kGWR, 4))
+            return false;
+        if (!encode(fn, &mm[3], f + 9 * np, 2, nx * spn, ny, 1, pitch * spn * 4, 0, (uint32_t)(32 * spn),
+                    (uint32_t)kMR, 1))
             return false;
     }
     return true;
@@ -87,7 +92,7 @@ void lattice_tmaps(felbm_state *s) {
     if (m->kind != 1 || m->sinfo.pitch % 4 != 0) return;
     PFN_cuTensorMapEncodeTiled_v12000 fn = encoder();
     if (!fn) return;
-    TMap maps[6];
+    TMap maps[8];
     const bool ok = s->esize == 8 ? encode_state<double>(fn, s, maps) : encode_state<float>(fn, s, maps);
     if (!ok) return;
     TMap *d = nullptr;
