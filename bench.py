@@ -97,9 +97,8 @@ def job_rate(world, nodes, steps, seconds):
 # Sources that determine a kernel's code (its ncu counters stay valid while
 # these are unchanged); kernels not listed depend on every source.
 KERNEL_SOURCES = {
-    "k_lat_march": ["csrc/felbm_march.cuh", "csrc/felbm_lattice.cuh", "csrc/felbm_kernels.cuh",
-                    "csrc/felbm_internal.h", "csrc/felbm_api.cu", "csrc/felbm_tmap.cu",
-                    "../include/felbm.h"],
+    "k_lattice_step": ["csrc/felbm_lattice.cuh", "csrc/felbm_kernels.cuh", "csrc/felbm_internal.h",
+                       "csrc/felbm_api.cu", "csrc/felbm_tmap.cu", "../include/felbm.h"],
 }
 
 
@@ -340,7 +339,7 @@ def run_batched(torch, felbm, steps=200):
             "value": nodes * steps / (bat_ms * 1e-3) / 1e6, "unit": UNIT,
             "sequential": nodes * steps / (seq_ms * 1e-3) / 1e6,
             "speedup": seq_ms / bat_ms, "launches_per_step": 1,
-            "segment_rows": info["segment_rows"], "item_order": info["tile_order"]}
+            "blocks_per_sm": info["blocks_per_sm"], "tile_order": info["tile_order"]}
 
 
 def run_serving(torch, felbm, capacity_mnups, n_requests):

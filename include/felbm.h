@@ -169,7 +169,7 @@ void felbm_mesh_destroy(felbm_mesh *mesh);
  *   p0    host, n_nodes doubles or NULL for zero pressure.
  * Device memory: 2 x 18 n_nodes values of the chosen precision plus scratch
  * (2 x 38 n_nodes on tetrahedral meshes)
- * (structured meshes: also 1024 bytes of TMA tensor maps; rows are padded to
+ * (structured meshes: also 768 bytes of TMA tensor maps; rows are padded to
  * a multiple of 4 slots, so every width qualifies).
  * Errors: INVALID_ARG, OOM, CUDA. */
 int felbm_state_init(const felbm_mesh *mesh, const felbm_params *params, const double *rho0,
@@ -210,18 +210,17 @@ void felbm_state_destroy(felbm_state *state);
 
 /* ---- batched launch (many runs per launch; the paper has a single run) ---
  * A batch advances many states on structured meshes (felbm_mesh_info kind
- * 1) of any sizes in one launch per time step: one block per work item, a
- * strip of 32 columns and a segment of rows of one mesh, marched along y as
- * felbm_step does.  The arithmetic of a node depends on its row only, so each
- * state's results are the same as from felbm_step alone.  Step pairs are
- * replayed from a CUDA graph.  With FELBM_BATCH_AUTOTUNE the first
- * felbm_batch_step long enough to afford it times real steps under each
- * candidate (segments of 32, 64 or 128 rows; items mesh-major or
- * interleaved across meshes) and keeps the fastest; those steps count toward
- * n_steps.  When every member has the same coefficient tables (same lattice
- * spacing and dt, and the same walls), the launch carries them once as
- * kernel parameters; otherwise each item reads its mesh's tables.  Results
- * are the same either way.
+ * 1) of any sizes in one launch per time step over every 32 x 8 tile of every
+ * mesh.  Each state's results are the same as from felbm_step alone (same
+ * per-tile code).  Step pairs are replayed from a CUDA graph.  With
+ * FELBM_BATCH_AUTOTUNE the first felbm_batch_step long enough to afford it
+ * times real steps under each candidate (a persistent grid of 1 to the
+ * co-resident maximum blocks per SM, or one block per tile, reported as 0;
+ * tile order mesh-major or interleaved) and keeps the fastest; those steps
+ * count toward n_steps.  When every member has the same coefficient tables
+ * (same lattice spacing and dt, and the same walls), the launch carries them
+ * once as kernel parameters; otherwise each tile reads its mesh's tables.
+ * Results are the same either way.
  *   states   n_states distinct states, same precision, meshes on the same
  *            stream; the batch borrows them (they must outlive it).
  * Stepping a member state on its own between batch steps is allowed; the
@@ -235,9 +234,8 @@ int felbm_batch_create(felbm_state *const *states, int32_t n_states, uint32_t fl
 int felbm_batch_step(felbm_batch *batch, int64_t n_steps);
 int felbm_batch_sync(felbm_batch *batch);
 /* Chosen configuration and counters; any output pointer may be NULL.
- * segment_rows: rows per work item; tile_order: 0 mesh-major, 1 interleaved
- * across meshes; n_tiles: work items per launch. */
-int felbm_batch_info(const felbm_batch *batch, int32_t *segment_rows, int32_t *tile_order,
+ * tile_order: 0 mesh-major, 1 interleaved across meshes. */
+int felbm_batch_info(const felbm_batch *batch, int32_t *blocks_per_sm, int32_t *tile_order,
                      int32_t *n_tiles, int64_t *launches, double *tuned_ms_per_step);
 void felbm_batch_destroy(felbm_batch *batch);
 

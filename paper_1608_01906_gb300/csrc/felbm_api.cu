@@ -4,14 +4,12 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 #include <new>
 #include <vector>
 
 #include "felbm_internal.h"
 #include "felbm_kernels.cuh"
 #include "felbm_lattice.cuh"
-#include "felbm_march.cuh"
 
 using namespace felbm;
 
@@ -137,7 +135,6 @@ static DevLattice<T> dev_lattice(const felbm_mesh *m) {
     d.ny = m->sinfo.ny;
     d.walls = m->sinfo.walls ? 1 : 0;
     d.pitch = m->sinfo.pitch;
-    d.gy = m->sinfo.gy;
     for (int k = 0; k < 3; ++k)
         for (int o = 0; o < 6; ++o) {
             d.c[k][o][0] = (T)m->sinfo.a[k][o][0];
@@ -234,88 +231,61 @@ static LatCoef<T> lat_coef(const felbm_mesh *m, double dt) {
     return c;
 }
 
-// Launch facts of the march on the current device: SM count and resident
-// blocks per SM, with the dynamic shared-memory attribute of k_lat_march set
-// (above the default limit).  Computed once per device (ordinals below 64;
-// others at every call); a refusal is returned to the caller of felbm_step.
 template <typename T>
-static cudaError_t march_setup(int &sms, int &bps) {
-    static std::mutex mu;
-    static int cache[64][2];
+static void step_lattice(felbm_state *s, LatArgs<T> &A, bool write_mom) {
+    const felbm_mesh *m = s->mesh;
+    A.fin = reinterpret_cast<const T *>(s->f[s->cur]);
+    A.fout = reinterpret_cast<T *>(s->f[s->cur ^ 1]);
+    A.mom = write_mom ? reinterpret_cast<T *>(s->mom) : nullptr;
+    A.tmap = s->d_tmap ? s->d_tmap + 3 * s->cur : nullptr;
+    const dim3 grd((A.nx + kLTX - 1) / kLTX, (A.ny + kLTY - 1) / kLTY);
+    const int sl = prof_begin(s, 4);
+    k_lat_step<T><<<grd, dim3(kLTX, kLTY), lat_smem<T>(), m->stream>>>(A);
+    prof_end(s, sl);
+    s->cur ^= 1;
+}
+
+// The dynamic shared memory of k_lat_step is above the default limit: set
+// the function attribute once per device (bit d of done, set only once the
+// call succeeded; devices from 64 on set it at every call).  A refusal is
+// returned to the caller of felbm_step.
+template <typename T>
+static cudaError_t lat_smem_attr() {
+    static std::atomic<uint64_t> done{0};
     int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    std::lock_guard<std::mutex> lock(mu);
-    if (dev >= 0 && dev < 64 && cache[dev][0] > 0) {
-        sms = cache[dev][0];
-        bps = cache[dev][1];
-        return cudaSuccess;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        dev = -1;
     }
-    e = cudaFuncSetAttribute(k_lat_march<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)march_smem<T>());
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_lat_march<T>, kMT, march_smem<T>());
+    const uint64_t bit = (dev >= 0 && dev < 64) ? (uint64_t(1) << dev) : 0;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_lat_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lat_smem<T>());
     if (e != cudaSuccess) {
         cudaGetLastError();
         return e;
     }
-    if (bps < 1) bps = 1;
-    if (dev >= 0 && dev < 64) {
-        cache[dev][0] = sms;
-        cache[dev][1] = bps;
-    }
+    if (bit) done.fetch_or(bit, std::memory_order_release);
     return cudaSuccess;
-}
-
-// Rows per segment of the march: as many segments per strip as keep every
-// block of the grid resident at once (one wave), each a whole number of
-// 8-row iterations; at least one iteration per segment.
-static int march_seg(int nx, int ny, int sms, int bps) {
-    const int nstrips = (nx + 31) / 32;
-    const int rows8 = (ny + kMR - 1) / kMR;
-    int nsegs = std::max(1, (sms * bps) / nstrips);
-    nsegs = std::min(nsegs, rows8);
-    return ((rows8 + nsegs - 1) / nsegs) * kMR;
-}
-
-template <typename T>
-static void step_lattice(felbm_state *s, MarchArgs<T> &M, bool write_mom) {
-    const felbm_mesh *m = s->mesh;
-    LatArgs<T> &A = M.a;
-    A.fin = reinterpret_cast<const T *>(s->f[s->cur]);
-    A.fout = reinterpret_cast<T *>(s->f[s->cur ^ 1]);
-    A.mom = write_mom ? reinterpret_cast<T *>(s->mom) : nullptr;
-    A.tmap = nullptr;
-    M.tmap = s->d_tmap ? s->d_tmap + 4 * s->cur : nullptr;
-    const dim3 grd((A.nx + 31) / 32, (A.ny + M.seg - 1) / M.seg);
-    const int sl = prof_begin(s, 4);
-    k_lat_march<T><<<grd, kMT, march_smem<T>(), m->stream>>>(M);
-    prof_end(s, sl);
-    s->cur ^= 1;
 }
 
 template <typename T>
 static int do_steps(felbm_state *s, int64_t n) {
     const felbm_mesh *m = s->mesh;
     if (m->kind == 1) {
-        int sms = 0, bps = 0;
-        const cudaError_t ea = march_setup<T>(sms, bps);
+        const cudaError_t ea = lat_smem_attr<T>();
         if (ea != cudaSuccess) return cuda_status(ea);
-        MarchArgs<T> M;
-        M.seg = march_seg(m->sinfo.nx, m->sinfo.ny, sms, bps);
-        march_consts<T>(m->sinfo, s->params.dt, M);
-        LatArgs<T> &A = M.a;
+        LatArgs<T> A;
         A.nx = m->sinfo.nx;
         A.ny = m->sinfo.ny;
         A.pitch = m->sinfo.pitch;
-        A.gy = m->sinfo.gy;
-        A.rows = m->sinfo.rows;
         A.walls = m->sinfo.walls ? 1 : 0;
         A.c = lat_coef<T>(m, s->params.dt);
+        lat_uniform_consts<T>(m->sinfo, s->params.dt, A);
         A.P = phys_of<T>(s->params);
         A.rho = fields_of<T>(s).rho;
         A.flag = s->d_flag;
-        for (int64_t k = 0; k < n; ++k) step_lattice<T>(s, M, k == n - 1);
+        for (int64_t k = 0; k < n; ++k) step_lattice<T>(s, A, k == n - 1);
     } else {
         const DevCSR<T> d = dev_csr<T>(m);
         for (int64_t k = 0; k < n; ++k) step_topo<T>(s, d, k == n - 1);
@@ -323,46 +293,12 @@ static int do_steps(felbm_state *s, int64_t n) {
     return FELBM_OK;
 }
 
-// Copy each node's populations into its ghost slots (structured meshes:
-// the copies a window reads past a periodic edge).  After initialisation or
-// an import; the step keeps them current itself.
-template <typename T>
-__global__ void k_fill_ghosts(T *f, int nx, int ny, int pitch, int gy, int rows, size_t np) {
-    const size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= (size_t)pitch * rows) return;
-    const int x = (int)(s % pitch) - kGX, y = (int)(s / pitch) - gy;
-    if (x < -kGX || x >= nx + kGX || y < -gy || y >= ny + gy) return;  // padding
-    if (x >= 0 && x < nx && y >= 0 && y < ny) return;                 // a node's own slot
-    const int xs = (x + nx) % nx, ys = (y + ny) % ny;
-    const size_t src = (size_t)(xs + kGX) + (size_t)pitch * (ys + gy);
-    f[s] = f[src];
-    f[9 * np + s] = f[9 * np + src];
-    V2<T> *ph = reinterpret_cast<V2<T> *>(f + np), *pg = reinterpret_cast<V2<T> *>(f + 10 * np);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        ph[q * np + s] = ph[q * np + src];
-        pg[q * np + s] = pg[q * np + src];
-    }
-}
-
-template <typename T>
-static void fill_ghosts(felbm_state *s) {
-    const felbm_mesh *m = s->mesh;
-    if (m->kind != 1) return;
-    const StructuredInfo &si = m->sinfo;
-    const size_t slots = (size_t)si.pitch * si.rows;
-    k_fill_ghosts<T><<<nblocks((int64_t)slots, 256), 256, 0, m->stream>>>(
-        reinterpret_cast<T *>(s->f[s->cur]), si.nx, si.ny, si.pitch, si.gy, si.rows, pad4(slots));
-}
-
 template <typename T>
 static void init_any(felbm_state *s) {
-    if (s->mesh->kind == 1) {
+    if (s->mesh->kind == 1)
         init_topo<T>(s, dev_lattice<T>(s->mesh));
-        fill_ghosts<T>(s);
-    } else {
+    else
         init_topo<T>(s, dev_csr<T>(s->mesh));
-    }
 }
 
 template <typename T>
@@ -717,13 +653,6 @@ int felbm_state_import(felbm_state *s, const double *hbar, const double *gbar) {
         }
     cudaError_t e = cudaMemcpyAsync(s->f[s->cur], buf.data(), buf.size(), cudaMemcpyHostToDevice,
                                     s->mesh->stream);
-    if (e == cudaSuccess) {
-        if (es == 8)
-            fill_ghosts<double>(s);
-        else
-            fill_ghosts<float>(s);
-        e = cudaGetLastError();
-    }
     if (e == cudaSuccess) e = cudaMemsetAsync(s->d_flag, 0, sizeof(int), s->mesh->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->mesh->stream);
     if (e != cudaSuccess) return cuda_status(e);
@@ -782,7 +711,7 @@ int felbm_profile_read(felbm_state *s, double *ms, int64_t *timed, int64_t *laun
 
 const char *felbm_profile_kind_name(int k) {
     static const char *names[FELBM_PROFILE_KINDS] = {
-        "k_rho", "k_grad", "k_mu", "k_collide", "k_lat_march", "unused5", "unused6",
+        "k_rho", "k_grad", "k_mu", "k_collide", "k_lattice_step", "unused5", "unused6",
         "unused7"};
     return (k >= 0 && k < FELBM_PROFILE_KINDS) ? names[k] : nullptr;
 }

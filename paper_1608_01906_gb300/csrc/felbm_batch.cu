@@ -1,16 +1,16 @@
 // Batched time step: many structured-lattice states of uneven size advance
 // in one launch per time step.
 //
-// The launch runs the march along y of the single-mesh step
-// (felbm_march.cuh) over a list of work items, one block per item: a strip
-// of 32 columns and a segment of rows of one mesh.  The arithmetic of every
-// node depends only on its row (interior rows of a uniform split take the
-// integer-weight operators, wall rows the weight tables), never on the
-// segment that computes it, so a state's results are the same as from
-// felbm_step alone, whatever the batch's segment length.  A step reads only
-// the previous step's populations, so no block waits for another within a
-// launch.  Launches of whole step pairs are captured in a CUDA graph.  An
-// autotuner picks the segment length and the item order by timing real
+// The launch walks a global list of the 32 x 8 tiles of all meshes and runs
+// the single-mesh tile step on each (so a state's results do not depend on
+// which other states share the launch).  A tile step reads only the previous
+// step's populations, so no tile waits for another within a launch.  The
+// grid is either persistent (blocks per SM x SMs) or one block per tile.
+// Block b starts with tile b and claims each further tile from the launch's
+// counter at the start of its current tile; when the claimed tile is on the
+// same mesh and loads by TMA, its h halo is requested as soon as the current
+// tile has formed rho.  Launches of whole step pairs are captured in a CUDA
+// graph.  An autotuner picks the grid and the tile order by timing real
 // steps (all candidates compute identical values, so tuning steps are
 // ordinary steps of the runs).
 #include <algorithm>
@@ -21,20 +21,19 @@
 #include "felbm_internal.h"
 #include "felbm_kernels.cuh"
 #include "felbm_lattice.cuh"
-#include "felbm_march.cuh"
 
 namespace felbm {
 
 struct TileRef {
-    uint16_t mesh, bx, by, pad;  // mesh, strip, segment
+    uint16_t mesh, bx, by, pad;
 };
 
 template <typename T>
 struct BatchMesh {
-    MarchArgs<T> m;  // fin / fout / mom / tmap / seg are set per launch
+    LatArgs<T> a;  // fin / fout / mom / tmap are set per launch from f[], c0
     T *f[2];
     T *mom;
-    const TMap *tmap;  // the state's 2 x 4 tensor maps, or nullptr
+    const TMap *tmap;  // the state's 2 x 3 tensor maps, or nullptr
     int32_t c0;
 };
 
@@ -43,49 +42,100 @@ struct BatchArgs {
     const BatchMesh<T> *meshes;
     const TileRef *tiles;
     int32_t ntiles;
-    int32_t seg;  // rows per segment
+    unsigned *ctr;  // 2 tile counters, by parity
     int parity;
     int write_mom;
     // the coefficient tables of every mesh when they are all the same (same
-    // lattice spacing, dt and walls): read as kernel parameters by the SC
-    // kernel
+    // lattice spacing and dt): read as kernel parameters by the SC kernels
     LatCoef<T> c;
 };
 
-// One block per work item.  SC: the wall rows read the shared tables B.c
-// (kernel parameters), else each mesh's own from its descriptor.
-template <typename T, bool SC>
-__global__ void __launch_bounds__(kMT, sizeof(T) == 4 ? 2 : 1) k_batch_march(const __grid_constant__ BatchArgs<T> B) {
-    __shared__ MarchBars bars;
-    __shared__ __align__(16) MarchArgs<T> sM;
-    extern __shared__ __align__(128) unsigned char bdsm[];
-    const TileRef r = B.tiles[blockIdx.x];
-    {
-        const BatchMesh<T> &bm = B.meshes[r.mesh];
-        static_assert(sizeof(MarchArgs<T>) % 4 == 0, "word copy");
-        const uint32_t *src = reinterpret_cast<const uint32_t *>(&bm.m);
-        uint32_t *dst = reinterpret_cast<uint32_t *>(&sM);
-        for (int w = threadIdx.x; w < (int)(sizeof(MarchArgs<T>) / 4); w += blockDim.x) dst[w] = src[w];
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const int c = bm.c0 ^ B.parity;
-            sM.a.fin = bm.f[c];
-            sM.a.fout = bm.f[c ^ 1];
-            sM.a.mom = B.write_mom ? bm.mom : nullptr;
-            sM.a.tmap = nullptr;
-            sM.tmap = bm.tmap ? bm.tmap + 4 * c : nullptr;
-            sM.seg = B.seg;
-            march_bars_init(bars);
-        }
-        __syncthreads();
+template <typename T>
+__device__ __forceinline__ void load_mesh(const BatchArgs<T> &B, int m, LatArgs<T> &sA, int &cur) {
+    if (m == cur) return;
+    const BatchMesh<T> &bm = B.meshes[m];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    static_assert(sizeof(LatArgs<T>) % 4 == 0, "word copy");
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(&bm.a);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(&sA);
+    for (int w = tid; w < (int)(sizeof(LatArgs<T>) / 4); w += blockDim.x * blockDim.y) dst[w] = src[w];
+    __syncthreads();
+    if (tid == 0) {
+        const int c = bm.c0 ^ B.parity;
+        sA.fin = bm.f[c];
+        sA.fout = bm.f[c ^ 1];
+        sA.mom = B.write_mom ? bm.mom : nullptr;
+        sA.tmap = bm.tmap ? bm.tmap + 3 * c : nullptr;
     }
-    const int x0 = r.bx * 32;
-    const int ya = r.by * B.seg;
-    const int yend = min(ya + B.seg, sM.a.ny);
-    if (SC)
-        march_block<T>(sM, B.c, x0, ya, yend, bdsm, bars);
+    __syncthreads();
+    cur = m;
+}
+
+// SC: all meshes share B.c (interior tiles then read the coefficients as
+// constant operands, as the single-mesh step does), else each mesh's own
+// tables from its shared-memory descriptor.
+template <typename T, bool SC>
+__device__ __forceinline__ const LatCoef<T> &batch_coef(const BatchArgs<T> &B, const LatArgs<T> &sA) {
+    if constexpr (SC)
+        return B.c;
     else
-        march_block<T>(sM, sM.a.c, x0, ya, yend, bdsm, bars);
+        return sA.c;
+}
+
+template <typename T, bool SC>
+__global__ void __launch_bounds__(kNT, (sizeof(T) == 4 ? 768 : 512) / kNT) k_batch_step(const __grid_constant__ BatchArgs<T> B) {
+    __shared__ StepSmem<T> S;
+    __shared__ __align__(16) LatArgs<T> sA;
+    extern __shared__ __align__(128) unsigned char bdsm[];
+    const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
+    if (lead && blockIdx.x == 0) B.ctr[B.parity ^ 1] = 0u;
+    if ((int)blockIdx.x >= B.ntiles) return;
+    lat_block_init<T>(S);
+    TilePipe pp;
+    int cur = -1;
+    // block b starts with tile b and claims the following ones from
+    // ctr[parity]; a claimed tile's h group is requested early only when it
+    // is on the same mesh
+    int t = blockIdx.x;
+    for (;;) {
+        const TileRef r = B.tiles[t];
+        load_mesh<T>(B, r.mesh, sA, cur);
+        NextTile next{0, 0, 0, false, false};
+        if (lead) {
+            next.t = (int)gridDim.x + (int)atomicAdd(&B.ctr[B.parity], 1u);
+            next.valid = next.t < B.ntiles;
+            if (next.valid) {
+                const TileRef rn = B.tiles[next.t];
+                next.bx = rn.bx;
+                next.by = rn.by;
+                next.tma = rn.mesh == r.mesh && tile_tma(sA, rn.bx, rn.by, bdsm);
+            }
+        }
+        if (!lat_tile<T>(sA, batch_coef<T, SC>(B, sA), r.bx, r.by, S, bdsm, pp, next)) return;
+        if (!take_next(S, pp)) return;
+        t = S.nt[0];
+    }
+}
+
+// One block per tile of the batch's tile list, at the register budget of
+// the single-mesh step (4 blocks per SM in FP32).  Zeroes both tile counters,
+// so that a walking launch after it starts from zero.
+template <typename T, bool SC>
+__global__ void __launch_bounds__(kNT, (sizeof(T) == 4 ? 1024 : 512) / kNT) k_batch_tile(const __grid_constant__ BatchArgs<T> B) {
+    __shared__ StepSmem<T> S;
+    __shared__ __align__(16) LatArgs<T> sA;
+    extern __shared__ __align__(128) unsigned char bdsm[];
+    if (blockIdx.x == 0 && threadIdx.x == 0 && threadIdx.y == 0) {
+        B.ctr[0] = 0u;
+        B.ctr[1] = 0u;
+    }
+    lat_block_init<T>(S);
+    const TileRef r = B.tiles[blockIdx.x];
+    int cur = -1;
+    load_mesh<T>(B, r.mesh, sA, cur);
+    TilePipe pp;
+    const NextTile none{0, 0, 0, false, false};
+    lat_tile<T>(sA, batch_coef<T, SC>(B, sA), r.bx, r.by, S, bdsm, pp, none);
 }
 
 template <typename T>
@@ -139,10 +189,11 @@ struct felbm_batch {
     cudaStream_t stream = nullptr;
     void *d_meshes = nullptr;
     TileRef *d_tiles = nullptr;
-    int32_t ntiles = 0, max_tiles = 0;
+    unsigned *d_ctr = nullptr;  // tile counters of the launches, by parity
+    int32_t ntiles = 0;
     int parity = 0;
     int sm_count = 0, max_bps = 1;
-    int seg = 64, order = 0;  // chosen configuration: rows per segment, item order
+    int bps = 1, order = 0;  // chosen configuration (bps 0: one block per tile)
     bool autotune = false, tuned = false;
     double tuned_ms = 0.0;
     cudaGraphExec_t graph = nullptr;
@@ -164,38 +215,7 @@ static int b_status(cudaError_t e) {
 }
 
 static size_t batch_smem(int esize) {
-    return esize == 8 ? march_smem<double>() : march_smem<float>();
-}
-
-// Segment lengths the autotuner tries (rows; multiples of the march's
-// iteration of 8 rows).
-static const int kSegCandidates[] = {32, 64, 128};
-
-// Work items of every member for segments of seg rows: mesh-major and
-// round-robin over meshes.
-static void build_items(felbm_batch *b, int seg) {
-    const size_t n = b->states.size();
-    std::vector<std::vector<TileRef>> per(n);
-    b->tiles_mesh_major.clear();
-    b->tiles_interleaved.clear();
-    for (size_t k = 0; k < n; ++k) {
-        const int tx = (b->states[k]->mesh->sinfo.nx + 31) / 32;
-        const int ty = (b->states[k]->mesh->sinfo.ny + seg - 1) / seg;
-        for (int by = 0; by < ty; ++by)
-            for (int bx = 0; bx < tx; ++bx) per[k].push_back(TileRef{(uint16_t)k, (uint16_t)bx, (uint16_t)by, 0});
-        b->tiles_mesh_major.insert(b->tiles_mesh_major.end(), per[k].begin(), per[k].end());
-    }
-    std::vector<size_t> pos(n, 0);
-    bool any = true;
-    while (any) {
-        any = false;
-        for (size_t k = 0; k < n; ++k)
-            if (pos[k] < per[k].size()) {
-                b->tiles_interleaved.push_back(per[k][pos[k]++]);
-                any = true;
-            }
-    }
-    b->ntiles = (int32_t)b->tiles_mesh_major.size();
+    return esize == 8 ? lat_smem<double>() : lat_smem<float>();
 }
 
 template <typename T>
@@ -204,17 +224,25 @@ static cudaError_t batch_launch(felbm_batch *b, int parity, int write_mom) {
     B.meshes = reinterpret_cast<const BatchMesh<T> *>(b->d_meshes);
     B.tiles = b->d_tiles;
     B.ntiles = b->ntiles;
-    B.seg = b->seg;
+    B.ctr = b->d_ctr;
     B.parity = parity;
     B.write_mom = write_mom;
     std::memset(&B.c, 0, sizeof(B.c));
     if (b->shared_coef) std::memcpy(&B.c, b->coef.data(), sizeof(B.c));
     b->launches++;
+    const dim3 blk(kLTX, kLTY);
     const size_t sm = batch_smem(sizeof(T));
-    if (b->shared_coef)
-        k_batch_march<T, true><<<(unsigned)b->ntiles, kMT, sm, b->stream>>>(B);
-    else
-        k_batch_march<T, false><<<(unsigned)b->ntiles, kMT, sm, b->stream>>>(B);
+    if (b->bps > 0) {
+        const unsigned grid = (unsigned)(b->bps * b->sm_count);
+        if (b->shared_coef)
+            k_batch_step<T, true><<<grid, blk, sm, b->stream>>>(B);
+        else
+            k_batch_step<T, false><<<grid, blk, sm, b->stream>>>(B);
+    } else if (b->shared_coef) {
+        k_batch_tile<T, true><<<(unsigned)b->ntiles, blk, sm, b->stream>>>(B);
+    } else {
+        k_batch_tile<T, false><<<(unsigned)b->ntiles, blk, sm, b->stream>>>(B);
+    }
     return cudaGetLastError();
 }
 
@@ -223,10 +251,7 @@ static cudaError_t launch_any(felbm_batch *b, int parity, int write_mom) {
                          : batch_launch<float>(b, parity, write_mom);
 }
 
-// Items of the current segment length and order to the device (the item
-// array holds the most items of any candidate).
 static cudaError_t upload_tiles(felbm_batch *b) {
-    build_items(b, b->seg);
     const std::vector<TileRef> &src = b->order ? b->tiles_interleaved : b->tiles_mesh_major;
     return cudaMemcpy(b->d_tiles, src.data(), src.size() * sizeof(TileRef), cudaMemcpyHostToDevice);
 }
@@ -269,18 +294,15 @@ static int setup_meshes(felbm_batch *b) {
         const felbm_mesh *m = s->mesh;
         BatchMesh<T> &bm = hm[k];
         std::memset(&bm, 0, sizeof(bm));
-        LatArgs<T> &a = bm.m.a;
-        a.nx = m->sinfo.nx;
-        a.ny = m->sinfo.ny;
-        a.pitch = m->sinfo.pitch;
-        a.gy = m->sinfo.gy;
-        a.rows = m->sinfo.rows;
-        a.walls = m->sinfo.walls ? 1 : 0;
-        a.c = lat_coef_b<T>(m, s->params.dt);
-        a.P = phys_b<T>(s->params);
-        a.rho = reinterpret_cast<T *>(s->scratch);  // first scratch field
-        a.flag = s->d_flag;
-        march_consts<T>(m->sinfo, s->params.dt, bm.m);
+        bm.a.nx = m->sinfo.nx;
+        bm.a.ny = m->sinfo.ny;
+        bm.a.pitch = m->sinfo.pitch;
+        bm.a.walls = m->sinfo.walls ? 1 : 0;
+        bm.a.c = lat_coef_b<T>(m, s->params.dt);
+        bm.a.P = phys_b<T>(s->params);
+        bm.a.rho = reinterpret_cast<T *>(s->scratch);  // first scratch field
+        bm.a.flag = s->d_flag;
+        lat_uniform_consts<T>(m->sinfo, s->params.dt, bm.a);
         bm.f[0] = reinterpret_cast<T *>(s->f[0]);
         bm.f[1] = reinterpret_cast<T *>(s->f[1]);
         bm.mom = reinterpret_cast<T *>(s->mom);
@@ -290,9 +312,9 @@ static int setup_meshes(felbm_batch *b) {
     }
     b->shared_coef = true;
     for (size_t k = 1; k < n; ++k)
-        if (std::memcmp(&hm[k].m.a.c, &hm[0].m.a.c, sizeof(LatCoef<T>)) != 0) b->shared_coef = false;
+        if (std::memcmp(&hm[k].a.c, &hm[0].a.c, sizeof(LatCoef<T>)) != 0) b->shared_coef = false;
     if (n) {
-        const unsigned char *c = reinterpret_cast<const unsigned char *>(&hm[0].m.a.c);
+        const unsigned char *c = reinterpret_cast<const unsigned char *>(&hm[0].a.c);
         b->coef.assign(c, c + sizeof(LatCoef<T>));
     }
     return b_status(cudaMemcpy(b->d_meshes, hm.data(), n * sizeof(BatchMesh<T>), cudaMemcpyHostToDevice));
@@ -302,11 +324,16 @@ template <typename T>
 static int occupancy(felbm_batch *b) {
     int bps = 0;
     const int sm = (int)batch_smem(sizeof(T));
-    cudaError_t e = cudaFuncSetAttribute(k_batch_march<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    cudaError_t e = cudaFuncSetAttribute(k_batch_tile<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_batch_march<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        e = cudaFuncSetAttribute(k_batch_tile<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_batch_march<T, false>, kMT, batch_smem(sizeof(T)));
+        e = cudaFuncSetAttribute(k_batch_step<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_batch_step<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_batch_step<T, false>, kLTX * kLTY,
+                                                          batch_smem(sizeof(T)));
     if (e != cudaSuccess) return b_status(e);
     b->max_bps = std::max(1, bps);
     return FELBM_OK;
@@ -343,8 +370,8 @@ int felbm_batch_create(felbm_state *const *states, int32_t n_states, uint32_t fl
     for (int32_t k = 0; k < n_states; ++k) {
         felbm_state *s = states[k];
         if (!s || s->mesh->kind != 1 || (int)s->esize != (int)states[0]->esize ||
-            s->mesh->stream != states[0]->mesh->stream || s->mesh->sinfo.nx > 65535 * 32 ||
-            s->mesh->sinfo.ny > 65535 * kSegCandidates[0]) {
+            s->mesh->stream != states[0]->mesh->stream || s->mesh->sinfo.nx > 65535 * kLTX ||
+            s->mesh->sinfo.ny > 65535 * kLTY) {
             delete b;
             return (s && s->mesh->kind != 1) ? FELBM_ERR_UNSUPPORTED : FELBM_ERR_INVALID_ARG;
         }
@@ -358,20 +385,42 @@ int felbm_batch_create(felbm_state *const *states, int32_t n_states, uint32_t fl
     b->c0.assign(n_states, 0);
     b->stream = states[0]->mesh->stream;
     b->autotune = (flags & FELBM_BATCH_AUTOTUNE) != 0;
-    // the item array holds the most items of any candidate segment length
-    build_items(b, kSegCandidates[0]);
-    b->max_tiles = b->ntiles;
+    // tile lists: mesh-major and round-robin over meshes (largest first)
+    std::vector<std::vector<TileRef>> per(n_states);
+    for (int32_t k = 0; k < n_states; ++k) {
+        const int tx = (states[k]->mesh->sinfo.nx + kLTX - 1) / kLTX;
+        const int ty = (states[k]->mesh->sinfo.ny + kLTY - 1) / kLTY;
+        for (int by = 0; by < ty; ++by)
+            for (int bx = 0; bx < tx; ++bx)
+                per[k].push_back(TileRef{(uint16_t)k, (uint16_t)bx, (uint16_t)by, 0});
+        b->tiles_mesh_major.insert(b->tiles_mesh_major.end(), per[k].begin(), per[k].end());
+    }
+    {
+        std::vector<size_t> pos(n_states, 0);
+        bool any = true;
+        while (any) {
+            any = false;
+            for (int32_t k = 0; k < n_states; ++k)
+                if (pos[k] < per[k].size()) {
+                    b->tiles_interleaved.push_back(per[k][pos[k]++]);
+                    any = true;
+                }
+        }
+    }
+    b->ntiles = (int32_t)b->tiles_mesh_major.size();
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sm_count, cudaDevAttrMultiProcessorCount, dev);
     const size_t mesh_bytes = (size_t)n_states * (b->esize == 8 ? sizeof(BatchMesh<double>)
                                                                 : sizeof(BatchMesh<float>));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_meshes, mesh_bytes);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_tiles, (size_t)b->max_tiles * sizeof(TileRef));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_tiles, (size_t)b->ntiles * sizeof(TileRef));
+    if (e == cudaSuccess) e = cudaMalloc((void **)&b->d_ctr, 2 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(b->d_ctr, 0, 2 * sizeof(unsigned));
     int st = b_status(e);
     if (st == FELBM_OK) st = b->esize == 8 ? occupancy<double>(b) : occupancy<float>(b);
     if (st == FELBM_OK) {
-        b->seg = 64;
+        b->bps = b->max_bps;
         b->order = 0;
         st = b_status(upload_tiles(b));
     }
@@ -384,8 +433,8 @@ int felbm_batch_create(felbm_state *const *states, int32_t n_states, uint32_t fl
     return FELBM_OK;
 }
 
-// Time `trial` direct steps under each candidate (segment length x item
-// order) and keep the fastest.  Steps taken here are ordinary steps.
+// Time `trial` direct steps under each candidate (blocks per SM, or one
+// block per tile, x tile order) and keep the fastest.  Steps taken here are ordinary steps.
 static int autotune(felbm_batch *b, int trial, int64_t *used) {
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return FELBM_ERR_CUDA;
@@ -394,15 +443,13 @@ static int autotune(felbm_batch *b, int trial, int64_t *used) {
         return FELBM_ERR_CUDA;
     }
     double best = 1e30;
-    int best_seg = b->seg, best_order = b->order;
+    int best_bps = b->bps, best_order = b->order;
     int st = FELBM_OK;
     for (int order = 0; order < 2 && st == FELBM_OK; ++order) {
-        for (int seg : kSegCandidates) {
-            if (st != FELBM_OK) break;
-            b->order = order;
-            b->seg = seg;
-            st = b_status(upload_tiles(b));
-            if (st != FELBM_OK) break;
+        b->order = order;
+        st = b_status(upload_tiles(b));
+        for (int bps = 0; bps <= b->max_bps && st == FELBM_OK; ++bps) {
+            b->bps = bps;
             // one untimed step, then `trial` timed steps
             cudaError_t e = launch_any(b, b->parity, 0);
             b->parity ^= 1;
@@ -420,7 +467,7 @@ static int autotune(felbm_batch *b, int trial, int64_t *used) {
             st = b_status(e);
             if (st == FELBM_OK && ms / trial < best) {
                 best = ms / trial;
-                best_seg = seg;
+                best_bps = bps;
                 best_order = order;
             }
         }
@@ -428,7 +475,7 @@ static int autotune(felbm_batch *b, int trial, int64_t *used) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != FELBM_OK) return st;
-    b->seg = best_seg;
+    b->bps = best_bps;
     b->order = best_order;
     b->tuned = true;
     b->tuned_ms = best;
@@ -444,7 +491,7 @@ int felbm_batch_step(felbm_batch *b, int64_t n_steps) {
     cudaError_t e = cudaSuccess;
     if (b->autotune && !b->tuned) {
         const int trial = 3;
-        const int64_t need = 2LL * (int64_t)(sizeof(kSegCandidates) / sizeof(int)) * (trial + 1) + 1;
+        const int64_t need = 2LL * (b->max_bps + 1) * (trial + 1) + 1;
         if (left > need) {
             int64_t used = 0;
             int st = autotune(b, trial, &used);
@@ -506,10 +553,10 @@ int felbm_batch_sync(felbm_batch *b) {
     return FELBM_OK;
 }
 
-int felbm_batch_info(const felbm_batch *b, int32_t *segment_rows, int32_t *tile_order,
+int felbm_batch_info(const felbm_batch *b, int32_t *blocks_per_sm, int32_t *tile_order,
                      int32_t *n_tiles, int64_t *launches, double *tuned_ms_per_step) {
     if (!b) return FELBM_ERR_INVALID_ARG;
-    if (segment_rows) *segment_rows = b->seg;
+    if (blocks_per_sm) *blocks_per_sm = b->bps;
     if (tile_order) *tile_order = b->order;
     if (n_tiles) *n_tiles = b->ntiles;
     if (launches) *launches = b->launches;
@@ -523,6 +570,7 @@ void felbm_batch_destroy(felbm_batch *b) {
     drop_graph(b);
     cudaFree(b->d_meshes);
     cudaFree(b->d_tiles);
+    cudaFree(b->d_ctr);
     delete b;
 }
 

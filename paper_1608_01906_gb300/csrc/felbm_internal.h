@@ -76,19 +76,10 @@ constexpr int lat3_dz(int o) {
     return (o == 4 || o == 8 || o == 10 || o == 12) ? 1 : (o == 5 || o == 9 || o == 11 || o == 13) ? -1 : 0;
 }
 
-// Population storage of a structured mesh: node (x, y) has slot
-// (x + kGX) + pitch (y + gy), rows of pitch = nx rounded up to a multiple of
-// 32, plus 2 kGX, slots.  The kGX ghost columns on each side (and, when y is
-// periodic, gy = kGX ghost rows below and above) hold copies of the periodic
-// images, so that every halo window of the step is one rectangle of slots.
-constexpr int kGX = 4;
-
 struct StructuredInfo {
     bool ok = false;
     int32_t nx = 0, ny = 0;
-    int32_t pitch = 0;   // population row pitch in slots (see above)
-    int32_t gy = 0;      // ghost rows on each side (kGX if y is periodic, else 0)
-    int32_t rows = 0;    // ny + 2 gy
+    int32_t pitch = 0;   // population row pitch: nx rounded up to a multiple of 4
     bool walls = false;  // non-periodic y with walls on the first and last row
     double h = 1.0;
     // 6 neighbour offsets (dx, dy) and their assembled a/b coefficients of an
@@ -147,8 +138,8 @@ struct DevCSR {
 // Structured lattice split (node i = x + nx*y): six neighbours at fixed
 // offsets, coefficients of three row kinds (0 interior, 1 bottom wall row,
 // 2 top wall row) held in the kernel parameters.  Populations are stored in
-// rows of `pitch` slots with ghost columns and rows (StructuredInfo), so that
-// every row starts 16-byte aligned.
+// rows of `pitch` slots (x + pitch*y), pitch = nx rounded up to a multiple
+// of 4, so that every row starts 16-byte aligned.
 // offsets o = 0..5: (1,0), (1,1), (0,1), (-1,0), (-1,-1), (0,-1)
 #ifdef __CUDACC__
 __host__ __device__
@@ -161,7 +152,7 @@ constexpr int lat_dy(int o) { return o == 1 || o == 2 ? 1 : (o == 4 || o == 5 ? 
 
 template <typename T>
 struct DevLattice {
-    int32_t n, nx, ny, walls, pitch, gy;
+    int32_t n, nx, ny, walls, pitch;
     T c[3][6][5];  // ax, ay, bxx, bxy, byy
 #ifdef __CUDACC__
     template <typename Fn>
@@ -186,9 +177,9 @@ struct DevLattice {
     }
     __device__ __forceinline__ size_t slot(int32_t i) const {
         const int32_t y = i / nx;
-        return (size_t)(i - y * nx + kGX) + (size_t)pitch * (size_t)(y + gy);
+        return (size_t)(i - y * nx) + (size_t)pitch * (size_t)y;
     }
-    __device__ __forceinline__ size_t slots() const { return (size_t)pitch * (size_t)(ny + 2 * gy); }
+    __device__ __forceinline__ size_t slots() const { return (size_t)pitch * (size_t)ny; }
 #endif
 };
 
@@ -281,12 +272,12 @@ struct felbm_mesh {
 inline int mesh_dim(const felbm_mesh *m) { return m->kind >= 2 ? 3 : 2; }
 inline int mesh_q(const felbm_mesh *m) { return m->kind >= 2 ? 19 : 9; }
 inline size_t pop_slots(const felbm_mesh *m) {
-    return m->kind == 1 ? (size_t)m->sinfo.pitch * (size_t)m->sinfo.rows : (size_t)m->n_nodes;
+    return m->kind == 1 ? (size_t)m->sinfo.pitch * (size_t)m->sinfo.ny : (size_t)m->n_nodes;
 }
 inline size_t pop_slot(const felbm_mesh *m, size_t i) {
     if (m->kind != 1) return i;
     const size_t nx = (size_t)m->sinfo.nx;
-    return i % nx + felbm::kGX + (size_t)m->sinfo.pitch * (i / nx + (size_t)m->sinfo.gy);
+    return i % nx + (size_t)m->sinfo.pitch * (i / nx);
 }
 
 struct felbm_state {
@@ -300,7 +291,7 @@ struct felbm_state {
     void *mom = nullptr;              // 4 N: rho, ux, uy, p (internal order)
     double *d_out = nullptr;          // 5 N staging in caller order + reduction partials
     int *d_flag = nullptr;            // bit 0: non-finite field, bit 2: bounded wait gave up
-    TMap *d_tmap = nullptr;           // structured meshes: 2 buffers x {h pairs, h rest, g pairs, g rest}
+    TMap *d_tmap = nullptr;           // structured meshes: 2 buffers x {h pairs, h rest, g pairs}
     bool have_moments = false;
     int64_t steps_done = 0;
     // profiling: event pairs around launches (felbm_profile_enable)

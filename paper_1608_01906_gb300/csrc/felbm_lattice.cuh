@@ -1,15 +1,27 @@
-// Building blocks of the structured-lattice step (felbm_march.cuh): the
-// coefficient tables and arguments of a lattice, halo windows filled with
-// cp.async or loaded by TMA (cp.async.bulk.tensor with mbarrier waits that
-// are bounded), the Taylor-Galerkin streaming of a pair of opposite
-// populations from a shared-memory window (Sec. 2.2.1), bounce-back at wall
-// rows (Sec. 3.3) and the collision of a pair (Sec. 2.2).
+// Structured-lattice step: one launch per time step, one 32 x 8 tile of
+// nodes per block (k_lat_step).
 //
+//   1. the 4 h pair tiles (halo depth 4) and the h rest tile are staged in
+//      shared memory; the h populations are streamed (Taylor-Galerkin,
+//      Sec. 2.2.1) and bounced back at walls on the tile's depth-3 halo, and
+//      rho = sum_a h_a there; the tile's own streamed h pairs are kept;
+//   2. grad rho (depth 2), lap rho and mu (depth 1), then grad mu and the
+//      stress force at the tile's nodes (Sec. 2.3 recovery, Sec. 2.1 mu,
+//      stress form);
+//   3. the g pairs are streamed from depth-1 tiles, the moments formed and
+//      all populations collided (Sec. 2.2); one write of the 18 populations.
+//
+// The density stage recomputes the streaming of h on the halo instead of a
+// separate density launch: neighbouring tiles share no data within a step.
 // Opposite directions (a, abar) are stored interleaved (pop_index): the
 // stencil of a pair reads one 8-byte (FP32) word per neighbour and runs in
 // packed two-wide arithmetic (FFMA2 on sm_103a), each lane with its own
 // coefficient.  Population rows are stored with a pitch of nx rounded up to
-// a multiple of 4 slots, so every row starts 16-byte aligned.
+// a multiple of 4 slots, so every row starts 16-byte aligned.  Halo windows
+// that need no periodic wrap arrive as TMA boxes, the others by cp.async
+// (16-byte chunks unless a chunk would straddle the wrap of a row whose
+// length is not a multiple of 4); all are requested when the block starts,
+// and the g tiles arrive while rho and the scalar chain are computed.
 //
 // Coefficient tables: for each row kind (interior, bottom wall row, top wall
 // row), offset o and pair q, the streaming coefficients of the pair's two
@@ -24,7 +36,7 @@
 
 namespace felbm {
 
-constexpr int kLTX = 32, kLTY = 8;  // strip width and rows per iteration of the march
+constexpr int kLTX = 32, kLTY = 8;  // tile of nodes per block
 
 template <int V>
 struct IntC {
@@ -40,9 +52,7 @@ struct LatCoef {
 template <typename T>
 struct LatArgs {
     int32_t nx, ny, walls;
-    int32_t pitch;  // population row pitch (slots)
-    int32_t gy;     // ghost rows on each side (slot row of mesh row y: y + gy)
-    int32_t rows;   // slot rows: ny + 2 gy
+    int32_t pitch;  // population row pitch (slots), nx rounded up to a multiple of 4
     LatCoef<T> c;
     Phys<T> P;
     const T *fin;
@@ -51,7 +61,112 @@ struct LatArgs {
     T *mom;  // 4N or nullptr
     int *flag;
     const TMap *tmap;  // {h pairs, h rest, g pairs} of fin, or nullptr
+    // interior operators of the uniform split (below): used on interior
+    // tiles when uni is set (the host checked the mesh's interior weights)
+    int32_t uni;
+    T al;        // 1 / (6 h)
+    V2<T> ka;    // (-dt/(6h), dt/(6h)): odd part of the streaming weights
+    V2<T> kb;    // (dt^2/(2h^2), dt^2/(2h^2)): even part
 };
+
+// ---- interior operators of the structured split --------------------------
+// On a split of a lattice of spacing h, every node whose six neighbours are
+// inside the mesh has the same assembled weights (felbm_mesh.cu reads them
+// off the assembled operators, a_ij = sum |T| grad N_j / (3 m_i) and the
+// symmetric part of b_ij = sum |T| / m_i grad N_i (x) grad N_j).  For the
+// offsets o = (1,0), (1,1), (0,1), (-1,0), (-1,-1), (0,-1):
+//   6h a_o = (2,-1), (1,1), (-1,2), (-2,1), (-1,-1), (1,-2)   (a_{o+3} = -a_o)
+//   h^2 b_o (xx, xy, yy) = (-1,1/2,0), (0,-1/2,0), (0,1/2,-1), the same for o+3.
+// With E_k = f(o_k) - f(o_{k+3}) and S_k = (f(o_k) - f) + (f(o_{k+3}) - f):
+//   recovered gradient  R_x f = (2 E_0 + E_1 - E_2) / (6h),
+//                       R_y f = (-E_0 + E_1 + 2 E_2) / (6h);
+//   streaming of the pair q (directions e, -e):
+//     psi* = psi + (-dt/(6h), dt/(6h)) (.) SA_q + dt^2/(2h^2) SB_q
+//   with SA = e.(2E_0 + E_1 - E_2, -E_0 + E_1 + 2E_2) and SB = -sum_o
+//   (e.(h^2 b_o).e) d_o:  q0 e = (1,0): SA = 2E_0 + E_1 - E_2, SB = S_0;
+//   q1 (0,1): -E_0 + E_1 + 2E_2, S_2;  q2 (1,1): E_0 + 2E_1 + E_2, S_1;
+//   q3 (-1,1): 3(E_2 - E_0), 2(S_0 + S_2) - S_1.
+// Only differences of neighbouring values are rounded, as in the weighted
+// difference form of the tables (exact for constant fields); no weight is
+// loaded.  Opposite offsets carry opposite recovery weights, so a recovered
+// derivative needs three differences instead of six.
+
+template <typename T>
+__device__ __forceinline__ V2<T> vsub(V2<T> a, V2<T> b) {
+    return vfma(b, vset(T(-1), T(-1)), a);
+}
+
+// streamed pair Q of the node at index c of a window with rows of W pairs
+template <typename T, int W, int Q>
+__device__ __forceinline__ V2<T> stream_uni(const V2<T> *b, int c, V2<T> ka, V2<T> kb) {
+    const V2<T> s = b[c];
+    const V2<T> n0 = b[c + 1], n1 = b[c + W + 1], n2 = b[c + W];
+    const V2<T> n3 = b[c - 1], n4 = b[c - W - 1], n5 = b[c - W];
+    const V2<T> two = vset(T(2), T(2));
+    if (Q == 0) {
+        const V2<T> SA = vfma(vsub<T>(n0, n3), two, vsub<T>(vsub<T>(n1, n4), vsub<T>(n2, n5)));
+        const V2<T> SB = vadd(vsub<T>(n0, s), vsub<T>(n3, s));
+        return vfma(ka, SA, vfma(kb, SB, s));
+    } else if (Q == 1) {
+        const V2<T> SA = vfma(vsub<T>(n2, n5), two, vsub<T>(vsub<T>(n1, n4), vsub<T>(n0, n3)));
+        const V2<T> SB = vadd(vsub<T>(n2, s), vsub<T>(n5, s));
+        return vfma(ka, SA, vfma(kb, SB, s));
+    } else if (Q == 2) {
+        const V2<T> SA = vfma(vsub<T>(n1, n4), two, vadd(vsub<T>(n0, n3), vsub<T>(n2, n5)));
+        const V2<T> SB = vadd(vsub<T>(n1, s), vsub<T>(n4, s));
+        return vfma(ka, SA, vfma(kb, SB, s));
+    } else {
+        const V2<T> d0 = vsub<T>(n0, s), d1 = vsub<T>(n1, s), d2 = vsub<T>(n2, s);
+        const V2<T> d3 = vsub<T>(n3, s), d4 = vsub<T>(n4, s), d5 = vsub<T>(n5, s);
+        const V2<T> S02 = vadd(vadd(d0, d3), vadd(d2, d5));
+        const V2<T> SB = vsub<T>(vadd(S02, S02), vadd(d1, d4));
+        const V2<T> SA = vsub<T>(vadd(d2, d3), vadd(d0, d5));  // E_2 - E_0
+        return vfma(vmul(ka, vset(T(3), T(3))), SA, vfma(kb, SB, s));
+    }
+}
+
+// (6h R_x f, 6h R_y f) from the six neighbour values
+template <typename T>
+__device__ __forceinline__ void rec_uni(T f0, T f1, T f2, T f3, T f4, T f5, T &rx, T &ry) {
+    const T E0 = f0 - f3, E1 = f1 - f4, E2 = f2 - f5;
+    rx = fma(T(2), E0, E1 - E2);
+    ry = fma(T(2), E2, E1 - E0);
+}
+
+// Whether the interior weights of a structured mesh are those of the split
+// of a lattice of spacing h that the integer-weight operators assume (a_o
+// 6h and b_o h^2 to 1e-12 of their size); else every tile uses the tables.
+inline bool lattice_uniform(const StructuredInfo &si) {
+    static const double A[6][2] = {{2, -1}, {1, 1}, {-1, 2}, {-2, 1}, {-1, -1}, {1, -2}};
+    static const double B[6][3] = {{-1, 0.5, 0}, {0, -0.5, 0}, {0, 0.5, -1},
+                                   {-1, 0.5, 0}, {0, -0.5, 0}, {0, 0.5, -1}};
+    const double h = si.h;
+    if (!(h > 0.0)) return false;
+    for (int o = 0; o < 6; ++o) {
+        for (int c = 0; c < 2; ++c) {
+            const double d = si.a[0][o][c] * 6.0 * h - A[o][c];
+            if (d > 1e-12 || d < -1e-12) return false;
+        }
+        for (int c = 0; c < 3; ++c) {
+            const double d = si.b[0][o][c] * h * h - B[o][c];
+            if (d > 1e-12 || d < -1e-12) return false;
+        }
+    }
+    return true;
+}
+
+// The interior-operator constants of a mesh for time step dt.
+template <typename T>
+inline void lat_uniform_consts(const StructuredInfo &si, double dt, LatArgs<T> &A) {
+    const double h = si.h;
+    A.uni = lattice_uniform(si) ? 1 : 0;
+    A.al = (T)(1.0 / (6.0 * h));
+    const double ka = dt / (6.0 * h), kb = dt * dt / (2.0 * h * h);
+    A.ka.x = (T)-ka;
+    A.ka.y = (T)ka;
+    A.kb.x = (T)kb;
+    A.kb.y = (T)kb;
+}
 
 __device__ __forceinline__ int lat_kind(int walls, int y, int ny) {
     return walls ? (y == 0 ? 1 : (y == ny - 1 ? 2 : 0)) : 0;
@@ -100,38 +215,6 @@ __device__ __forceinline__ FillPlan fill_plan(int tid, int nthreads, int gx0, in
                 while (gy >= ny) gy -= ny;
             }
             f.src[t] = inside ? gx + pitch * gy : 0;
-            f.ok[t] = inside;
-            f.dst[t] = r * W + col;
-            f.n = t + 1;
-        }
-    }
-    return f;
-}
-
-// Fill plan of a window of H rows x W elements whose top-left element is
-// slot (sx0, sy0) of a storage with rows of `pitch` slots and `rows` slot
-// rows: the columns are inside by construction (ghost columns), rows outside
-// [0, rows) fill with zeros.
-template <typename E, int W, int H, bool VEC>
-__device__ __forceinline__ FillPlan fill_plan_slots(int tid, int nthreads, int sx0, int sy0, int pitch,
-                                                    int rows) {
-    constexpr int CE = 16 / (int)sizeof(E);
-    constexpr int PER_ROW = VEC ? W / CE : W;
-    constexpr int TOTAL = PER_ROW * H;
-    FillPlan f;
-    f.n = 0;
-#pragma unroll
-    for (int t = 0; t < kMaxSlots; ++t) {
-        const int q = tid + t * nthreads;
-        f.src[t] = 0;
-        f.dst[t] = 0;
-        f.ok[t] = 0;
-        if (q < TOTAL) {
-            const int r = q / PER_ROW, c = q - r * PER_ROW;
-            const int col = VEC ? c * CE : c;
-            const int sy = sy0 + r;
-            const bool inside = sy >= 0 && sy < rows;
-            f.src[t] = inside ? sx0 + col + pitch * sy : 0;
             f.ok[t] = inside;
             f.dst[t] = r * W + col;
             f.n = t + 1;
@@ -241,17 +324,6 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const TMap *map, int x, i
         : "memory");
 }
 
-// Bring a TMA box into L2 (no shared memory, no completion to wait for).
-__device__ __forceinline__ void tma_prefetch_2d(const TMap *map, int x, int y) {
-    asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];\n" ::"l"(map), "r"(x), "r"(y)
-                 : "memory");
-}
-__device__ __forceinline__ void tma_prefetch_3d(const TMap *map, int x, int y, int z) {
-    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];\n" ::"l"(map), "r"(x), "r"(y),
-                 "r"(z)
-                 : "memory");
-}
-
 // Request NF windows (src + f * src_stride -> dst + f * dst_stride).
 template <typename E, bool VEC, int NF>
 __device__ __forceinline__ void fill_issue(const FillPlan &f, const E *__restrict__ src, size_t src_stride,
@@ -279,6 +351,20 @@ struct PairTile {
     static constexpr int H = kLTY + 2 * D;
     static constexpr int N = W * H;
 };
+
+// Request the depth-D halo tiles of the 4 pairs of h (G = 0) or g (G = 1).
+// VEC: 16-byte chunks (needs a window without x wrap, or nx % 4 == 0, so
+// that no chunk straddles the wrap).
+template <typename T, int G, int D, bool VEC>
+__device__ __forceinline__ void issue_pair_tiles(const LatArgs<T> &A, int tid, int x0, int y0,
+                                                 V2<T> *tiles, size_t np) {
+    using E = V2<T>;
+    using PT = PairTile<T, D>;
+    const E *src = reinterpret_cast<const E *>(A.fin + (G ? 10 : 1) * np);  // pair 0; pair q at + q np
+    const FillPlan f =
+        fill_plan<E, PT::W, PT::H, VEC>(tid, kLTX * kLTY, x0 - PT::XH, y0 - D, A.nx, A.pitch, A.ny, A.walls);
+    fill_issue<E, VEC, 4>(f, src, np, tiles, PT::N);
+}
 
 // Streamed values of pair q of the node whose element in the halo tile buf
 // (rows of W elements) is c, at row kind k:
@@ -342,17 +428,470 @@ __device__ __forceinline__ V2<T> bounce_pair(int k, int q, V2<T> v) {
     return k == 1 ? vset(v.y, v.y) : vset(v.x, v.x);
 }
 
-// ---- windows of the march ------------------------------------------
+// ---- one step of a tile ---------------------------------------------------
 
-constexpr int kHD = 4;  // depth of the h windows in x (columns x0-4 .. x0+35)
+constexpr int kHD = 4;                            // depth of the h pair tiles
+constexpr int kH0W = kLTX + 8, kH0H = kLTY + 6;   // h rest tile: from (x0 - 4, y0 - 3)
+constexpr int kQW = kLTX + 6, kQH = kLTY + 6;     // rho region: halo 3
+constexpr int kRW = kLTX + 8, kRH = kLTY + 6;     // rho: rows from x0 - 4 (column 0, 39 unused)
+constexpr int kGW = kLTX + 4, kGH = kLTY + 4;     // grad rho: halo 2
+constexpr int kMW = kLTX + 2, kMH = kLTY + 2;     // mu: halo 1
+constexpr int kNT = kLTX * kLTY;
+
+// Shared memory of one tile: the scalar chain (static) and the population
+// tiles (dynamic, lat_smem bytes).  The streamed g pairs stay in registers.
+template <typename T>
+struct __align__(16) StepSmem {
+    uint64_t bar[2];  // TMA completion: h tiles, g tiles
+    int nt[4];        // the block's next tile as claimed by thread 0: index, bx, by, flags
+    T s_rho[kRH][kRW];
+    T s_gx[kGH][kGW], s_gy[kGH][kGW];
+    T s_mu[kMH][kMW];
+};
 
 constexpr size_t align128(size_t b) { return (b + 127) / 128 * 128; }
 
-// Whether the halo windows of a strip at x0 may be filled in 16-byte
-// chunks: rows are 16-byte aligned (pitch), so unless a window wraps around
-// a row whose length is not a multiple of 4.
+// Regions of the dynamic shared memory, each 128-byte aligned (TMA
+// destinations).  The byte sizes of the h tiles (pairs + rest) and of the g
+// tiles are what one TMA load group delivers.
+template <typename T>
+struct LatSmem {
+    using PH = PairTile<T, kHD>;
+    using PG = PairTile<T, 1>;
+    static constexpr unsigned hT_bytes = 4 * PH::N * sizeof(V2<T>);
+    static constexpr unsigned h0_bytes = kH0W * kH0H * sizeof(T);
+    static constexpr unsigned gT_bytes = 4 * PG::N * sizeof(V2<T>);
+    static constexpr size_t hT = 0;                             // 4 h pair tiles
+    static constexpr size_t h0 = align128(hT + hT_bytes);      // h rest tile
+    static constexpr size_t gT = align128(h0 + h0_bytes);      // 4 g pair tiles
+    static constexpr size_t psi = align128(gT + gT_bytes);     // streamed h pairs
+    static constexpr size_t bytes = psi + 4 * (size_t)kNT * sizeof(V2<T>);
+};
+
+template <typename T>
+constexpr size_t lat_smem() {
+    return LatSmem<T>::bytes;
+}
+
+// Whether the halo windows of a tile at x0 may be filled in 16-byte chunks:
+// rows are 16-byte aligned (pitch), so unless a window wraps around a row
+// whose length is not a multiple of 4.
 __device__ __forceinline__ bool vec_fills(int x0, int nx) {
     return (nx % 4) == 0 || (x0 >= kHD && x0 + kLTX + kHD <= nx);
+}
+
+// Whether tile (x0, y0) is whole (no node outside the mesh), its rho region
+// and h tiles hold no wall row nor a row outside a walled domain, and rows
+// are 16-byte aligned: such tiles run with the row kind fixed at compile
+// time and vector fills only.
+__device__ __forceinline__ bool tile_interior(int x0, int y0, int nx, int ny, int walls, int uni) {
+    const bool yin = walls ? (y0 >= kHD && y0 + kLTY + kHD <= ny) : (y0 + kLTY <= ny);
+    return uni && yin && x0 + kLTX <= nx && vec_fills(x0, nx);
+}
+
+// Whether the halo windows of tile (x0, y0) lie inside the mesh without a
+// periodic wrap: a TMA box then covers each of them.
+__device__ __forceinline__ bool tile_unwrapped(int x0, int y0, int nx, int ny) {
+    return x0 >= kHD && x0 + kLTX + kHD <= nx && y0 >= kHD && y0 + kLTY + kHD <= ny;
+}
+
+// Collision of one node: the g pairs are streamed here from their depth-1
+// tiles, the h pairs were streamed by the density stage.
+template <typename T, bool UNI>
+__device__ __forceinline__ void lat_node(const LatArgs<T> &A, const LatCoef<T> &C, int k, int lx, int ly,
+                                         int tid, int32_t i,
+                                         size_t ip, size_t n, size_t np, T h0, T g0, T r0, T drx, T dry,
+                                         T dmx, T dmy, T kx, T ky, const V2<T> *gT,
+                                         const V2<T> (*s_psi)[kNT]) {
+    using PG = PairTile<T, 1>;
+    const Phys<T> &P = A.P;
+    const int c = (ly + 1) * PG::W + lx + PG::XH;
+    V2<T> gq[4];
+    if (UNI) {
+        gq[0] = stream_uni<T, PG::W, 0>(gT + 0 * PG::N, c, A.ka, A.kb);
+        gq[1] = stream_uni<T, PG::W, 1>(gT + 1 * PG::N, c, A.ka, A.kb);
+        gq[2] = stream_uni<T, PG::W, 2>(gT + 2 * PG::N, c, A.ka, A.kb);
+        gq[3] = stream_uni<T, PG::W, 3>(gT + 3 * PG::N, c, A.ka, A.kb);
+    } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        gq[q] = bounce_pair<T>(k, q, stream_pair<T, PG::W>(C, k, q, gT + q * PG::N, c, P.dt));
+    }
+    T sg, mx, my;
+    // g_1 = q0.x, g_3 = q0.y, g_2 = q1.x, g_4 = q1.y, g_5 = q2.x, g_7 = q2.y, g_6 = q3.x, g_8 = q3.y
+    g_moments<T>(g0, gq[0].x, gq[1].x, gq[0].y, gq[1].y, gq[2].x, gq[3].x, gq[2].y, gq[3].y, sg, mx, my);
+    const CollidePrep<T> cp = collide_prep<T>(P, sg, mx, my, r0, drx, dry, dmx, dmy, kx, ky);
+    const T r = cp.r, ux = cp.ux, uy = cp.uy, p = cp.p;
+    // pairs, then the rest population, which also takes the sum of the h
+    // increments (zero in exact arithmetic): the collision then keeps the
+    // node's mass to one rounding instead of accumulating the rounding of the
+    // nine source terms every step
+    T dsum = T(0);
+    V2<T> *hout = reinterpret_cast<V2<T> *>(A.fout + np);
+    V2<T> *gout = reinterpret_cast<V2<T> *>(A.fout + 10 * np);
+    auto pair_update = [&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        const V2<T> hs = s_psi[q][tid];
+        V2<T> ho, go;
+        collide_pair<T, q>(cp, hs, gq[q], ho, go);
+        dsum += (ho.x - hs.x) + (ho.y - hs.y);
+        hout[(size_t)q * np + ip] = ho;
+        gout[(size_t)q * np + ip] = go;
+    };
+    pair_update(IntC<0>{});
+    pair_update(IntC<1>{});
+    pair_update(IntC<2>{});
+    pair_update(IntC<3>{});
+    {
+        T ho, go;
+        collide_pop_rt<T>(cp, 0, h0, g0, ho, go);
+        dsum += ho - h0;
+        A.fout[ip] = ho - dsum;
+        A.fout[9 * np + ip] = go;
+    }
+    if (!(finite_val(r) && finite_val(ux) && finite_val(uy) && finite_val(p))) atomicOr(A.flag, 1);
+    if (A.mom) {
+        A.mom[i] = r;
+        A.mom[n + i] = ux;
+        A.mom[2 * n + i] = uy;
+        A.mom[3 * n + i] = p;
+    }
+}
+
+// TMA state of a block walking its tiles (same value in every thread).
+struct TilePipe {
+    unsigned ph[2] = {0u, 0u};  // parity of the next phase of bar[0] (h group), bar[1] (g group)
+    bool h_issued = false;      // the current tile's h group was requested during the previous tile
+};
+
+// The block's next tile (known to thread 0 only): its h group is requested
+// as soon as the current tile has formed rho (tma: it loads by TMA, from
+// the same mesh).  Thread 0 publishes it in S.nt (flags: bit 0 valid, bit 1
+// h group requested) for the whole block after the tile.
+struct NextTile {
+    int t, bx, by;
+    bool valid, tma;
+};
+
+// Request the h group (4 h pair tiles + the rest tile) of tile (x0, y0).
+template <typename T>
+__device__ __forceinline__ void issue_h_group(const LatArgs<T> &A, int x0, int y0, StepSmem<T> &S,
+                                              unsigned char *dsm) {
+    using L = LatSmem<T>;
+    using PH = PairTile<T, kHD>;
+    constexpr int WPN = (int)sizeof(V2<T>) / 4, SPN = (int)sizeof(T) / 4;  // 4-byte words per element
+    fence_proxy_async();
+    mbar_expect_tx(&S.bar[0], L::hT_bytes + L::h0_bytes);
+    tma_load_3d(dsm + L::hT, A.tmap + 0, (x0 - PH::XH) * WPN, y0 - kHD, 0, &S.bar[0]);
+    tma_load_2d(dsm + L::h0, A.tmap + 1, (x0 - 4) * SPN, y0 - 3, &S.bar[0]);
+}
+
+// Request the g group (4 g pair tiles) of tile (x0, y0).
+template <typename T>
+__device__ __forceinline__ void issue_g_group(const LatArgs<T> &A, int x0, int y0, StepSmem<T> &S,
+                                              unsigned char *dsm) {
+    using L = LatSmem<T>;
+    using PG = PairTile<T, 1>;
+    constexpr int WPN = (int)sizeof(V2<T>) / 4;
+    fence_proxy_async();
+    mbar_expect_tx(&S.bar[1], L::gT_bytes);
+    tma_load_3d(dsm + L::gT, A.tmap + 2, (x0 - PG::XH) * WPN, y0 - 1, 0, &S.bar[1]);
+}
+
+// A bounded wait for a TMA load ran out: record it, give the loads still in
+// flight one more bounded wait each, and stop (all threads alike).
+template <typename T>
+__device__ __noinline__ bool tma_gave_up(const LatArgs<T> &A, StepSmem<T> &S, const TilePipe &pp) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        atomicOr(A.flag, 4);
+        mbar_wait(&S.bar[0], pp.ph[0]);
+        mbar_wait(&S.bar[1], pp.ph[1]);
+    }
+    __syncthreads();
+    return false;
+}
+
+// One time step of tile (bx, by).  TMA: the halo windows come as TMA boxes
+// (tile_unwrapped, interior tiles) completing on S.bar, else as cp.async
+// fills.  C: the mesh's coefficient tables (kernel parameters where they
+// can be, so that interior tiles read them as constant operands).  Returns
+// false (all threads alike) when a bounded wait for a TMA load gave up; the
+// flag then carries bit 2.
+template <typename T, bool INTERIOR, bool TMA>
+__device__ __forceinline__ bool lat_tile_impl(const LatArgs<T> &A, const LatCoef<T> &C, int bx, int by,
+                                              StepSmem<T> &S, unsigned char *dsm, TilePipe &pp,
+                                              const NextTile &next) {
+    using L = LatSmem<T>;
+    using PH = PairTile<T, kHD>;
+    auto &s_rho = S.s_rho;
+    auto &s_gx = S.s_gx;
+    auto &s_gy = S.s_gy;
+    auto &s_mu = S.s_mu;
+    V2<T> *hT = reinterpret_cast<V2<T> *>(dsm + L::hT);
+    T(*s_h0)[kH0W] = reinterpret_cast<T(*)[kH0W]>(dsm + L::h0);
+    V2<T> *gT = reinterpret_cast<V2<T> *>(dsm + L::gT);
+    V2<T>(*s_psi)[kNT] = reinterpret_cast<V2<T>(*)[kNT]>(dsm + L::psi);
+    const int nx = A.nx, ny = A.ny, walls = A.walls;
+    const int x0 = bx * kLTX, y0 = by * kLTY;
+    const int tid = threadIdx.y * kLTX + threadIdx.x;
+    const size_t n = (size_t)nx * ny, np = pad4((size_t)A.pitch * ny);
+    const T dt = A.P.dt;
+    // 0. request the h pair tiles (depth 4) and the h rest tile (depth 3) as
+    //    group 1, the g pair tiles (depth 1) as group 2; the g tiles arrive
+    //    while rho and the scalar chain are computed
+    if (TMA) {
+        if (tid == 0) {
+            if (!pp.h_issued) issue_h_group<T>(A, x0, y0, S, dsm);
+            issue_g_group<T>(A, x0, y0, S, dsm);
+        }
+    } else if (INTERIOR || vec_fills(x0, nx)) {
+        issue_pair_tiles<T, 0, kHD, true>(A, tid, x0, y0, hT, np);
+        fill_issue<T, true, 1>(fill_plan<T, kH0W, kH0H, true>(tid, kNT, x0 - 4, y0 - 3, nx, A.pitch, ny, walls),
+                               A.fin, 0, &s_h0[0][0], 0);
+        cp_async_commit();
+        issue_pair_tiles<T, 1, 1, true>(A, tid, x0, y0, gT, np);
+    } else {
+        issue_pair_tiles<T, 0, kHD, false>(A, tid, x0, y0, hT, np);
+        fill_issue<T, false, 1>(fill_plan<T, kH0W, kH0H, false>(tid, kNT, x0 - 4, y0 - 3, nx, A.pitch, ny, walls),
+                                A.fin, 0, &s_h0[0][0], 0);
+        cp_async_commit();
+        issue_pair_tiles<T, 1, 1, false>(A, tid, x0, y0, gT, np);
+    }
+    if (!TMA) cp_async_commit();
+    // the node's g rest population (not moved by streaming): requested now so
+    // that its latency overlaps the density stage and the scalar chain
+    const int x = x0 + (int)threadIdx.x, y = y0 + (int)threadIdx.y;
+    const bool valid = INTERIOR || (x < nx && y < ny);
+    const int32_t i = valid ? x + nx * y : 0;                        // node (moments)
+    const size_t ip = valid ? (size_t)x + (size_t)A.pitch * y : 0;  // population slot
+    const T g0 = valid ? __ldg(A.fin + 9 * np + ip) : T(0);
+    // rows of the rho region (y0 - 3 .. y0 + 10) all of kind 0 and inside
+    const bool rows_in = INTERIOR || !walls || (y0 >= kHD && y0 + kLTY + kHD <= ny);
+    if (TMA) {
+        if (!block_mbar_wait(&S.bar[0], pp.ph[0])) return tma_gave_up(A, S, pp);
+        pp.ph[0] ^= 1u;
+    } else {
+        cp_async_wait_group<1>();
+        __syncthreads();
+    }
+    // the node's own rest population, read before the h tiles are reused
+    const T h0 = s_h0[threadIdx.y + 3][threadIdx.x + 4];
+    // 1. rho = sum of the streamed, bounced-back h on the depth-3 region
+    //    (s_rho[r][c] = global (x0 - 4 + c, y0 - 3 + r); zero outside a walled
+    //    domain, where only zero coefficients meet it); the tile's own
+    //    streamed h pairs are kept for the collision
+    for (int q = tid; q < kQW * kQH; q += kNT) {
+        const int ry = q / kQW, rx = q - ry * kQW;
+        const int gy = y0 + ry - 3;
+        T r = T(0);
+        if (rows_in || (gy >= 0 && gy < ny)) {
+            const int k = rows_in ? 0 : lat_kind(walls, gy, ny);
+            const int c = (ry + 1) * PH::W + rx + (PH::XH - 3);
+            const bool own = (unsigned)(rx - 3) < (unsigned)kLTX && (unsigned)(ry - 3) < (unsigned)kLTY;
+            const int o = (ry - 3) * kLTX + (rx - 3);
+            r = s_h0[ry][rx + 1];
+            V2<T> v[4];
+            if (INTERIOR) {
+                // interior tile: the integer-weight operators
+                v[0] = stream_uni<T, PH::W, 0>(hT + 0 * PH::N, c, A.ka, A.kb);
+                v[1] = stream_uni<T, PH::W, 1>(hT + 1 * PH::N, c, A.ka, A.kb);
+                v[2] = stream_uni<T, PH::W, 2>(hT + 2 * PH::N, c, A.ka, A.kb);
+                v[3] = stream_uni<T, PH::W, 3>(hT + 3 * PH::N, c, A.ka, A.kb);
+            } else {
+#pragma unroll
+                for (int p = 0; p < 4; ++p)
+                    v[p] = bounce_pair<T>(k, p, stream_pair<T, PH::W>(C, k, p, hT + p * PH::N, c, dt));
+            }
+            r = r + ((v[0].x + v[0].y) + (v[1].x + v[1].y)) + ((v[2].x + v[2].y) + (v[3].x + v[3].y));
+            if (own) {
+#pragma unroll
+                for (int p = 0; p < 4; ++p) s_psi[p][o] = v[p];
+            }
+        }
+        s_rho[ry][rx + 1] = r;
+    }
+    __syncthreads();
+    // the h pair tiles and the rest tile are dead (nothing below reads them):
+    // request the next tile's h group now, so that it arrives while this
+    // tile finishes
+    if (tid == 0) {
+        if (next.tma) issue_h_group<T>(A, next.bx * kLTX, next.by * kLTY, S, dsm);
+        S.nt[0] = next.t;
+        S.nt[1] = next.bx;
+        S.nt[2] = next.by;
+        S.nt[3] = (next.valid ? 1 : 0) | (next.tma ? 2 : 0);
+    }
+    const auto &rc = C.r;  // recovery coefficients
+    // 2. recovered grad rho on the depth-2 region
+    for (int q = tid; q < kGW * kGH; q += kNT) {
+        const int ly = q / kGW, lx = q - ly * kGW;
+        const int gy = y0 + ly - 2;
+        const int k = (!INTERIOR && walls && (gy == 0 || gy == ny - 1)) ? (gy == 0 ? 1 : 2) : 0;
+        T sx = T(0), sy = T(0);
+        if (INTERIOR) {
+            const int a = ly + 1, b = lx + 2;
+            rec_uni<T>(s_rho[a][b + 1], s_rho[a + 1][b + 1], s_rho[a + 1][b], s_rho[a][b - 1], s_rho[a - 1][b - 1],
+                       s_rho[a - 1][b], sx, sy);
+            sx *= A.al;
+            sy *= A.al;
+        } else {
+            const T c0 = s_rho[ly + 1][lx + 2];
+#pragma unroll
+            for (int o = 0; o < 6; ++o) {
+                const T d = s_rho[ly + 1 + lat_dy(o)][lx + 2 + lat_dx(o)] - c0;
+                sx += rc[k][o][0] * d;
+                sy += rc[k][o][1] * d;
+            }
+        }
+        s_gx[ly][lx] = sx;
+        s_gy[ly][lx] = sy;
+    }
+    __syncthreads();
+    // 3. lap rho and mu on the depth-1 region
+    const Phys<T> &P = A.P;
+    for (int q = tid; q < kMW * kMH; q += kNT) {
+        const int ly = q / kMW, lx = q - ly * kMW;
+        const int gy = y0 + ly - 1;
+        const int k = (!INTERIOR && walls && (gy == 0 || gy == ny - 1)) ? (gy == 0 ? 1 : 2) : 0;
+        T lap = T(0);
+        if (INTERIOR) {
+            const int a = ly + 1, b = lx + 1;
+            const T E0x = s_gx[a][b + 1] - s_gx[a][b - 1], E1x = s_gx[a + 1][b + 1] - s_gx[a - 1][b - 1],
+                    E2x = s_gx[a + 1][b] - s_gx[a - 1][b];
+            const T E0y = s_gy[a][b + 1] - s_gy[a][b - 1], E1y = s_gy[a + 1][b + 1] - s_gy[a - 1][b - 1],
+                    E2y = s_gy[a + 1][b] - s_gy[a - 1][b];
+            lap = A.al * (fma(T(2), E0x, E1x - E2x) + fma(T(2), E2y, E1y - E0y));
+        } else {
+            const T gxc = s_gx[ly + 1][lx + 1], gyc = s_gy[ly + 1][lx + 1];
+#pragma unroll
+            for (int o = 0; o < 6; ++o) {
+                lap += rc[k][o][0] * (s_gx[ly + 1 + lat_dy(o)][lx + 1 + lat_dx(o)] - gxc) +
+                       rc[k][o][1] * (s_gy[ly + 1 + lat_dy(o)][lx + 1 + lat_dx(o)] - gyc);
+            }
+        }
+        s_mu[ly][lx] = mu_bulk<T>(P, s_rho[ly + 2][lx + 3]) - P.kappa * lap;
+    }
+    __syncthreads();
+    // 4. per node: grad mu, stress force, then the collision.  Threads of a
+    //    ragged tile outside the mesh take part in every barrier.
+    const int lx = threadIdx.x, ly = threadIdx.y;
+    const int k = (rows_in || !valid) ? 0 : lat_kind(walls, y, ny);
+    T dmx, dmy, kx, ky;
+    if (INTERIOR) {
+        const int a = ly + 1, b = lx + 1, a2 = ly + 2, b2 = lx + 2;
+        rec_uni<T>(s_mu[a][b + 1], s_mu[a + 1][b + 1], s_mu[a + 1][b], s_mu[a][b - 1], s_mu[a - 1][b - 1], s_mu[a - 1][b],
+                   dmx, dmy);
+        dmx *= A.al;
+        dmy *= A.al;
+        // differences of the gradient products across opposite neighbours,
+        // in product form: (P.x, P.y) = E(d_x rho^2), E(d_y rho^2);
+        // Q = E(d_x rho d_y rho); then
+        // K_x = kappa [R_x(d_y rho^2) - R_y(d_x rho d_y rho)],
+        // K_y = kappa [R_y(d_x rho^2) - R_x(d_x rho d_y rho)]
+        V2<T> Pk[3];
+        T Qk[3];
+        auto prod = [&](int j, V2<T> u, V2<T> w) {
+            const V2<T> D = vsub<T>(u, w);
+            Pk[j] = vmul(D, vadd(u, w));
+            Qk[j] = fma(u.x, D.y, w.y * D.x);
+        };
+        prod(0, vset(s_gx[a2][b2 + 1], s_gy[a2][b2 + 1]), vset(s_gx[a2][b2 - 1], s_gy[a2][b2 - 1]));
+        prod(1, vset(s_gx[a2 + 1][b2 + 1], s_gy[a2 + 1][b2 + 1]), vset(s_gx[a2 - 1][b2 - 1], s_gy[a2 - 1][b2 - 1]));
+        prod(2, vset(s_gx[a2 + 1][b2], s_gy[a2 + 1][b2]), vset(s_gx[a2 - 1][b2], s_gy[a2 - 1][b2]));
+        const T rxy = fma(T(2), Pk[0].y, Pk[1].y - Pk[2].y), ryq = fma(T(2), Qk[2], Qk[1] - Qk[0]);
+        const T ryx = fma(T(2), Pk[2].x, Pk[1].x - Pk[0].x), rxq = fma(T(2), Qk[0], Qk[1] - Qk[2]);
+        const T kka = P.kappa * A.al;
+        kx = kka * (rxy - ryq);
+        ky = kka * (ryx - rxq);
+    } else {
+        T smx = T(0), smy = T(0), skx = T(0), sky = T(0);
+        const T mc = s_mu[ly + 1][lx + 1];
+        const T gxc = s_gx[ly + 2][lx + 2], gyc = s_gy[ly + 2][lx + 2];
+#pragma unroll
+        for (int o = 0; o < 6; ++o) {
+            const T ax = rc[k][o][0], ay = rc[k][o][1];
+            const T dm = s_mu[ly + 1 + lat_dy(o)][lx + 1 + lat_dx(o)] - mc;
+            smx += ax * dm;
+            smy += ay * dm;
+            const T gxj = s_gx[ly + 2 + lat_dy(o)][lx + 2 + lat_dx(o)];
+            const T gyj = s_gy[ly + 2 + lat_dy(o)][lx + 2 + lat_dx(o)];
+            const T ddx = gxj - gxc, ddy = gyj - gyc;  // product form, see k_mu
+            const T dxx = ddx * (gxj + gxc), dxy = gxj * ddy + gyc * ddx, dyy = ddy * (gyj + gyc);
+            skx += ax * dyy - ay * dxy;
+            sky += ay * dxx - ax * dxy;
+        }
+        dmx = smx;
+        dmy = smy;
+        kx = P.kappa * skx;
+        ky = P.kappa * sky;
+    }
+    const T r0 = s_rho[ly + 3][lx + 4];
+    const T drx = s_gx[ly + 2][lx + 2], dry = s_gy[ly + 2][lx + 2];
+    if (TMA) {
+        if (!block_mbar_wait(&S.bar[1], pp.ph[1])) return tma_gave_up(A, S, pp);
+        pp.ph[1] ^= 1u;
+    } else {
+        cp_async_wait_group<0>();
+        __syncthreads();
+    }
+    if (valid)
+        lat_node<T, INTERIOR>(A, C, k, lx, ly, tid, i, ip, n, np, h0, g0, r0, drx, dry, dmx, dmy, kx, ky, gT, s_psi);
+    __syncthreads();  // the caller may reuse shared memory for the next tile
+    return true;
+}
+
+// Barriers of the TMA loads; once per block before its first tile.
+template <typename T>
+__device__ __forceinline__ void lat_block_init(StepSmem<T> &S) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        mbar_init(&S.bar[0], 1);
+        mbar_init(&S.bar[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+}
+
+// Whether tile (bx, by) loads its halo windows by TMA.
+template <typename T>
+__device__ __forceinline__ bool tile_tma(const LatArgs<T> &A, int bx, int by, const unsigned char *dsm) {
+    const int x0 = bx * kLTX, y0 = by * kLTY;
+    return A.tmap && tile_interior(x0, y0, A.nx, A.ny, A.walls, A.uni) && tile_unwrapped(x0, y0, A.nx, A.ny) &&
+           (smem_u32(dsm) & 127u) == 0;
+}
+
+// One tile of a block's walk (pp carries the TMA barrier phases and whether
+// this tile's h group was already requested; next is the block's next tile).
+// False when a bounded wait gave up.
+template <typename T>
+__device__ __forceinline__ bool lat_tile(const LatArgs<T> &A, const LatCoef<T> &C, int bx, int by, StepSmem<T> &S,
+                                         unsigned char *dsm, TilePipe &pp, const NextTile &next) {
+    if (tile_tma(A, bx, by, dsm)) return lat_tile_impl<T, true, true>(A, C, bx, by, S, dsm, pp, next);
+    if (tile_interior(bx * kLTX, by * kLTY, A.nx, A.ny, A.walls, A.uni))
+        return lat_tile_impl<T, true, false>(A, C, bx, by, S, dsm, pp, next);
+    return lat_tile_impl<T, false, false>(A, C, bx, by, S, dsm, pp, next);
+}
+
+// After a tile: the published next tile (false: none), and whether its h
+// group was requested.
+template <typename T>
+__device__ __forceinline__ bool take_next(const StepSmem<T> &S, TilePipe &pp) {
+    const int f = S.nt[3];
+    pp.h_issued = (f & 2) != 0;
+    return (f & 1) != 0;
+}
+
+// One tile per block (grid ntx x nty).  Halo windows of interior tiles come
+// by TMA; walking several tiles per block with the next tile's h group
+// requested early measured slower for a single mesh (more instructions per
+// node, no better issue rate), so that walk is left to the batched kernel.
+template <typename T>
+__global__ void __launch_bounds__(kNT, (sizeof(T) == 4 ? 1024 : 512) / kNT) k_lat_step(LatArgs<T> A) {
+    __shared__ StepSmem<T> S;
+    extern __shared__ __align__(128) unsigned char lat_dsm[];
+    lat_block_init<T>(S);
+    TilePipe pp;
+    const NextTile none{0, 0, 0, false, false};
+    lat_tile<T>(A, A.c, blockIdx.x, blockIdx.y, S, lat_dsm, pp, none);
 }
 
 }  // namespace felbm

@@ -330,10 +330,8 @@ void detect_structured(const double *xy, int64_t n_nodes, const int32_t *tri, in
         }
     }
     info.nx = (int32_t)nx;
-    info.pitch = (int32_t)(((nx + 31) & ~(int64_t)31) + 2 * kGX);
+    info.pitch = (int32_t)((nx + 3) & ~(int64_t)3);
     info.ny = (int32_t)ny;
-    info.gy = py ? kGX : 0;
-    info.rows = (int32_t)ny + 2 * info.gy;
     info.walls = walls;
     info.h = h;
     info.ok = true;

@@ -1,15 +1,16 @@
 // TMA tensor maps of a state on a structured mesh.
 //
-// For each of the two population buffers c, four maps (4c + 0 .. 3)
-// describe the halo windows of one iteration of the march along y
-// (felbm_march.cuh), over the slot arrays (ghost columns and rows included,
-// coordinates in slots): the 4 h pairs as a 3-D tensor (x in 4-byte words,
-// y, pair) with a box of 40 columns x 10 rows x 4 pairs; the h rest population
-// as a 2-D tensor with a box of 40 x 8; the 4 g pairs as a 3-D tensor with a
-// box of the g window (10 rows); the g rest population with a box of the
-// strip's own 32 x 8 nodes.  Rows outside the slot rows load zeros (outside
-// a walled domain).  The maps need the driver's encoder; without it the state
-// keeps d_tmap null and every window is filled by cp.async.
+// For each of the two population buffers, three maps describe the halo
+// windows a tile step loads (felbm_lattice.cuh):
+//   0  the 4 h pairs: 3-D (x in 4-byte words, y, pair), box of the depth-4
+//      pair tile;
+//   1  the h rest population: 2-D (x in words, y), box of the rest tile;
+//   2  the 4 g pairs: 3-D, box of the depth-1 pair tile.
+// Coordinates outside the mesh load zeros (walls); tiles whose windows would
+// wrap periodically use cp.async fills instead.  The maps need rows of a
+// multiple of 16 bytes (the row pitch, a multiple of 4 slots) and the
+// driver's encoder; without it the state keeps d_tmap null and every tile
+// uses cp.async.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -19,7 +20,6 @@
 #include "felbm_internal.h"
 #include "felbm_kernels.cuh"
 #include "felbm_lattice.cuh"
-#include "felbm_march.cuh"
 
 namespace felbm {
 
@@ -58,29 +58,24 @@ static bool encode(PFN_cuTensorMapEncodeTiled_v12000 fn, TMap *out, void *base, 
 }
 
 template <typename T>
-static bool encode_state(PFN_cuTensorMapEncodeTiled_v12000 fn, const felbm_state *s, TMap maps[8]) {
-    using MS = MarchSmem<T>;
-    // the tensors are the slot arrays: pitch slots per row (ghost columns and
-    // padding included), rows slot rows (ghost rows included)
-    const uint64_t pitch = (uint64_t)s->mesh->sinfo.pitch, rows = (uint64_t)s->mesh->sinfo.rows;
-    const uint64_t nx = pitch, ny = rows;
+static bool encode_state(PFN_cuTensorMapEncodeTiled_v12000 fn, const felbm_state *s, TMap maps[6]) {
+    using PH = PairTile<T, kHD>;
+    using PG = PairTile<T, 1>;
+    const uint64_t nx = (uint64_t)s->mesh->sinfo.nx, ny = (uint64_t)s->mesh->sinfo.ny;
+    const uint64_t pitch = (uint64_t)s->mesh->sinfo.pitch;
     const uint64_t np = pad4(pop_slots(s->mesh));
     const uint64_t wpn = sizeof(T) * 2 / 4, spn = sizeof(T) / 4;  // words per pair, per scalar
     for (int c = 0; c < 2; ++c) {
         T *f = reinterpret_cast<T *>(s->f[c]);
         const uint64_t pair_rows = pitch * wpn * 4, pair_planes = 2 * np * sizeof(T);
-        TMap *mm = maps + 4 * c;
-        if (!encode(fn, &mm[0], f + np, 3, nx * wpn, ny, 4, pair_rows, pair_planes, (uint32_t)(kMX * wpn),
-                    (uint32_t)kHWR, 4))
+        if (!encode(fn, &maps[3 * c + 0], f + np, 3, nx * wpn, ny, 4, pair_rows, pair_planes,
+                    (uint32_t)(PH::W * wpn), (uint32_t)PH::H, 4))
             return false;
-        if (!encode(fn, &mm[1], f, 2, nx * spn, ny, 1, pitch * spn * 4, 0, (uint32_t)(kMX * spn), (uint32_t)kMR,
-                    1))
+        if (!encode(fn, &maps[3 * c + 1], f, 2, nx * spn, ny, 1, pitch * spn * 4, 0, (uint32_t)(kH0W * spn),
+                    (uint32_t)kH0H, 1))
             return false;
-        if (!encode(fn, &mm[2], f + 10 * np, 3, nx * wpn, ny, 4, pair_rows, pair_planes,
-                    (uint32_t)(MS::GW * wpn), (uint32_t)kGWR, 4))
-            return false;
-        if (!encode(fn, &mm[3], f + 9 * np, 2, nx * spn, ny, 1, pitch * spn * 4, 0, (uint32_t)(32 * spn),
-                    (uint32_t)kMR, 1))
+        if (!encode(fn, &maps[3 * c + 2], f + 10 * np, 3, nx * wpn, ny, 4, pair_rows, pair_planes,
+                    (uint32_t)(PG::W * wpn), (uint32_t)PG::H, 4))
             return false;
     }
     return true;
@@ -92,7 +87,7 @@ void lattice_tmaps(felbm_state *s) {
     if (m->kind != 1 || m->sinfo.pitch % 4 != 0) return;
     PFN_cuTensorMapEncodeTiled_v12000 fn = encoder();
     if (!fn) return;
-    TMap maps[8];
+    TMap maps[6];
     const bool ok = s->esize == 8 ? encode_state<double>(fn, s, maps) : encode_state<float>(fn, s, maps);
     if (!ok) return;
     TMap *d = nullptr;

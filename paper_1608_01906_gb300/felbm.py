@@ -362,11 +362,11 @@ class Batch:
         _check(load().felbm_batch_sync(self.handle), "felbm_batch_sync")
 
     def info(self):
-        seg, order, nt = C.c_int32(), C.c_int32(), C.c_int32()
+        bps, order, nt = C.c_int32(), C.c_int32(), C.c_int32()
         launches, ms = C.c_int64(), C.c_double()
-        _check(load().felbm_batch_info(self.handle, C.byref(seg), C.byref(order), C.byref(nt),
+        _check(load().felbm_batch_info(self.handle, C.byref(bps), C.byref(order), C.byref(nt),
                                        C.byref(launches), C.byref(ms)), "felbm_batch_info")
-        return {"segment_rows": seg.value, "tile_order": order.value, "n_tiles": nt.value,
+        return {"blocks_per_sm": bps.value, "tile_order": order.value, "n_tiles": nt.value,
                 "launches": launches.value, "tuned_ms_per_step": ms.value}
 
     def close(self):
