@@ -96,12 +96,11 @@ __device__ __forceinline__ V2<T> vsub(V2<T> a, V2<T> b) {
     return vfma(b, vset(T(-1), T(-1)), a);
 }
 
-// streamed pair Q of the node at index c of a window with rows of W pairs
-template <typename T, int W, int Q>
-__device__ __forceinline__ V2<T> stream_uni(const V2<T> *b, int c, V2<T> ka, V2<T> kb) {
-    const V2<T> s = b[c];
-    const V2<T> n0 = b[c + 1], n1 = b[c + W + 1], n2 = b[c + W];
-    const V2<T> n3 = b[c - 1], n4 = b[c - W - 1], n5 = b[c - W];
+// streamed pair Q of a node from its own value s and its neighbours n_o at
+// the offsets o = (1,0), (1,1), (0,1), (-1,0), (-1,-1), (0,-1)
+template <typename T, int Q>
+__device__ __forceinline__ V2<T> stream_uni_v(V2<T> s, V2<T> n0, V2<T> n1, V2<T> n2, V2<T> n3, V2<T> n4,
+                                              V2<T> n5, V2<T> ka, V2<T> kb) {
     const V2<T> two = vset(T(2), T(2));
     if (Q == 0) {
         const V2<T> SA = vfma(vsub<T>(n0, n3), two, vsub<T>(vsub<T>(n1, n4), vsub<T>(n2, n5)));
@@ -123,6 +122,30 @@ __device__ __forceinline__ V2<T> stream_uni(const V2<T> *b, int c, V2<T> ka, V2<
         const V2<T> SA = vsub<T>(vadd(d2, d3), vadd(d0, d5));  // E_2 - E_0
         return vfma(vmul(ka, vset(T(3), T(3))), SA, vfma(kb, SB, s));
     }
+}
+
+// streamed pair Q of the node at index c of a window with rows of W pairs
+template <typename T, int W, int Q>
+__device__ __forceinline__ V2<T> stream_uni(const V2<T> *b, int c, V2<T> ka, V2<T> kb) {
+    return stream_uni_v<T, Q>(b[c], b[c + 1], b[c + W + 1], b[c + W], b[c - 1], b[c - W - 1], b[c - W], ka, kb);
+}
+
+// The same for three nodes stacked in one column, from 13 loads instead of
+// 21: rb[j] is the offset of the window row holding y - 1 + j (j = 0 .. 4,
+// y the first node's row), c the column.
+template <typename T, int Q>
+__device__ __forceinline__ void stream_uni3(const V2<T> *b, const int *rb, int c, V2<T> ka, V2<T> kb, V2<T> *out) {
+    V2<T> cx[5], cl[4], cr[4];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) cx[j] = b[rb[j] + c];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        cl[j] = b[rb[j] + c - 1];
+        cr[j] = b[rb[j + 1] + c + 1];
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+        out[i] = stream_uni_v<T, Q>(cx[i + 1], cr[i], cr[i + 1], cx[i + 2], cl[i + 1], cl[i], cx[i], ka, kb);
 }
 
 // (6h R_x f, 6h R_y f) from the six neighbour values
@@ -445,7 +468,7 @@ struct __align__(16) StepSmem {
     uint64_t bar[2];  // TMA completion: h tiles, g tiles
     int nt[4];        // the block's next tile as claimed by thread 0: index, bx, by, flags
     T s_rho[kRH][kRW];
-    T s_gx[kGH][kGW], s_gy[kGH][kGW];
+    V2<T> s_g[kGH][kGW];  // recovered grad rho, (x, y) interleaved
     T s_mu[kMH][kMW];
 };
 
@@ -624,8 +647,7 @@ __device__ __forceinline__ bool lat_tile_impl(const LatArgs<T> &A, const LatCoef
     using L = LatSmem<T>;
     using PH = PairTile<T, kHD>;
     auto &s_rho = S.s_rho;
-    auto &s_gx = S.s_gx;
-    auto &s_gy = S.s_gy;
+    auto &s_g = S.s_g;
     auto &s_mu = S.s_mu;
     V2<T> *hT = reinterpret_cast<V2<T> *>(dsm + L::hT);
     T(*s_h0)[kH0W] = reinterpret_cast<T(*)[kH0W]>(dsm + L::h0);
@@ -680,35 +702,75 @@ __device__ __forceinline__ bool lat_tile_impl(const LatArgs<T> &A, const LatCoef
     //    (s_rho[r][c] = global (x0 - 4 + c, y0 - 3 + r); zero outside a walled
     //    domain, where only zero coefficients meet it); the tile's own
     //    streamed h pairs are kept for the collision
-    for (int q = tid; q < kQW * kQH; q += kNT) {
-        const int ry = q / kQW, rx = q - ry * kQW;
-        const int gy = y0 + ry - 3;
-        T r = T(0);
-        if (rows_in || (gy >= 0 && gy < ny)) {
-            const int k = rows_in ? 0 : lat_kind(walls, gy, ny);
-            const int c = (ry + 1) * PH::W + rx + (PH::XH - 3);
-            const bool own = (unsigned)(rx - 3) < (unsigned)kLTX && (unsigned)(ry - 3) < (unsigned)kLTY;
-            const int o = (ry - 3) * kLTX + (rx - 3);
-            r = s_h0[ry][rx + 1];
-            V2<T> v[4];
-            if (INTERIOR) {
-                // interior tile: the integer-weight operators
-                v[0] = stream_uni<T, PH::W, 0>(hT + 0 * PH::N, c, A.ka, A.kb);
-                v[1] = stream_uni<T, PH::W, 1>(hT + 1 * PH::N, c, A.ka, A.kb);
-                v[2] = stream_uni<T, PH::W, 2>(hT + 2 * PH::N, c, A.ka, A.kb);
-                v[3] = stream_uni<T, PH::W, 3>(hT + 3 * PH::N, c, A.ka, A.kb);
-            } else {
+    // (items over whole 40-slot rows of the windows, so that the lanes of a
+    // warp read consecutive shared-memory words; slots 0 and 39 idle)
+    if (INTERIOR) {
+        // interior tile, integer-weight operators: three rows of one column
+        // per thread (neighbour loads shared), one pass over 5 row groups
+        if (tid < kRW * 5) {
+            const int g = tid / kRW, rw = tid - g * kRW;
+            if (rw >= 1 && rw <= kQW) {
+                const int rx = rw - 1, ry0 = 3 * g;
+                const int c = rx + (PH::XH - 3);
+                // window rows of y - 1 .. y + 3 (row ry sits at window row
+                // ry + 1); the last group's third row is not in the region,
+                // its rows are clamped to the window and its value dropped
+                int rb[5];
+#pragma unroll
+                for (int j = 0; j < 5; ++j) rb[j] = min(ry0 + j, PH::H - 1) * PH::W;
+                T ra[3], rb2[3];
+                auto pair = [&](auto qc) {
+                    constexpr int p = decltype(qc)::value;
+                    V2<T> v[3];
+                    stream_uni3<T, p>(hT + p * PH::N, rb, c, A.ka, A.kb, v);
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        const T t = v[i].x + v[i].y;
+                        if (p == 0) ra[i] = t;
+                        if (p == 1) ra[i] += t;
+                        if (p == 2) rb2[i] = t;
+                        if (p == 3) rb2[i] += t;
+                        const int ry = ry0 + i;
+                        if ((unsigned)(rx - 3) < (unsigned)kLTX && (unsigned)(ry - 3) < (unsigned)kLTY)
+                            s_psi[p][(ry - 3) * kLTX + (rx - 3)] = v[i];
+                    }
+                };
+                pair(IntC<0>{});
+                pair(IntC<1>{});
+                pair(IntC<2>{});
+                pair(IntC<3>{});
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const int ry = ry0 + i;
+                    if (ry < kQH) s_rho[ry][rw] = s_h0[ry][rw] + ra[i] + rb2[i];
+                }
+            }
+        }
+    } else {
+        for (int q = tid; q < kRW * kQH; q += kNT) {
+            const int ry = q / kRW, rw = q - ry * kRW;
+            if (rw < 1 || rw > kQW) continue;
+            const int rx = rw - 1;
+            const int gy = y0 + ry - 3;
+            T r = T(0);
+            if (rows_in || (gy >= 0 && gy < ny)) {
+                const int k = rows_in ? 0 : lat_kind(walls, gy, ny);
+                const int c = (ry + 1) * PH::W + rx + (PH::XH - 3);
+                const bool own = (unsigned)(rx - 3) < (unsigned)kLTX && (unsigned)(ry - 3) < (unsigned)kLTY;
+                const int o = (ry - 3) * kLTX + (rx - 3);
+                V2<T> v[4];
 #pragma unroll
                 for (int p = 0; p < 4; ++p)
                     v[p] = bounce_pair<T>(k, p, stream_pair<T, PH::W>(C, k, p, hT + p * PH::N, c, dt));
-            }
-            r = r + ((v[0].x + v[0].y) + (v[1].x + v[1].y)) + ((v[2].x + v[2].y) + (v[3].x + v[3].y));
-            if (own) {
+                r = s_h0[ry][rx + 1] + ((v[0].x + v[0].y) + (v[1].x + v[1].y)) +
+                    ((v[2].x + v[2].y) + (v[3].x + v[3].y));
+                if (own) {
 #pragma unroll
-                for (int p = 0; p < 4; ++p) s_psi[p][o] = v[p];
+                    for (int p = 0; p < 4; ++p) s_psi[p][o] = v[p];
+                }
             }
+            s_rho[ry][rx + 1] = r;
         }
-        s_rho[ry][rx + 1] = r;
     }
     __syncthreads();
     // the h pair tiles and the rest tile are dead (nothing below reads them):
@@ -723,18 +785,36 @@ __device__ __forceinline__ bool lat_tile_impl(const LatArgs<T> &A, const LatCoef
     }
     const auto &rc = C.r;  // recovery coefficients
     // 2. recovered grad rho on the depth-2 region
-    for (int q = tid; q < kGW * kGH; q += kNT) {
-        const int ly = q / kGW, lx = q - ly * kGW;
-        const int gy = y0 + ly - 2;
-        const int k = (!INTERIOR && walls && (gy == 0 || gy == ny - 1)) ? (gy == 0 ? 1 : 2) : 0;
-        T sx = T(0), sy = T(0);
-        if (INTERIOR) {
-            const int a = ly + 1, b = lx + 2;
-            rec_uni<T>(s_rho[a][b + 1], s_rho[a + 1][b + 1], s_rho[a + 1][b], s_rho[a][b - 1], s_rho[a - 1][b - 1],
-                       s_rho[a - 1][b], sx, sy);
-            sx *= A.al;
-            sy *= A.al;
-        } else {
+    if (INTERIOR) {
+        // three rows of one column per thread (s_rho column lw = lx + 2),
+        // one pass over 4 row groups
+        if (tid < kRW * 4) {
+            const int g = tid / kRW, lw = tid - g * kRW;
+            if (lw >= 2 && lw < kGW + 2) {
+                const int lx = lw - 2, ly0 = 3 * g;
+                // s_rho rows ly0 .. ly0 + 4 (rows a - 1 .. a + 1 of a = ly + 1)
+                T cx[5], cl[4], cr[4];
+#pragma unroll
+                for (int j = 0; j < 5; ++j) cx[j] = s_rho[ly0 + j][lw];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    cl[j] = s_rho[ly0 + j][lw - 1];
+                    cr[j] = s_rho[ly0 + 1 + j][lw + 1];
+                }
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    T sx, sy;
+                    rec_uni<T>(cr[i], cr[i + 1], cx[i + 2], cl[i + 1], cl[i], cx[i], sx, sy);
+                    s_g[ly0 + i][lx] = vset(sx * A.al, sy * A.al);
+                }
+            }
+        }
+    } else {
+        for (int q = tid; q < kGW * kGH; q += kNT) {
+            const int ly = q / kGW, lx = q - ly * kGW;
+            const int gy = y0 + ly - 2;
+            const int k = (walls && (gy == 0 || gy == ny - 1)) ? (gy == 0 ? 1 : 2) : 0;
+            T sx = T(0), sy = T(0);
             const T c0 = s_rho[ly + 1][lx + 2];
 #pragma unroll
             for (int o = 0; o < 6; ++o) {
@@ -742,34 +822,56 @@ __device__ __forceinline__ bool lat_tile_impl(const LatArgs<T> &A, const LatCoef
                 sx += rc[k][o][0] * d;
                 sy += rc[k][o][1] * d;
             }
+            s_g[ly][lx] = vset(sx, sy);
         }
-        s_gx[ly][lx] = sx;
-        s_gy[ly][lx] = sy;
     }
     __syncthreads();
     // 3. lap rho and mu on the depth-1 region
     const Phys<T> &P = A.P;
-    for (int q = tid; q < kMW * kMH; q += kNT) {
-        const int ly = q / kMW, lx = q - ly * kMW;
-        const int gy = y0 + ly - 1;
-        const int k = (!INTERIOR && walls && (gy == 0 || gy == ny - 1)) ? (gy == 0 ? 1 : 2) : 0;
-        T lap = T(0);
-        if (INTERIOR) {
-            const int a = ly + 1, b = lx + 1;
-            const T E0x = s_gx[a][b + 1] - s_gx[a][b - 1], E1x = s_gx[a + 1][b + 1] - s_gx[a - 1][b - 1],
-                    E2x = s_gx[a + 1][b] - s_gx[a - 1][b];
-            const T E0y = s_gy[a][b + 1] - s_gy[a][b - 1], E1y = s_gy[a + 1][b + 1] - s_gy[a - 1][b - 1],
-                    E2y = s_gy[a + 1][b] - s_gy[a - 1][b];
-            lap = A.al * (fma(T(2), E0x, E1x - E2x) + fma(T(2), E2y, E1y - E0y));
-        } else {
-            const T gxc = s_gx[ly + 1][lx + 1], gyc = s_gy[ly + 1][lx + 1];
+    if (INTERIOR) {
+        // three rows of one column per thread (s_g column lw = lx + 1), one
+        // pass over 4 row groups; the last group holds one row of the region
+        // (the others' loads are clamped to the tile, their values dropped)
+        if (tid < kRW * 4) {
+            const int g = tid / kRW, lw = tid - g * kRW;
+            if (lw >= 1 && lw < kMW + 1) {
+                const int lx = lw - 1, ly0 = 3 * g;
+                V2<T> cx[5], cl[4], cr[4];
 #pragma unroll
-            for (int o = 0; o < 6; ++o) {
-                lap += rc[k][o][0] * (s_gx[ly + 1 + lat_dy(o)][lx + 1 + lat_dx(o)] - gxc) +
-                       rc[k][o][1] * (s_gy[ly + 1 + lat_dy(o)][lx + 1 + lat_dx(o)] - gyc);
+                for (int j = 0; j < 5; ++j) cx[j] = s_g[min(ly0 + j, kGH - 1)][lw];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    cl[j] = s_g[min(ly0 + j, kGH - 1)][lw - 1];
+                    cr[j] = s_g[min(ly0 + 1 + j, kGH - 1)][lw + 1];
+                }
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const int ly = ly0 + i;
+                    if (ly < kMH) {
+                        const V2<T> E0 = vsub<T>(cr[i], cl[i + 1]);
+                        const V2<T> E1 = vsub<T>(cr[i + 1], cl[i]);
+                        const V2<T> E2 = vsub<T>(cx[i + 2], cx[i]);
+                        // R_x(d_x rho) + R_y(d_y rho)
+                        const T lap = A.al * (fma(T(2), E0.x, E1.x - E2.x) + fma(T(2), E2.y, E1.y - E0.y));
+                        s_mu[ly][lx] = mu_bulk<T>(P, s_rho[ly + 2][lx + 3]) - P.kappa * lap;
+                    }
+                }
             }
         }
-        s_mu[ly][lx] = mu_bulk<T>(P, s_rho[ly + 2][lx + 3]) - P.kappa * lap;
+    } else {
+        for (int q = tid; q < kMW * kMH; q += kNT) {
+            const int ly = q / kMW, lx = q - ly * kMW;
+            const int gy = y0 + ly - 1;
+            const int k = (walls && (gy == 0 || gy == ny - 1)) ? (gy == 0 ? 1 : 2) : 0;
+            T lap = T(0);
+            const V2<T> gc = s_g[ly + 1][lx + 1];
+#pragma unroll
+            for (int o = 0; o < 6; ++o) {
+                const V2<T> gj = s_g[ly + 1 + lat_dy(o)][lx + 1 + lat_dx(o)];
+                lap += rc[k][o][0] * (gj.x - gc.x) + rc[k][o][1] * (gj.y - gc.y);
+            }
+            s_mu[ly][lx] = mu_bulk<T>(P, s_rho[ly + 2][lx + 3]) - P.kappa * lap;
+        }
     }
     __syncthreads();
     // 4. per node: grad mu, stress force, then the collision.  Threads of a
@@ -795,9 +897,9 @@ __device__ __forceinline__ bool lat_tile_impl(const LatArgs<T> &A, const LatCoef
             Pk[j] = vmul(D, vadd(u, w));
             Qk[j] = fma(u.x, D.y, w.y * D.x);
         };
-        prod(0, vset(s_gx[a2][b2 + 1], s_gy[a2][b2 + 1]), vset(s_gx[a2][b2 - 1], s_gy[a2][b2 - 1]));
-        prod(1, vset(s_gx[a2 + 1][b2 + 1], s_gy[a2 + 1][b2 + 1]), vset(s_gx[a2 - 1][b2 - 1], s_gy[a2 - 1][b2 - 1]));
-        prod(2, vset(s_gx[a2 + 1][b2], s_gy[a2 + 1][b2]), vset(s_gx[a2 - 1][b2], s_gy[a2 - 1][b2]));
+        prod(0, s_g[a2][b2 + 1], s_g[a2][b2 - 1]);
+        prod(1, s_g[a2 + 1][b2 + 1], s_g[a2 - 1][b2 - 1]);
+        prod(2, s_g[a2 + 1][b2], s_g[a2 - 1][b2]);
         const T rxy = fma(T(2), Pk[0].y, Pk[1].y - Pk[2].y), ryq = fma(T(2), Qk[2], Qk[1] - Qk[0]);
         const T ryx = fma(T(2), Pk[2].x, Pk[1].x - Pk[0].x), rxq = fma(T(2), Qk[0], Qk[1] - Qk[2]);
         const T kka = P.kappa * A.al;
@@ -806,15 +908,16 @@ __device__ __forceinline__ bool lat_tile_impl(const LatArgs<T> &A, const LatCoef
     } else {
         T smx = T(0), smy = T(0), skx = T(0), sky = T(0);
         const T mc = s_mu[ly + 1][lx + 1];
-        const T gxc = s_gx[ly + 2][lx + 2], gyc = s_gy[ly + 2][lx + 2];
+        const V2<T> gcv = s_g[ly + 2][lx + 2];
+        const T gxc = gcv.x, gyc = gcv.y;
 #pragma unroll
         for (int o = 0; o < 6; ++o) {
             const T ax = rc[k][o][0], ay = rc[k][o][1];
             const T dm = s_mu[ly + 1 + lat_dy(o)][lx + 1 + lat_dx(o)] - mc;
             smx += ax * dm;
             smy += ay * dm;
-            const T gxj = s_gx[ly + 2 + lat_dy(o)][lx + 2 + lat_dx(o)];
-            const T gyj = s_gy[ly + 2 + lat_dy(o)][lx + 2 + lat_dx(o)];
+            const V2<T> gjv = s_g[ly + 2 + lat_dy(o)][lx + 2 + lat_dx(o)];
+            const T gxj = gjv.x, gyj = gjv.y;
             const T ddx = gxj - gxc, ddy = gyj - gyc;  // product form, see k_mu
             const T dxx = ddx * (gxj + gxc), dxy = gxj * ddy + gyc * ddx, dyy = ddy * (gyj + gyc);
             skx += ax * dyy - ay * dxy;
@@ -826,7 +929,8 @@ __device__ __forceinline__ bool lat_tile_impl(const LatArgs<T> &A, const LatCoef
         ky = P.kappa * sky;
     }
     const T r0 = s_rho[ly + 3][lx + 4];
-    const T drx = s_gx[ly + 2][lx + 2], dry = s_gy[ly + 2][lx + 2];
+    const V2<T> drv = s_g[ly + 2][lx + 2];
+    const T drx = drv.x, dry = drv.y;
     if (TMA) {
         if (!block_mbar_wait(&S.bar[1], pp.ph[1])) return tma_gave_up(A, S, pp);
         pp.ph[1] ^= 1u;
