@@ -460,6 +460,9 @@ constexpr int kRW = kLTX + 8, kRH = kLTY + 6;     // rho: rows from x0 - 4 (colu
 constexpr int kGW = kLTX + 4, kGH = kLTY + 4;     // grad rho: halo 2
 constexpr int kMW = kLTX + 2, kMH = kLTY + 2;     // mu: halo 1
 constexpr int kNT = kLTX * kLTY;
+// row groups of three of the blocked stages on interior tiles (one pass each)
+constexpr int kDG = (kQH + 2) / 3, kGG = (kGH + 2) / 3, kMG = (kMH + 2) / 3;
+static_assert(kRW * kDG <= kNT && kRW * kGG <= kNT && kRW * kMG <= kNT, "one pass per blocked stage");
 
 // Shared memory of one tile: the scalar chain (static) and the population
 // tiles (dynamic, lat_smem bytes).  The streamed g pairs stay in registers.
@@ -537,8 +540,8 @@ __device__ __forceinline__ void lat_node(const LatArgs<T> &A, const LatCoef<T> &
         gq[3] = stream_uni<T, PG::W, 3>(gT + 3 * PG::N, c, A.ka, A.kb);
     } else {
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-        gq[q] = bounce_pair<T>(k, q, stream_pair<T, PG::W>(C, k, q, gT + q * PG::N, c, P.dt));
+        for (int q = 0; q < 4; ++q)
+            gq[q] = bounce_pair<T>(k, q, stream_pair<T, PG::W>(C, k, q, gT + q * PG::N, c, P.dt));
     }
     T sg, mx, my;
     // g_1 = q0.x, g_3 = q0.y, g_2 = q1.x, g_4 = q1.y, g_5 = q2.x, g_7 = q2.y, g_6 = q3.x, g_8 = q3.y
@@ -706,8 +709,8 @@ __device__ __forceinline__ bool lat_tile_impl(const LatArgs<T> &A, const LatCoef
     // warp read consecutive shared-memory words; slots 0 and 39 idle)
     if (INTERIOR) {
         // interior tile, integer-weight operators: three rows of one column
-        // per thread (neighbour loads shared), one pass over 5 row groups
-        if (tid < kRW * 5) {
+        // per thread (neighbour loads shared), one pass over the row groups
+        if (tid < kRW * kDG) {
             const int g = tid / kRW, rw = tid - g * kRW;
             if (rw >= 1 && rw <= kQW) {
                 const int rx = rw - 1, ry0 = 3 * g;
@@ -787,25 +790,28 @@ __device__ __forceinline__ bool lat_tile_impl(const LatArgs<T> &A, const LatCoef
     // 2. recovered grad rho on the depth-2 region
     if (INTERIOR) {
         // three rows of one column per thread (s_rho column lw = lx + 2),
-        // one pass over 4 row groups
-        if (tid < kRW * 4) {
+        // one pass over the row groups (the last group's loads are clamped to
+        // the region, values of rows past it dropped)
+        if (tid < kRW * kGG) {
             const int g = tid / kRW, lw = tid - g * kRW;
             if (lw >= 2 && lw < kGW + 2) {
                 const int lx = lw - 2, ly0 = 3 * g;
                 // s_rho rows ly0 .. ly0 + 4 (rows a - 1 .. a + 1 of a = ly + 1)
                 T cx[5], cl[4], cr[4];
 #pragma unroll
-                for (int j = 0; j < 5; ++j) cx[j] = s_rho[ly0 + j][lw];
+                for (int j = 0; j < 5; ++j) cx[j] = s_rho[min(ly0 + j, kRH - 1)][lw];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    cl[j] = s_rho[ly0 + j][lw - 1];
-                    cr[j] = s_rho[ly0 + 1 + j][lw + 1];
+                    cl[j] = s_rho[min(ly0 + j, kRH - 1)][lw - 1];
+                    cr[j] = s_rho[min(ly0 + 1 + j, kRH - 1)][lw + 1];
                 }
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
-                    T sx, sy;
-                    rec_uni<T>(cr[i], cr[i + 1], cx[i + 2], cl[i + 1], cl[i], cx[i], sx, sy);
-                    s_g[ly0 + i][lx] = vset(sx * A.al, sy * A.al);
+                    if (ly0 + i < kGH) {
+                        T sx, sy;
+                        rec_uni<T>(cr[i], cr[i + 1], cx[i + 2], cl[i + 1], cl[i], cx[i], sx, sy);
+                        s_g[ly0 + i][lx] = vset(sx * A.al, sy * A.al);
+                    }
                 }
             }
         }
@@ -830,9 +836,9 @@ __device__ __forceinline__ bool lat_tile_impl(const LatArgs<T> &A, const LatCoef
     const Phys<T> &P = A.P;
     if (INTERIOR) {
         // three rows of one column per thread (s_g column lw = lx + 1), one
-        // pass over 4 row groups; the last group holds one row of the region
-        // (the others' loads are clamped to the tile, their values dropped)
-        if (tid < kRW * 4) {
+        // pass over the row groups (loads clamped to the region, values of
+        // rows past it dropped)
+        if (tid < kRW * kMG) {
             const int g = tid / kRW, lw = tid - g * kRW;
             if (lw >= 1 && lw < kMW + 1) {
                 const int lx = lw - 1, ly0 = 3 * g;
