@@ -52,6 +52,11 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-all-cores", action="store_true",
+                    help="time the oracle on one thread only")
+    ap.add_argument("--no-fp64", action="store_true",
+                    help="leave out the FP64 rate of the same workload")
+    ap.add_argument("--fp64-steps", type=int, default=500)
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--general", action="store_true",
@@ -249,6 +254,71 @@ def oracle_rate(prob, seconds, max_steps=None):
     return prob.n_nodes * n / el / 1e6, n, el
 
 
+def _oracle_replica(name, seconds, barrier, out):
+    """One single-threaded oracle replica of a workload (a spawned process):
+    build, initialise, wait for the others, then step for about `seconds`."""
+    from oracle import oracle as orc  # noqa: F401  (built by the parent)
+
+    prob = workload(name)
+    o = make_oracle(prob)
+    o.init(prob.rho0, prob.u0, prob.p0)
+    barrier.wait(timeout=600)
+    n, t = 0, time.perf_counter()
+    while True:
+        o.step(1)
+        n += 1
+        el = time.perf_counter() - t
+        if el >= seconds:
+            break
+    out.put((n, el))
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def oracle_rate_all_cores(name, seconds, n_nodes, procs=None):
+    """Aggregate rate of one plain single-threaded oracle replica per host
+    core, each a separate spawned process stepping the same workload at the
+    same time (the oracle itself stays free of threading)."""
+    import multiprocessing as mp
+
+    procs = procs or host_cores()
+    ctx = mp.get_context("spawn")
+    barrier, out = ctx.Barrier(procs), ctx.Queue()
+    env = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in env:
+        os.environ[k] = "1"
+    ps = []
+    try:
+        ps = [ctx.Process(target=_oracle_replica, args=(name, seconds, barrier, out)) for _ in range(procs)]
+        for p in ps:
+            p.start()
+        res, t_end = [], time.monotonic() + 600 + 4 * seconds
+        while len(res) < procs:
+            try:
+                res.append(out.get(timeout=1.0))
+            except Exception:  # noqa: BLE001  (queue.Empty)
+                if any(p.exitcode not in (None, 0) for p in ps) or time.monotonic() > t_end:
+                    raise RuntimeError("an oracle replica failed or did not finish")
+        for p in ps:
+            p.join(timeout=60)
+    finally:
+        for p in ps:
+            if p.is_alive():
+                p.terminate()
+        for k, v in env.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    rate = sum(n_nodes * n / el for n, el in res) / 1e6
+    return rate, procs, sum(n for n, _ in res), max(el for _, el in res)
+
+
 def run_reference(args):
     world, rank, local = dist_env()
     if rank != 0:
@@ -290,7 +360,7 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": config_dict(full, "fp64", args.workload),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                             "nproc": host_cores(), "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -473,6 +543,41 @@ def main():
                     "hbm_gbs": achieved, "hbm_frac": achieved / peak,
                     "kernel_share": dom_ms / max(sum(v[0] for v in prof.values()), 1e-12)}
 
+    # ---- the same workload in FP64 (after the FP32 timed region): its rate
+    # and its roofline against the measured FP64 FMA ceiling
+    fp64 = None
+    if args.precision == "fp32" and not args.no_fp64:
+        p64 = felbm.make_params(precision="fp64", **prob.params)
+        s64 = felbm.State(mesh, p64, prob.rho0, prob.u0, prob.p0)
+        s64.step(args.warmup)
+        s64.sync()
+        s64.profile_enable(True)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        s64.step(args.fp64_steps)
+        f1.record(stream)
+        f1.synchronize()
+        ms64 = f0.elapsed_time(f1)
+        pr64 = s64.profile_read()
+        s64.close()
+        per64 = {k: v for k, v in pr64.items() if v[2] >= args.fp64_steps}
+        k64_ms = sum(v[0] / max(v[1], 1) for v in per64.values())
+        algo64 = ALGO_BYTES_PER_NODE["fp64"] * (19 if dim == 3 else 9) // 9 * prob.n_nodes
+        hbm64 = algo64 / (k64_ms * 1e-3) / 1e9
+        fp64 = {"value": job_rate(1, prob.n_nodes, args.fp64_steps, ms64 * 1e-3), "unit": UNIT,
+                "steps": args.fp64_steps, "ms_per_step": ms64 / args.fp64_steps, "dtype": "f64",
+                "kernel": "+".join(per64), "kernel_ms": k64_ms,
+                "hbm": {"achieved": hbm64, "peak": peak, "unit": "GB/s", "frac": hbm64 / peak}}
+        if dim == 2 and len(per64) == 1:
+            tf = FP64_ALGO_FLOPS_PER_NODE * prob.n_nodes / (k64_ms * 1e-3) / 1e12
+            pk = alu.get("fp64") or FP64_PEAK_TFLOPS
+            fp64["roofline"] = {"bound": "alu", "achieved": tf, "peak": pk, "unit": "TFLOP/s",
+                                "frac": tf / pk,
+                                "peak_source": ("measured FP64 FMA streams (felbm_alu_peak)"
+                                                if alu.get("fp64") else "nominal dense FP64 rate")}
+
     # ---- end to end through the C ABI with host buffers
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -498,8 +603,18 @@ def main():
         else:
             v, nsteps, el = oracle_rate(prob, args.cpu_seconds)
             what = "full %s mesh" % args.workload
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "nproc": host_cores(),
                "sample": "FP64 C oracle (1 thread), %s, %d time steps, %.1f s" % (what, nsteps, el)}
+        if dim == 2 and not args.no_all_cores:
+            try:
+                va, procs, nall, elall = oracle_rate_all_cores(args.workload, args.cpu_seconds, prob.n_nodes)
+                cpu["all_cores"] = {
+                    "value": va, "unit": UNIT, "cores": procs, "kind": "oracle",
+                    "sample": ("one single-threaded FP64 C oracle replica per host core (%d spawned "
+                               "processes) on the full %s mesh, stepping together: %d time steps "
+                               "in all, %.1f s" % (procs, args.workload, nall, elall))}
+            except Exception as e:  # noqa: BLE001
+                cpu["all_cores"] = {"error": "%s: %s" % (type(e).__name__, e)}
     batched = serving = None
     if rank == 0 and world == 1 and not args.skip_batched:
         # the headline line prints even if a secondary measurement fails
@@ -526,7 +641,7 @@ def main():
                 "kernels": {k: {"ms": v[0], "timed": v[1], "launches": v[2]}
                             for k, v in prof.items() if v[2]},
                 "mass": float(mom["totals"][0]), "alu_peaks_tflops": alu,
-                "batched": batched, "serving": serving}
+                "fp64": fp64, "batched": batched, "serving": serving}
         print(json.dumps(line), flush=True)
     st.close()
     mesh.close()

@@ -71,3 +71,17 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
     monkeypatch.setenv("RANK", "1")
     # a non-zero rank returns before building or running the oracle
     assert bench.run_reference(None) is None
+
+
+def test_all_cores_oracle_replicas_aggregate():
+    """The all-cores CPU baseline: one single-threaded oracle replica per
+    core in its own spawned process; the aggregate counts every replica."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from oracle import oracle as orc
+
+    orc.build()
+    rate, procs, steps, seconds = bench.oracle_rate_all_cores("delaunay_droplet_256x256", 0.3, 65536, procs=2)
+    assert procs == 2 and steps >= 2 and seconds >= 0.3
+    assert 0.0 < rate < 65536 * steps / 0.3 / 1e6
+    assert bench.host_cores() >= 1
