@@ -185,6 +185,19 @@ int felbm_step(felbm_state *state, int64_t n_steps);
  * up (that step's tile was not updated). */
 int felbm_state_sync(felbm_state *state);
 
+/* Self-test of the failure detection of the bounded device waits (no GPU
+ * fault involved): enqueues on the state's stream one block that waits, as a
+ * tile waits for its TMA halo loads, on a shared-memory mbarrier that nothing
+ * arrives on, with the time limit limit_ns (1 .. 2e9 nanoseconds) in place of
+ * the step's 2 s.  When the limit runs out the block records the give-up in
+ * the state's device flag exactly as a tile does, then returns, so the
+ * context stays usable.  The next synchronising call on the state
+ * (felbm_state_sync, felbm_moments_get, felbm_state_export) reports
+ * FELBM_ERR_TIMEOUT, and keeps reporting it until felbm_state_import loads
+ * new distributions.  Errors: INVALID_ARG (NULL state, limit out of range),
+ * CUDA (launch failure). */
+int felbm_wait_selftest(felbm_state *state, int64_t limit_ns);
+
 /* Moments of the latest step (or of the initial fields before any step):
  *   rho  n_nodes doubles, C n_nodes doubles ((rho - rho_v)/(rho_l - rho_v)),
  *   u    n_nodes x 2 doubles (x 3 on tetrahedral meshes), p n_nodes doubles,

@@ -350,10 +350,30 @@ bool params_ok(const felbm_params *p) {
            (p->precision == FELBM_FP64 || p->precision == FELBM_FP32) && p->flags == 0;
 }
 
+// One block waits on an mbarrier that nothing arrives on (phase 0 never
+// completes), through the same bounded wait the tiles use for their TMA
+// loads, and records the give-up in the flag as a tile does.
+__global__ void k_wait_selftest(int *flag, uint64_t limit_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    const bool ok = threadIdx.x != 0 || mbar_wait(&bar, 0u, limit_ns);
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(flag, 4);
+}
+
 }  // namespace felbm
 
 // ============================================================================
 extern "C" {
+
+int felbm_wait_selftest(felbm_state *s, int64_t limit_ns) {
+    if (!s || limit_ns < 1 || limit_ns > 2000000000LL) return FELBM_ERR_INVALID_ARG;
+    k_wait_selftest<<<1, 32, 0, s->mesh->stream>>>(s->d_flag, (uint64_t)limit_ns);
+    return cuda_status(cudaGetLastError());
+}
 
 const char *felbm_status_string(int st) {
     switch (st) {

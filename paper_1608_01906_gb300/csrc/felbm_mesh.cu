@@ -107,6 +107,57 @@ std::vector<int32_t> rcm_order(int32_t n, const std::vector<int32_t> &rp,
     return order;
 }
 
+// Conformity of a P1 triangulation (the Galerkin streaming of Sec. 2.2.1
+// assumes a conforming mesh): every edge lies in at most two triangles, an
+// edge of two triangles is traversed in opposite directions by them (both
+// counter-clockwise), an edge of one triangle lies on the boundary of a
+// non-periodic direction (both ends on the lowest or both on the highest
+// coordinate of the nodes in that direction), and, with both directions
+// periodic, the triangles tile the box once (areas sum to the box area).
+static bool conforming(const double *xy, int32_t N, const int32_t *tri, int64_t n_tri, const double Lp[2],
+                       const std::vector<ElemGeom> &geo) {
+    std::vector<uint64_t> ed;  // (low end, high end, direction) per triangle side
+    ed.reserve((size_t)n_tri * 3);
+    for (int64_t t = 0; t < n_tri; ++t)
+        for (int k = 0; k < 3; ++k) {
+            const uint32_t a = (uint32_t)tri[3 * t + k], b = (uint32_t)tri[3 * t + (k + 1) % 3];
+            const uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
+            ed.push_back((lo * (uint64_t)N + hi) << 1 | (a < b ? 0u : 1u));
+        }
+    std::sort(ed.begin(), ed.end());
+    double lo[2] = {xy[0], xy[1]}, hi[2] = {xy[0], xy[1]};
+    for (int32_t i = 1; i < N; ++i)
+        for (int d = 0; d < 2; ++d) {
+            lo[d] = std::min(lo[d], xy[2 * i + d]);
+            hi[d] = std::max(hi[d], xy[2 * i + d]);
+        }
+    auto on_boundary = [&](uint32_t a, uint32_t b) {
+        for (int d = 0; d < 2; ++d) {
+            if (Lp[d] > 0.0) continue;
+            const double tol = 1e-9 * std::max(hi[d] - lo[d], 1.0);
+            if (std::fabs(xy[2 * a + d] - lo[d]) <= tol && std::fabs(xy[2 * b + d] - lo[d]) <= tol) return true;
+            if (std::fabs(xy[2 * a + d] - hi[d]) <= tol && std::fabs(xy[2 * b + d] - hi[d]) <= tol) return true;
+        }
+        return false;
+    };
+    for (size_t k = 0; k < ed.size();) {
+        size_t m = k + 1;
+        while (m < ed.size() && (ed[m] >> 1) == (ed[k] >> 1)) ++m;
+        const uint64_t key = ed[k] >> 1;
+        if (m - k > 2) return false;
+        if (m - k == 2 && (ed[k] & 1u) == (ed[k + 1] & 1u)) return false;
+        if (m - k == 1 && !on_boundary((uint32_t)(key / (uint64_t)N), (uint32_t)(key % (uint64_t)N)))
+            return false;
+        k = m;
+    }
+    if (Lp[0] > 0.0 && Lp[1] > 0.0) {
+        double area = 0.0;
+        for (const ElemGeom &g : geo) area += g.area;
+        if (std::fabs(area - Lp[0] * Lp[1]) > 1e-9 * Lp[0] * Lp[1]) return false;
+    }
+    return true;
+}
+
 int build_csr(const double *xy, int64_t n_nodes, const int32_t *tri, int64_t n_tri,
               const double box[2], uint32_t flags, const uint8_t *tag, HostCSR &out) {
     const int32_t N = (int32_t)n_nodes;
@@ -132,6 +183,7 @@ int build_csr(const double *xy, int64_t n_nodes, const int32_t *tri, int64_t n_t
     }
     for (int32_t i = 0; i < N; ++i)
         if (!(mass[i] > 0.0)) return FELBM_ERR_INVALID_MESH;  // isolated node
+    if (!conforming(xy, N, tri, n_tri, Lp, geo)) return FELBM_ERR_INVALID_MESH;
     // assemble a_ij, b_ij (j != i) as triplets, then merge duplicates
     std::vector<Entry> ent;
     ent.reserve((size_t)n_tri * 6);

@@ -37,7 +37,7 @@ EXPORTED = [
     "felbm_state_import", "felbm_state_destroy", "felbm_status_string",
     "felbm_profile_enable", "felbm_profile_read", "felbm_profile_kind_name",
     "felbm_batch_create", "felbm_batch_step", "felbm_batch_sync", "felbm_batch_info",
-    "felbm_batch_destroy", "felbm_totals_nalloc", "felbm_alu_peak",
+    "felbm_batch_destroy", "felbm_totals_nalloc", "felbm_alu_peak", "felbm_wait_selftest",
 ]
 FELBM_BATCH_AUTOTUNE = 0x1
 FELBM_PROFILE_KINDS = 8
@@ -88,6 +88,8 @@ def load(path: str = LIB_PATH):
     lib.felbm_step.argtypes = [vp, i64]
     lib.felbm_state_sync.restype = C.c_int
     lib.felbm_state_sync.argtypes = [vp]
+    lib.felbm_wait_selftest.restype = C.c_int
+    lib.felbm_wait_selftest.argtypes = [vp, C.c_int64]
     lib.felbm_moments_get.restype = C.c_int
     lib.felbm_moments_get.argtypes = [vp, vp, vp, vp, vp, vp]
     lib.felbm_state_export.restype = C.c_int
@@ -295,6 +297,11 @@ class State:
 
     def sync(self):
         _check(felbm_state_sync(self.handle), "felbm_state_sync")
+
+    def wait_selftest(self, limit_ns):
+        """Enqueue the bounded-wait self-test (an mbarrier nothing arrives
+        on, limit_ns); the next sync then raises the TIMEOUT status."""
+        _check(load().felbm_wait_selftest(self.handle, int(limit_ns)), "felbm_wait_selftest")
 
     def moments(self):
         n, d = self.n, self.mesh.dim

@@ -89,6 +89,42 @@ def test_size_limits_and_null_pointers_need_no_gpu():
                                      C.byref(out)) == felbm.FELBM_ERR_INVALID_ARG
     assert lib.felbm_mesh_create_tet(p(xy), 4, p(tri), 1, p(box), flags, None, None,
                                      None) == felbm.FELBM_ERR_INVALID_ARG
+    assert lib.felbm_wait_selftest(None, 1000) == felbm.FELBM_ERR_INVALID_ARG
     v = C.c_double()
     assert lib.felbm_alu_peak(0, None) == felbm.FELBM_ERR_INVALID_ARG
     assert lib.felbm_alu_peak(-1, C.byref(v)) == felbm.FELBM_ERR_INVALID_ARG
+
+
+def test_triangle_mesh_conformity_needs_no_gpu():
+    """felbm_mesh_create rejects, on the host and before any device work,
+    triangulations that are not conforming (Sec. 2.2.1 streams on a
+    conforming P1 mesh): a hole, a repeated triangle, overlapping triangles
+    with consistent orientation, and a periodic box covered twice.  Meshes
+    that conform get past the check (on a host without a GPU they then stop
+    at the first device allocation)."""
+    import numpy as np
+
+    from paper_1608_01906_gb300 import inputs
+
+    lib = felbm.load()
+
+    def status(xy, tri, box, tag=None):
+        st, h = felbm.felbm_mesh_create(xy, tri, box, felbm.flags_for(box, general=True), tag)
+        if st == 0:
+            lib.felbm_mesh_destroy(h)
+        return st
+
+    bad = felbm.FELBM_ERR_INVALID_MESH
+    xy, tri, box = inputs.jittered_delaunay_mesh(12, 10, seed=5)[:3]
+    assert status(xy, tri, box) != bad
+    assert status(xy, np.delete(tri, 17, axis=0), box) == bad            # hole
+    assert status(xy, np.vstack([tri, tri[3:4]]), box) == bad            # repeated triangle
+    twice = np.vstack([xy, xy])
+    assert status(twice, np.vstack([tri, tri + len(xy)]), box) == bad    # box covered twice
+    sx, stri, sbox, stag = inputs.structured_mesh(8, 6, periodic_y=False)
+    assert status(sx, stri, sbox, stag) != bad                          # walls: boundary edges
+    over = stri.copy()
+    a, b, c = over[0]                                                   # [(0,0),(1,0),(1,1)]
+    over[1] = [a, b, over[1][2]]                                        # [(0,0),(1,0),(0,1)]
+    assert status(sx, over, sbox, stag) == bad                          # overlap, same orientation
+    assert status(sx, np.delete(stri, 1, axis=0), sbox, stag) == bad     # hole next to a wall
