@@ -316,6 +316,67 @@ int felbm_totals_nalloc(const void *rho, const void *ux, const void *uy, const d
  * the call.  Errors: INVALID_ARG (NULL pointer, kind out of range), CUDA. */
 int felbm_alu_peak(int kind, double *flops_per_s);
 
+/* ---- Halo-sharded structured lattices ----------------------------------
+ * A structured lattice (felbm_mesh_create's split lattice) too large for one
+ * device is cut into slabs of whole rows, one per device (the paper's large
+ * single meshes, Sec. 3.4, split spatially).  A node's next state depends on
+ * the present populations up to 4 rows away (h streamed on the depth-3
+ * density region, whose rows are streamed from their depth-1 neighbours;
+ * rho -> grad rho -> lap rho and mu -> grad mu, Sec. 2.2.1 and Sec. 2.3), so
+ * a slab holds its own rows plus 4 halo rows below and above, steps its own
+ * rows, and after every step (and once after felbm_state_init) its halo
+ * rows are replaced by its neighbours' first and last 4 own rows.  The
+ * slabs of a run then reproduce the whole lattice's run bitwise when every
+ * cut (y_begin) is a multiple of 8 rows (the step's tile height: every node
+ * is then updated by the same code path as in the whole lattice).
+ *
+ * felbm_mesh_slab: the slab of rows [y_begin, y_begin + n_rows) of the
+ * whole structured lattice `mesh` (made by felbm_mesh_create; the slab
+ * copies what it needs, so `mesh` may be destroyed after the call), with its
+ * work on cuda_stream.
+ * Its nodes are the n_rows + 8 storage rows in lattice order, row r being
+ * row y_begin - 4 + r of the lattice (modulo its rows when y is periodic;
+ * rows outside a walled lattice are kept but never read): states on it take
+ * and return fields of nx * (n_rows + 8) nodes.  The lumped masses of the
+ * halo rows are zero, so a slab state's totals are its own rows' share.
+ * n_rows >= 8 and the slab inside the lattice; batches refuse slab states.
+ * Errors: INVALID_ARG, UNSUPPORTED (not a structured lattice, or a slab),
+ * OOM, CUDA. */
+int felbm_mesh_slab(const felbm_mesh *mesh, int64_t y_begin, int64_t n_rows, void *cuda_stream,
+                    felbm_mesh **out);
+
+/* The slab's first own row in the lattice, its own row count, and the bytes
+ * of one FP32 halo message (twice that in FP64).  INVALID_ARG if mesh is
+ * not a slab. */
+int felbm_slab_info(const felbm_mesh *mesh, int64_t *y_begin, int64_t *n_rows, int64_t *halo_bytes_fp32);
+
+/* The state's four halo messages (device memory owned by the state, 16-byte
+ * aligned, zeroed at first use): send[0] (its first 4 own rows, for the slab
+ * below), send[1] (its last 4 own rows, for the slab above), recv[0] (for
+ * its 4 halo rows below), recv[1] (above); *bytes per message.  A transport
+ * between devices (NCCL send/recv, peer copies) carries send[1] of slab k to
+ * recv[0] of slab k+1 and send[0] of slab k+1 to recv[1] of slab k, on the
+ * states' streams, between felbm_slab_pack and felbm_slab_unpack.
+ * Layout: per message, 4 rows (pitch = nx rounded up to 4 slots) of h_0, of
+ * the 4 h direction-pair arrays (2 values per slot), of g_0 and of the 4 g
+ * pair arrays: 72 x pitch values of the state's precision. */
+int felbm_slab_halo(felbm_state *state, void **send, void **recv, int64_t *bytes);
+
+/* Enqueue (one launch each, on the state's stream): pack the current
+ * populations' first and last 4 own rows into send[0], send[1]; unpack
+ * recv[0], recv[1] into the 4 halo rows below and above.  INVALID_ARG if the
+ * state is not on a slab. */
+int felbm_slab_pack(felbm_state *state);
+int felbm_slab_unpack(felbm_state *state);
+
+/* The exchange of one device's chain of slab states that together tile the
+ * lattice's rows in order (slabs[0] starting at row 0, all of one
+ * precision and on one stream): pack all, copy each message to its
+ * neighbour (periodic y: around the ends; walled: nothing across the
+ * walls), unpack all.  Asynchronous.  Errors: INVALID_ARG (not such a
+ * chain), CUDA. */
+int felbm_slab_exchange(felbm_state *const *slabs, int32_t n_slabs);
+
 /* Short static description of a status code. */
 const char *felbm_status_string(int status);
 

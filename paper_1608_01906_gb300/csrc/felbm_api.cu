@@ -135,6 +135,8 @@ static DevLattice<T> dev_lattice(const felbm_mesh *m) {
     d.ny = m->sinfo.ny;
     d.walls = m->sinfo.walls ? 1 : 0;
     d.pitch = m->sinfo.pitch;
+    d.row0 = m->sinfo.row0;
+    d.gny = m->sinfo.gny;
     for (int k = 0; k < 3; ++k)
         for (int o = 0; o < 6; ++o) {
             d.c[k][o][0] = (T)m->sinfo.a[k][o][0];
@@ -238,7 +240,7 @@ static void step_lattice(felbm_state *s, LatArgs<T> &A, bool write_mom) {
     A.fout = reinterpret_cast<T *>(s->f[s->cur ^ 1]);
     A.mom = write_mom ? reinterpret_cast<T *>(s->mom) : nullptr;
     A.tmap = s->d_tmap ? s->d_tmap + 3 * s->cur : nullptr;
-    const dim3 grd((A.nx + kLTX - 1) / kLTX, (A.ny + kLTY - 1) / kLTY);
+    const dim3 grd((A.nx + kLTX - 1) / kLTX, (A.yhi - A.ylo + kLTY - 1) / kLTY);
     const int sl = prof_begin(s, 4);
     k_lat_step<T><<<grd, dim3(kLTX, kLTY), lat_smem<T>(), m->stream>>>(A);
     prof_end(s, sl);
@@ -280,6 +282,10 @@ static int do_steps(felbm_state *s, int64_t n) {
         A.ny = m->sinfo.ny;
         A.pitch = m->sinfo.pitch;
         A.walls = m->sinfo.walls ? 1 : 0;
+        A.row0 = m->sinfo.row0;
+        A.gny = m->sinfo.gny;
+        A.ylo = m->sinfo.ylo;
+        A.yhi = m->sinfo.yhi;
         A.c = lat_coef<T>(m, s->params.dt);
         lat_uniform_consts<T>(m->sinfo, s->params.dt, A);
         A.P = phys_of<T>(s->params);
@@ -337,6 +343,7 @@ void state_free(felbm_state *s) {
     cudaFree(s->d_out);
     cudaFree(s->d_flag);
     cudaFree(s->d_tmap);
+    cudaFree(s->halo);
     delete s;
 }
 

@@ -298,6 +298,9 @@ static int setup_meshes(felbm_batch *b) {
         bm.a.ny = m->sinfo.ny;
         bm.a.pitch = m->sinfo.pitch;
         bm.a.walls = m->sinfo.walls ? 1 : 0;
+        bm.a.row0 = 0;  // whole lattices only (slabs are refused)
+        bm.a.gny = bm.a.yhi = m->sinfo.ny;
+        bm.a.ylo = 0;
         bm.a.c = lat_coef_b<T>(m, s->params.dt);
         bm.a.P = phys_b<T>(s->params);
         bm.a.rho = reinterpret_cast<T *>(s->scratch);  // first scratch field
@@ -369,11 +372,12 @@ int felbm_batch_create(felbm_state *const *states, int32_t n_states, uint32_t fl
     }
     for (int32_t k = 0; k < n_states; ++k) {
         felbm_state *s = states[k];
-        if (!s || s->mesh->kind != 1 || (int)s->esize != (int)states[0]->esize ||
+        const bool slab = s && s->mesh->kind == 1 && s->mesh->sinfo.gny != s->mesh->sinfo.ny;
+        if (!s || s->mesh->kind != 1 || slab || (int)s->esize != (int)states[0]->esize ||
             s->mesh->stream != states[0]->mesh->stream || s->mesh->sinfo.nx > 65535 * kLTX ||
             s->mesh->sinfo.ny > 65535 * kLTY) {
             delete b;
-            return (s && s->mesh->kind != 1) ? FELBM_ERR_UNSUPPORTED : FELBM_ERR_INVALID_ARG;
+            return (s && (s->mesh->kind != 1 || slab)) ? FELBM_ERR_UNSUPPORTED : FELBM_ERR_INVALID_ARG;
         }
         for (int32_t q = 0; q < k; ++q)
             if (states[q] == s) {

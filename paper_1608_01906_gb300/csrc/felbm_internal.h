@@ -82,6 +82,11 @@ struct StructuredInfo {
     int32_t pitch = 0;   // population row pitch: nx rounded up to a multiple of 4
     bool walls = false;  // non-periodic y with walls on the first and last row
     double h = 1.0;
+    // A slab of a sharded lattice (felbm_mesh_slab): storage row r is row
+    // r + row0 of the whole lattice of gny rows, the slab's own rows are the
+    // storage rows [ylo, yhi), with 4 halo rows below and above.  A whole
+    // lattice: row0 = ylo = 0, gny = yhi = ny.
+    int32_t row0 = 0, gny = 0, ylo = 0, yhi = 0;
     // 6 neighbour offsets (dx, dy) and their assembled a/b coefficients of an
     // interior node; wall rows get their own sets (bottom, top).
     double a[3][6][2];
@@ -153,16 +158,20 @@ constexpr int lat_dy(int o) { return o == 1 || o == 2 ? 1 : (o == 4 || o == 5 ? 
 template <typename T>
 struct DevLattice {
     int32_t n, nx, ny, walls, pitch;
+    int32_t row0, gny;  // storage row y is row y + row0 of a lattice of gny rows
     T c[3][6][5];  // ax, ay, bxx, bxy, byy
 #ifdef __CUDACC__
     template <typename Fn>
     __device__ __forceinline__ void for_each(int32_t i, Fn &&fn) const {
-        const int32_t y = i / nx, x = i - y * nx;
-        const int kind = walls ? (y == 0 ? 1 : (y == ny - 1 ? 2 : 0)) : 0;
+        const int32_t y = i / nx, x = i - y * nx, gy = y + row0;
+        const int kind = walls ? (gy == 0 ? 1 : (gy == gny - 1 ? 2 : 0)) : 0;
 #pragma unroll
         for (int o = 0; o < 6; ++o) {
             int32_t yy = y + lat_dy(o);
-            if (walls && (yy < 0 || yy >= ny)) continue;
+            if (walls && (yy + row0 < 0 || yy + row0 >= gny)) continue;
+            // (a slab's halo rows at the ends of its storage wrap onto its
+            // own rows: their values feed only halo rows, which the halo
+            // exchange replaces)
             yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
             int32_t xx = x + lat_dx(o);
             xx = xx < 0 ? xx + nx : (xx >= nx ? xx - nx : xx);
@@ -172,8 +181,8 @@ struct DevLattice {
     }
     __device__ __forceinline__ int tag_of(int32_t i) const {
         if (!walls) return 0;
-        const int32_t y = i / nx;
-        return y == 0 ? 2 : (y == ny - 1 ? 4 : 0);
+        const int32_t gy = i / nx + row0;
+        return gy == 0 ? 2 : (gy == gny - 1 ? 4 : 0);
     }
     __device__ __forceinline__ size_t slot(int32_t i) const {
         const int32_t y = i / nx;
@@ -292,6 +301,7 @@ struct felbm_state {
     double *d_out = nullptr;          // 5 N staging in caller order + reduction partials
     int *d_flag = nullptr;            // bit 0: non-finite field, bit 2: bounded wait gave up
     TMap *d_tmap = nullptr;           // structured meshes: 2 buffers x {h pairs, h rest, g pairs}
+    void *halo = nullptr;             // slabs: halo messages send lo, send hi, recv lo, recv hi
     bool have_moments = false;
     int64_t steps_done = 0;
     // profiling: event pairs around launches (felbm_profile_enable)

@@ -53,6 +53,12 @@ template <typename T>
 struct LatArgs {
     int32_t nx, ny, walls;
     int32_t pitch;  // population row pitch (slots), nx rounded up to a multiple of 4
+    // storage row r is row r + row0 of the whole lattice of gny rows (wall
+    // rows and the outside of a walled domain are decided on those rows);
+    // the tiles cover the storage rows [ylo, yhi).  A whole lattice has
+    // row0 = ylo = 0 and gny = yhi = ny; a slab of a sharded lattice keeps
+    // depth-4 halo rows on both sides of its rows.
+    int32_t row0, gny, ylo, yhi;
     LatCoef<T> c;
     Phys<T> P;
     const T *fin;
@@ -212,7 +218,7 @@ struct FillPlan {
 
 template <typename E, int W, int H, bool VEC>
 __device__ __forceinline__ FillPlan fill_plan(int tid, int nthreads, int gx0, int gy0, int nx, int pitch, int ny,
-                                              int walls) {
+                                              int walls, int row0, int gny) {
     constexpr int CE = 16 / (int)sizeof(E);
     constexpr int PER_ROW = VEC ? W / CE : W;
     constexpr int TOTAL = PER_ROW * H;
@@ -232,7 +238,9 @@ __device__ __forceinline__ FillPlan fill_plan(int tid, int nthreads, int gx0, in
             while (gx >= nx) gx -= nx;
             bool inside = true;
             if (walls) {
-                inside = gy >= 0 && gy < ny;
+                // (a storage row past a slab's halo only feeds nodes outside
+                // the slab's rows: zero-filled like the outside)
+                inside = gy + row0 >= 0 && gy + row0 < gny && gy >= 0 && gy < ny;
             } else {
                 while (gy < 0) gy += ny;
                 while (gy >= ny) gy -= ny;
@@ -385,7 +393,8 @@ __device__ __forceinline__ void issue_pair_tiles(const LatArgs<T> &A, int tid, i
     using PT = PairTile<T, D>;
     const E *src = reinterpret_cast<const E *>(A.fin + (G ? 10 : 1) * np);  // pair 0; pair q at + q np
     const FillPlan f =
-        fill_plan<E, PT::W, PT::H, VEC>(tid, kLTX * kLTY, x0 - PT::XH, y0 - D, A.nx, A.pitch, A.ny, A.walls);
+        fill_plan<E, PT::W, PT::H, VEC>(tid, kLTX * kLTY, x0 - PT::XH, y0 - D, A.nx, A.pitch, A.ny, A.walls,
+                                        A.row0, A.gny);
     fill_issue<E, VEC, 4>(f, src, np, tiles, PT::N);
 }
 
@@ -510,9 +519,11 @@ __device__ __forceinline__ bool vec_fills(int x0, int nx) {
 // and h tiles hold no wall row nor a row outside a walled domain, and rows
 // are 16-byte aligned: such tiles run with the row kind fixed at compile
 // time and vector fills only.
-__device__ __forceinline__ bool tile_interior(int x0, int y0, int nx, int ny, int walls, int uni) {
-    const bool yin = walls ? (y0 >= kHD && y0 + kLTY + kHD <= ny) : (y0 + kLTY <= ny);
-    return uni && yin && x0 + kLTX <= nx && vec_fills(x0, nx);
+template <typename T>
+__device__ __forceinline__ bool tile_interior(const LatArgs<T> &A, int x0, int y0) {
+    const int g0 = y0 + A.row0;  // the tile's first row in the whole lattice
+    const bool yin = y0 + kLTY <= A.yhi && (!A.walls || (g0 >= kHD && g0 + kLTY + kHD <= A.gny));
+    return A.uni && yin && x0 + kLTX <= A.nx && vec_fills(x0, A.nx);
 }
 
 // Whether the halo windows of tile (x0, y0) lie inside the mesh without a
@@ -657,7 +668,7 @@ __device__ __forceinline__ bool lat_tile_impl(const LatArgs<T> &A, const LatCoef
     V2<T> *gT = reinterpret_cast<V2<T> *>(dsm + L::gT);
     V2<T>(*s_psi)[kNT] = reinterpret_cast<V2<T>(*)[kNT]>(dsm + L::psi);
     const int nx = A.nx, ny = A.ny, walls = A.walls;
-    const int x0 = bx * kLTX, y0 = by * kLTY;
+    const int x0 = bx * kLTX, y0 = A.ylo + by * kLTY;
     const int tid = threadIdx.y * kLTX + threadIdx.x;
     const size_t n = (size_t)nx * ny, np = pad4((size_t)A.pitch * ny);
     const T dt = A.P.dt;
@@ -671,13 +682,15 @@ __device__ __forceinline__ bool lat_tile_impl(const LatArgs<T> &A, const LatCoef
         }
     } else if (INTERIOR || vec_fills(x0, nx)) {
         issue_pair_tiles<T, 0, kHD, true>(A, tid, x0, y0, hT, np);
-        fill_issue<T, true, 1>(fill_plan<T, kH0W, kH0H, true>(tid, kNT, x0 - 4, y0 - 3, nx, A.pitch, ny, walls),
+        fill_issue<T, true, 1>(fill_plan<T, kH0W, kH0H, true>(tid, kNT, x0 - 4, y0 - 3, nx, A.pitch, ny, walls,
+                                                              A.row0, A.gny),
                                A.fin, 0, &s_h0[0][0], 0);
         cp_async_commit();
         issue_pair_tiles<T, 1, 1, true>(A, tid, x0, y0, gT, np);
     } else {
         issue_pair_tiles<T, 0, kHD, false>(A, tid, x0, y0, hT, np);
-        fill_issue<T, false, 1>(fill_plan<T, kH0W, kH0H, false>(tid, kNT, x0 - 4, y0 - 3, nx, A.pitch, ny, walls),
+        fill_issue<T, false, 1>(fill_plan<T, kH0W, kH0H, false>(tid, kNT, x0 - 4, y0 - 3, nx, A.pitch, ny, walls,
+                                                                A.row0, A.gny),
                                 A.fin, 0, &s_h0[0][0], 0);
         cp_async_commit();
         issue_pair_tiles<T, 1, 1, false>(A, tid, x0, y0, gT, np);
@@ -686,12 +699,13 @@ __device__ __forceinline__ bool lat_tile_impl(const LatArgs<T> &A, const LatCoef
     // the node's g rest population (not moved by streaming): requested now so
     // that its latency overlaps the density stage and the scalar chain
     const int x = x0 + (int)threadIdx.x, y = y0 + (int)threadIdx.y;
-    const bool valid = INTERIOR || (x < nx && y < ny);
+    const bool valid = INTERIOR || (x < nx && y < A.yhi);
     const int32_t i = valid ? x + nx * y : 0;                        // node (moments)
     const size_t ip = valid ? (size_t)x + (size_t)A.pitch * y : 0;  // population slot
     const T g0 = valid ? __ldg(A.fin + 9 * np + ip) : T(0);
     // rows of the rho region (y0 - 3 .. y0 + 10) all of kind 0 and inside
-    const bool rows_in = INTERIOR || !walls || (y0 >= kHD && y0 + kLTY + kHD <= ny);
+    // (decided on the whole lattice's rows: row y0 + row0 of gny)
+    const bool rows_in = INTERIOR || !walls || (y0 + A.row0 >= kHD && y0 + A.row0 + kLTY + kHD <= A.gny);
     if (TMA) {
         if (!block_mbar_wait(&S.bar[0], pp.ph[0])) return tma_gave_up(A, S, pp);
         pp.ph[0] ^= 1u;
@@ -754,10 +768,10 @@ __device__ __forceinline__ bool lat_tile_impl(const LatArgs<T> &A, const LatCoef
             const int ry = q / kRW, rw = q - ry * kRW;
             if (rw < 1 || rw > kQW) continue;
             const int rx = rw - 1;
-            const int gy = y0 + ry - 3;
+            const int gy = y0 + A.row0 + ry - 3;
             T r = T(0);
-            if (rows_in || (gy >= 0 && gy < ny)) {
-                const int k = rows_in ? 0 : lat_kind(walls, gy, ny);
+            if (rows_in || (gy >= 0 && gy < A.gny && y0 + ry - 3 >= 0 && y0 + ry - 3 < ny)) {
+                const int k = rows_in ? 0 : lat_kind(walls, gy, A.gny);
                 const int c = (ry + 1) * PH::W + rx + (PH::XH - 3);
                 const bool own = (unsigned)(rx - 3) < (unsigned)kLTX && (unsigned)(ry - 3) < (unsigned)kLTY;
                 const int o = (ry - 3) * kLTX + (rx - 3);
@@ -818,8 +832,8 @@ __device__ __forceinline__ bool lat_tile_impl(const LatArgs<T> &A, const LatCoef
     } else {
         for (int q = tid; q < kGW * kGH; q += kNT) {
             const int ly = q / kGW, lx = q - ly * kGW;
-            const int gy = y0 + ly - 2;
-            const int k = (walls && (gy == 0 || gy == ny - 1)) ? (gy == 0 ? 1 : 2) : 0;
+            const int gy = y0 + A.row0 + ly - 2;
+            const int k = (walls && (gy == 0 || gy == A.gny - 1)) ? (gy == 0 ? 1 : 2) : 0;
             T sx = T(0), sy = T(0);
             const T c0 = s_rho[ly + 1][lx + 2];
 #pragma unroll
@@ -867,8 +881,8 @@ __device__ __forceinline__ bool lat_tile_impl(const LatArgs<T> &A, const LatCoef
     } else {
         for (int q = tid; q < kMW * kMH; q += kNT) {
             const int ly = q / kMW, lx = q - ly * kMW;
-            const int gy = y0 + ly - 1;
-            const int k = (walls && (gy == 0 || gy == ny - 1)) ? (gy == 0 ? 1 : 2) : 0;
+            const int gy = y0 + A.row0 + ly - 1;
+            const int k = (walls && (gy == 0 || gy == A.gny - 1)) ? (gy == 0 ? 1 : 2) : 0;
             T lap = T(0);
             const V2<T> gc = s_g[ly + 1][lx + 1];
 #pragma unroll
@@ -883,7 +897,7 @@ __device__ __forceinline__ bool lat_tile_impl(const LatArgs<T> &A, const LatCoef
     // 4. per node: grad mu, stress force, then the collision.  Threads of a
     //    ragged tile outside the mesh take part in every barrier.
     const int lx = threadIdx.x, ly = threadIdx.y;
-    const int k = (rows_in || !valid) ? 0 : lat_kind(walls, y, ny);
+    const int k = (rows_in || !valid) ? 0 : lat_kind(walls, y + A.row0, A.gny);
     T dmx, dmy, kx, ky;
     if (INTERIOR) {
         const int a = ly + 1, b = lx + 1, a2 = ly + 2, b2 = lx + 2;
@@ -964,8 +978,8 @@ __device__ __forceinline__ void lat_block_init(StepSmem<T> &S) {
 // Whether tile (bx, by) loads its halo windows by TMA.
 template <typename T>
 __device__ __forceinline__ bool tile_tma(const LatArgs<T> &A, int bx, int by, const unsigned char *dsm) {
-    const int x0 = bx * kLTX, y0 = by * kLTY;
-    return A.tmap && tile_interior(x0, y0, A.nx, A.ny, A.walls, A.uni) && tile_unwrapped(x0, y0, A.nx, A.ny) &&
+    const int x0 = bx * kLTX, y0 = A.ylo + by * kLTY;
+    return A.tmap && tile_interior(A, x0, y0) && tile_unwrapped(x0, y0, A.nx, A.ny) &&
            (smem_u32(dsm) & 127u) == 0;
 }
 
@@ -976,7 +990,7 @@ template <typename T>
 __device__ __forceinline__ bool lat_tile(const LatArgs<T> &A, const LatCoef<T> &C, int bx, int by, StepSmem<T> &S,
                                          unsigned char *dsm, TilePipe &pp, const NextTile &next) {
     if (tile_tma(A, bx, by, dsm)) return lat_tile_impl<T, true, true>(A, C, bx, by, S, dsm, pp, next);
-    if (tile_interior(bx * kLTX, by * kLTY, A.nx, A.ny, A.walls, A.uni))
+    if (tile_interior(A, bx * kLTX, A.ylo + by * kLTY))
         return lat_tile_impl<T, true, false>(A, C, bx, by, S, dsm, pp, next);
     return lat_tile_impl<T, false, false>(A, C, bx, by, S, dsm, pp, next);
 }

@@ -386,6 +386,8 @@ void detect_structured(const double *xy, int64_t n_nodes, const int32_t *tri, in
     info.ny = (int32_t)ny;
     info.walls = walls;
     info.h = h;
+    info.row0 = info.ylo = 0;
+    info.gny = info.yhi = (int32_t)ny;
     info.ok = true;
 }
 

@@ -38,6 +38,8 @@ EXPORTED = [
     "felbm_profile_enable", "felbm_profile_read", "felbm_profile_kind_name",
     "felbm_batch_create", "felbm_batch_step", "felbm_batch_sync", "felbm_batch_info",
     "felbm_batch_destroy", "felbm_totals_nalloc", "felbm_alu_peak", "felbm_wait_selftest",
+    "felbm_mesh_slab", "felbm_slab_info", "felbm_slab_halo", "felbm_slab_pack", "felbm_slab_unpack",
+    "felbm_slab_exchange",
 ]
 FELBM_BATCH_AUTOTUNE = 0x1
 FELBM_PROFILE_KINDS = 8
@@ -131,6 +133,18 @@ def _declare_extra(lib):
         lib.felbm_totals_nalloc.argtypes = [vp, vp, vp, vp, i64, i32, vp, vp]
     lib.felbm_alu_peak.restype = C.c_int
     lib.felbm_alu_peak.argtypes = [C.c_int, vp]
+    lib.felbm_mesh_slab.restype = C.c_int
+    lib.felbm_mesh_slab.argtypes = [vp, i64, i64, vp, pp]
+    lib.felbm_slab_info.restype = C.c_int
+    lib.felbm_slab_info.argtypes = [vp, vp, vp, vp]
+    lib.felbm_slab_halo.restype = C.c_int
+    lib.felbm_slab_halo.argtypes = [vp, pp, pp, vp]
+    lib.felbm_slab_pack.restype = C.c_int
+    lib.felbm_slab_pack.argtypes = [vp]
+    lib.felbm_slab_unpack.restype = C.c_int
+    lib.felbm_slab_unpack.argtypes = [vp]
+    lib.felbm_slab_exchange.restype = C.c_int
+    lib.felbm_slab_exchange.argtypes = [C.POINTER(C.c_void_p), i32]
 
 
 def _p(a):
@@ -255,6 +269,24 @@ class Mesh:
         self.q = 19 if self.dim == 3 else 9
         self.handle = h
 
+    @classmethod
+    def slab(cls, mesh, y_begin, n_rows, stream=None):
+        """Slab of rows [y_begin, y_begin + n_rows) of a structured lattice
+        mesh, with 4 halo rows on both sides (felbm_mesh_slab)."""
+        out = C.c_void_p()
+        _check(load().felbm_mesh_slab(mesh.handle, int(y_begin), int(n_rows),
+                                      C.c_void_p(stream) if stream else None, C.byref(out)),
+               "felbm_mesh_slab")
+        self = cls.__new__(cls)
+        self.handle, self.dim, self.q = out, 2, 9
+        self.n_nodes = self.info()["n_nodes"]
+        return self
+
+    def slab_info(self):
+        y0, rows, b = C.c_int64(), C.c_int64(), C.c_int64()
+        _check(load().felbm_slab_info(self.handle, C.byref(y0), C.byref(rows), C.byref(b)), "felbm_slab_info")
+        return {"y_begin": y0.value, "n_rows": rows.value, "halo_bytes_fp32": b.value}
+
     def info(self):
         n, t, k, b = C.c_int64(), C.c_int64(), C.c_int32(), C.c_int64()
         _check(load().felbm_mesh_info(self.handle, C.byref(n), C.byref(t), C.byref(k),
@@ -297,6 +329,19 @@ class State:
 
     def sync(self):
         _check(felbm_state_sync(self.handle), "felbm_state_sync")
+
+    def halo(self):
+        """Device addresses of the slab's halo messages: ([send lo, send hi],
+        [recv lo, recv hi], bytes per message)."""
+        send, recv, b = (C.c_void_p * 2)(), (C.c_void_p * 2)(), C.c_int64()
+        _check(load().felbm_slab_halo(self.handle, send, recv, C.byref(b)), "felbm_slab_halo")
+        return [send[0], send[1]], [recv[0], recv[1]], b.value
+
+    def pack(self):
+        _check(load().felbm_slab_pack(self.handle), "felbm_slab_pack")
+
+    def unpack(self):
+        _check(load().felbm_slab_unpack(self.handle), "felbm_slab_unpack")
 
     def wait_selftest(self, limit_ns):
         """Enqueue the bounded-wait self-test (an mbarrier nothing arrives
@@ -346,6 +391,13 @@ class State:
             self.close()
         except Exception:
             pass
+
+
+def slab_exchange(states):
+    """Halo exchange of one device's chain of slab states (felbm_slab_exchange)."""
+    arr = (C.c_void_p * len(states))(*[s.handle.value if isinstance(s.handle, C.c_void_p) else s.handle
+                                       for s in states])
+    _check(load().felbm_slab_exchange(arr, len(states)), "felbm_slab_exchange")
 
 
 class Batch:
