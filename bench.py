@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true",
                     help="leave out the FP64 rate of the same workload")
     ap.add_argument("--fp64-steps", type=int, default=500)
+    ap.add_argument("--shards", type=int, default=2,
+                    help="slabs of the halo-sharded run of the same lattice on this GPU (<= 1: none)")
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
     ap.add_argument("--general", action="store_true",
@@ -578,6 +580,37 @@ def main():
                                 "peak_source": ("measured FP64 FMA streams (felbm_alu_peak)"
                                                 if alu.get("fp64") else "nominal dense FP64 rate")}
 
+    # ---- the same lattice cut into halo-sharded slabs on this device: each
+    # step is every slab's step plus the halo exchange (pack, copies, unpack)
+    sharded = None
+    if kind == 1 and dim == 2 and args.shards > 1:
+        from paper_1608_01906_gb300 import sharding
+
+        try:
+            nx = int(round(prob.box[0])) if prob.box[0] > 0 else int(np.max(prob.xy[:, 0])) + 1
+            ny = prob.n_nodes // nx
+            run = sharding.SlabRun(prob.xy, prob.tri, prob.box, prob.tag, nx, ny, params, prob.rho0, prob.u0,
+                                   prob.p0, n_slabs=args.shards, stream=stream.cuda_stream)
+            run.step(args.warmup)
+            torch.cuda.synchronize()
+            k_sh = min(args.steps, 1000)
+            g0 = torch.cuda.Event(enable_timing=True)
+            g1 = torch.cuda.Event(enable_timing=True)
+            g0.record(stream)
+            run.step(k_sh)
+            g1.record(stream)
+            g1.synchronize()
+            ms_sh = g0.elapsed_time(g1)
+            msg = run.states[0].halo()[2]
+            sharded = {"slabs": [list(r) for r in run.rows], "value": job_rate(1, prob.n_nodes, k_sh, ms_sh * 1e-3),
+                       "unit": UNIT, "steps": k_sh, "ms_per_step": ms_sh / k_sh,
+                       "halo_bytes_per_step": 2 * len(run.rows) * msg,
+                       "note": ("slabs of the same lattice on one GPU, stepped one after another, halo exchange "
+                                "after every step; bitwise equal to the whole-lattice run")}
+            run.close()
+        except Exception as e:  # noqa: BLE001
+            sharded = {"error": "%s: %s" % (type(e).__name__, e)}
+
     # ---- end to end through the C ABI with host buffers
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -641,7 +674,7 @@ def main():
                 "kernels": {k: {"ms": v[0], "timed": v[1], "launches": v[2]}
                             for k, v in prof.items() if v[2]},
                 "mass": float(mom["totals"][0]), "alu_peaks_tflops": alu,
-                "fp64": fp64, "batched": batched, "serving": serving}
+                "fp64": fp64, "sharded": sharded, "batched": batched, "serving": serving}
         print(json.dumps(line), flush=True)
     st.close()
     mesh.close()

@@ -87,8 +87,17 @@ typedef struct felbm_params {
     double dt;
     double gravity[3];
     int32_t precision; /* FELBM_FP64 or FELBM_FP32 */
-    int32_t flags;     /* must be 0 */
+    int32_t flags;     /* 0, or FELBM_PARAM_LAP_FP64 */
 } felbm_params;
+
+/* felbm_params.flags: FP32 states on triangle meshes form the kappa lap rho
+ * term of mu (Sec. 2.1, Eq. F) in FP64: the Laplacian of rho (recovery of
+ * the recovered FP32 gradient, with the mesh's FP64 coefficients) and its
+ * product with kappa in FP64, subtracted from the FP32 bulk term in FP64 and
+ * rounded once (for large density ratios, where kappa is large).
+ * Everything else stays FP32.  No effect on FP64 states.  Tetrahedral
+ * meshes and batches refuse it (UNSUPPORTED). */
+#define FELBM_PARAM_LAP_FP64 0x1
 
 /* Create a device-resident mesh (Sec. 2.2.1 P1 elements, Sec. 2.3 recovery).
  *   xy        host, n_nodes x 2 doubles (x, y), node coordinates.

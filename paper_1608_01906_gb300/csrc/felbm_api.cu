@@ -154,6 +154,18 @@ static DevLattice<T> dev_lattice(const felbm_mesh *m) {
 // ran 3-7% slower than 256.
 constexpr int kGenBlock = 256;
 
+// kappa in FP64 (the FP64 kappa lap rho term of FELBM_PARAM_LAP_FP64)
+static double kappa64(const felbm_params &p) {
+    const double d = p.rho_l - p.rho_v;
+    return 1.5 * p.xi * p.sigma / (d * d);
+}
+
+static bool lap_fp64(const felbm_state *s) { return s->esize == 4 && (s->params.flags & FELBM_PARAM_LAP_FP64); }
+
+// The mesh's operators with FP64 coefficients, for the FP64 Laplacian.
+static DevCSR<double> topo64(const felbm_mesh *m, const DevCSR<float> &) { return dev_csr<double>(m); }
+static DevLattice<double> topo64(const felbm_mesh *m, const DevLattice<float> &) { return dev_lattice<double>(m); }
+
 template <typename T, typename Topo>
 static void launch_chain(felbm_state *s, const Topo &d) {
     const felbm_mesh *m = s->mesh;
@@ -164,7 +176,16 @@ static void launch_chain(felbm_state *s, const Topo &d) {
     k_grad<T, Topo><<<g, kGenBlock, 0, m->stream>>>(d, F);
     prof_end(s, sl);
     sl = prof_begin(s, 2);
-    k_mu<T, Topo><<<g, kGenBlock, 0, m->stream>>>(d, F, P);
+    if constexpr (sizeof(T) == 4) {
+        if (lap_fp64(s)) {
+            const auto d64 = topo64(m, d);
+            k_mu_lap64<decltype(d64)><<<g, kGenBlock, 0, m->stream>>>(d64, F, P, kappa64(s->params));
+        } else {
+            k_mu<T, Topo><<<g, kGenBlock, 0, m->stream>>>(d, F, P);
+        }
+    } else {
+        k_mu<T, Topo><<<g, kGenBlock, 0, m->stream>>>(d, F, P);
+    }
     prof_end(s, sl);
 }
 
@@ -233,7 +254,7 @@ static LatCoef<T> lat_coef(const felbm_mesh *m, double dt) {
     return c;
 }
 
-template <typename T>
+template <typename T, bool LAP64>
 static void step_lattice(felbm_state *s, LatArgs<T> &A, bool write_mom) {
     const felbm_mesh *m = s->mesh;
     A.fin = reinterpret_cast<const T *>(s->f[s->cur]);
@@ -242,7 +263,7 @@ static void step_lattice(felbm_state *s, LatArgs<T> &A, bool write_mom) {
     A.tmap = s->d_tmap ? s->d_tmap + 3 * s->cur : nullptr;
     const dim3 grd((A.nx + kLTX - 1) / kLTX, (A.yhi - A.ylo + kLTY - 1) / kLTY);
     const int sl = prof_begin(s, 4);
-    k_lat_step<T><<<grd, dim3(kLTX, kLTY), lat_smem<T>(), m->stream>>>(A);
+    k_lat_step<T, LAP64><<<grd, dim3(kLTX, kLTY), lat_smem<T>(), m->stream>>>(A);
     prof_end(s, sl);
     s->cur ^= 1;
 }
@@ -251,7 +272,7 @@ static void step_lattice(felbm_state *s, LatArgs<T> &A, bool write_mom) {
 // the function attribute once per device (bit d of done, set only once the
 // call succeeded; devices from 64 on set it at every call).  A refusal is
 // returned to the caller of felbm_step.
-template <typename T>
+template <typename T, bool LAP64>
 static cudaError_t lat_smem_attr() {
     static std::atomic<uint64_t> done{0};
     int dev = -1;
@@ -262,7 +283,7 @@ static cudaError_t lat_smem_attr() {
     const uint64_t bit = (dev >= 0 && dev < 64) ? (uint64_t(1) << dev) : 0;
     if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
     const cudaError_t e =
-        cudaFuncSetAttribute(k_lat_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lat_smem<T>());
+        cudaFuncSetAttribute(k_lat_step<T, LAP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lat_smem<T>());
     if (e != cudaSuccess) {
         cudaGetLastError();
         return e;
@@ -275,7 +296,12 @@ template <typename T>
 static int do_steps(felbm_state *s, int64_t n) {
     const felbm_mesh *m = s->mesh;
     if (m->kind == 1) {
-        const cudaError_t ea = lat_smem_attr<T>();
+        const bool l64 = lap_fp64(s);
+        cudaError_t ea;
+        if constexpr (sizeof(T) == 4)
+            ea = l64 ? lat_smem_attr<T, true>() : lat_smem_attr<T, false>();
+        else
+            ea = lat_smem_attr<T, false>();
         if (ea != cudaSuccess) return cuda_status(ea);
         LatArgs<T> A;
         A.nx = m->sinfo.nx;
@@ -291,7 +317,20 @@ static int do_steps(felbm_state *s, int64_t n) {
         A.P = phys_of<T>(s->params);
         A.rho = fields_of<T>(s).rho;
         A.flag = s->d_flag;
-        for (int64_t k = 0; k < n; ++k) step_lattice<T>(s, A, k == n - 1);
+        A.al64 = 1.0 / (6.0 * m->sinfo.h);
+        A.kappa64 = kappa64(s->params);
+        for (int k = 0; k < 3; ++k)
+            for (int o = 0; o < 6; ++o)
+                for (int c = 0; c < 2; ++c) A.r64[k][o][c] = m->sinfo.a[k][o][c];
+        for (int64_t k = 0; k < n; ++k) {
+            if constexpr (sizeof(T) == 4) {
+                if (l64) {
+                    step_lattice<T, true>(s, A, k == n - 1);
+                    continue;
+                }
+            }
+            step_lattice<T, false>(s, A, k == n - 1);
+        }
     } else {
         const DevCSR<T> d = dev_csr<T>(m);
         for (int64_t k = 0; k < n; ++k) step_topo<T>(s, d, k == n - 1);
@@ -354,7 +393,7 @@ bool params_ok(const felbm_params *p) {
         if (!std::isfinite(x)) return false;
     return p->rho_l > p->rho_v && p->rho_v > 0.0 && p->sigma >= 0.0 && p->xi > 0.0 &&
            p->tau_l > 0.0 && p->tau_v > 0.0 && p->dt > 0.0 &&
-           (p->precision == FELBM_FP64 || p->precision == FELBM_FP32) && p->flags == 0;
+           (p->precision == FELBM_FP64 || p->precision == FELBM_FP32) && (p->flags & ~FELBM_PARAM_LAP_FP64) == 0;
 }
 
 // One block waits on an mbarrier that nothing arrives on (phase 0 never

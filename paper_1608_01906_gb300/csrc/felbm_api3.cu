@@ -174,6 +174,7 @@ void steps3(felbm_state *s, int64_t n) {
 
 int state_init3(const felbm_mesh *mesh, const felbm_params *params, const double *rho0,
                 const double *u0, const double *p0, felbm_state **out) {
+    if (params->flags & FELBM_PARAM_LAP_FP64) return FELBM_ERR_UNSUPPORTED;
     const size_t N = (size_t)mesh->n_nodes;
     for (size_t i = 0; i < N; ++i)
         if (!(rho0[i] > 0.0) || !std::isfinite(rho0[i])) return FELBM_ERR_INVALID_ARG;

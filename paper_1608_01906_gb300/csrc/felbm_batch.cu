@@ -372,7 +372,8 @@ int felbm_batch_create(felbm_state *const *states, int32_t n_states, uint32_t fl
     }
     for (int32_t k = 0; k < n_states; ++k) {
         felbm_state *s = states[k];
-        const bool slab = s && s->mesh->kind == 1 && s->mesh->sinfo.gny != s->mesh->sinfo.ny;
+        const bool slab = s && s->mesh->kind == 1 && (s->mesh->sinfo.gny != s->mesh->sinfo.ny ||
+                                                      (s->params.flags & FELBM_PARAM_LAP_FP64));
         if (!s || s->mesh->kind != 1 || slab || (int)s->esize != (int)states[0]->esize ||
             s->mesh->stream != states[0]->mesh->stream || s->mesh->sinfo.nx > 65535 * kLTX ||
             s->mesh->sinfo.ny > 65535 * kLTY) {

@@ -259,6 +259,32 @@ __global__ void __launch_bounds__(256) k_mu(Topo m, Fields<T> F, Phys<T> P) {
     F.ky[i] = P.kappa * ky;
 }
 
+// k_mu for FP32 fields with the kappa lap rho term of mu in FP64
+// (FELBM_PARAM_LAP_FP64): Topo64 carries the mesh's FP64 coefficients; the
+// Laplacian of the FP32 gradient and its product with kappa are formed in
+// FP64 and subtracted from the bulk term in FP64, rounded once.  K is formed
+// as in k_mu, from the same coefficients rounded to FP32.
+template <typename Topo64>
+__global__ void __launch_bounds__(256) k_mu_lap64(Topo64 m, Fields<float> F, Phys<float> P, double kappa) {
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m.n) return;
+    const float gxi = F.drx[i], gyi = F.dry[i];
+    double lap = 0.0;
+    float kx = 0.f, ky = 0.f;
+    m.for_each(i, [&](int32_t j, double ax, double ay, double, double, double) {
+        const float gxj = __ldg(F.drx + j), gyj = __ldg(F.dry + j);
+        lap += ax * ((double)gxj - (double)gxi) + ay * ((double)gyj - (double)gyi);
+        const float fax = (float)ax, fay = (float)ay;
+        const float ddx = gxj - gxi, ddy = gyj - gyi;
+        const float dxx = ddx * (gxj + gxi), dxy = gxj * ddy + gyi * ddx, dyy = ddy * (gyj + gyi);
+        kx += fax * dyy - fay * dxy;
+        ky += fay * dxx - fax * dxy;
+    });
+    F.mu[i] = (float)((double)mu_bulk<float>(P, F.rho[i]) - kappa * lap);
+    F.kx[i] = P.kappa * kx;
+    F.ky[i] = P.kappa * ky;
+}
+
 // Local collision of one node (Sec. 2.2), split in two so that callers can
 // keep the streamed populations outside registers:
 //   collide_prep  moments (Eqs. velocity, pressure), tau, and the per-node

@@ -73,6 +73,10 @@ struct LatArgs {
     T al;        // 1 / (6 h)
     V2<T> ka;    // (-dt/(6h), dt/(6h)): odd part of the streaming weights
     V2<T> kb;    // (dt^2/(2h^2), dt^2/(2h^2)): even part
+    // FP64 kappa lap rho term of mu (FELBM_PARAM_LAP_FP64; read only by the
+    // kernel built for it): 1/(6h), kappa and the recovery coefficients
+    double al64, kappa64;
+    double r64[3][6][2];
 };
 
 // ---- interior operators of the structured split --------------------------
@@ -654,7 +658,7 @@ __device__ __noinline__ bool tma_gave_up(const LatArgs<T> &A, StepSmem<T> &S, co
 // can be, so that interior tiles read them as constant operands).  Returns
 // false (all threads alike) when a bounded wait for a TMA load gave up; the
 // flag then carries bit 2.
-template <typename T, bool INTERIOR, bool TMA>
+template <typename T, bool INTERIOR, bool TMA, bool LAP64>
 __device__ __forceinline__ bool lat_tile_impl(const LatArgs<T> &A, const LatCoef<T> &C, int bx, int by,
                                               StepSmem<T> &S, unsigned char *dsm, TilePipe &pp,
                                               const NextTile &next) {
@@ -872,8 +876,21 @@ __device__ __forceinline__ bool lat_tile_impl(const LatArgs<T> &A, const LatCoef
                         const V2<T> E1 = vsub<T>(cr[i + 1], cl[i]);
                         const V2<T> E2 = vsub<T>(cx[i + 2], cx[i]);
                         // R_x(d_x rho) + R_y(d_y rho)
-                        const T lap = A.al * (fma(T(2), E0.x, E1.x - E2.x) + fma(T(2), E2.y, E1.y - E0.y));
-                        s_mu[ly][lx] = mu_bulk<T>(P, s_rho[ly + 2][lx + 3]) - P.kappa * lap;
+                        if (LAP64) {
+                            // the same differences and weights in FP64
+                            const double e0x = (double)cr[i].x - (double)cl[i + 1].x;
+                            const double e0y = (double)cr[i].y - (double)cl[i + 1].y;
+                            const double e1x = (double)cr[i + 1].x - (double)cl[i].x;
+                            const double e1y = (double)cr[i + 1].y - (double)cl[i].y;
+                            const double e2x = (double)cx[i + 2].x - (double)cx[i].x;
+                            const double e2y = (double)cx[i + 2].y - (double)cx[i].y;
+                            const double lap = A.al64 * (fma(2.0, e0x, e1x - e2x) + fma(2.0, e2y, e1y - e0y));
+                            s_mu[ly][lx] =
+                                (T)((double)mu_bulk<T>(P, s_rho[ly + 2][lx + 3]) - A.kappa64 * lap);
+                        } else {
+                            const T lap = A.al * (fma(T(2), E0.x, E1.x - E2.x) + fma(T(2), E2.y, E1.y - E0.y));
+                            s_mu[ly][lx] = mu_bulk<T>(P, s_rho[ly + 2][lx + 3]) - P.kappa * lap;
+                        }
                     }
                 }
             }
@@ -883,14 +900,25 @@ __device__ __forceinline__ bool lat_tile_impl(const LatArgs<T> &A, const LatCoef
             const int ly = q / kMW, lx = q - ly * kMW;
             const int gy = y0 + A.row0 + ly - 1;
             const int k = (walls && (gy == 0 || gy == A.gny - 1)) ? (gy == 0 ? 1 : 2) : 0;
-            T lap = T(0);
             const V2<T> gc = s_g[ly + 1][lx + 1];
+            if (LAP64) {
+                double lap = 0.0;
 #pragma unroll
-            for (int o = 0; o < 6; ++o) {
-                const V2<T> gj = s_g[ly + 1 + lat_dy(o)][lx + 1 + lat_dx(o)];
-                lap += rc[k][o][0] * (gj.x - gc.x) + rc[k][o][1] * (gj.y - gc.y);
+                for (int o = 0; o < 6; ++o) {
+                    const V2<T> gj = s_g[ly + 1 + lat_dy(o)][lx + 1 + lat_dx(o)];
+                    lap += A.r64[k][o][0] * ((double)gj.x - (double)gc.x) +
+                           A.r64[k][o][1] * ((double)gj.y - (double)gc.y);
+                }
+                s_mu[ly][lx] = (T)((double)mu_bulk<T>(P, s_rho[ly + 2][lx + 3]) - A.kappa64 * lap);
+            } else {
+                T lap = T(0);
+#pragma unroll
+                for (int o = 0; o < 6; ++o) {
+                    const V2<T> gj = s_g[ly + 1 + lat_dy(o)][lx + 1 + lat_dx(o)];
+                    lap += rc[k][o][0] * (gj.x - gc.x) + rc[k][o][1] * (gj.y - gc.y);
+                }
+                s_mu[ly][lx] = mu_bulk<T>(P, s_rho[ly + 2][lx + 3]) - P.kappa * lap;
             }
-            s_mu[ly][lx] = mu_bulk<T>(P, s_rho[ly + 2][lx + 3]) - P.kappa * lap;
         }
     }
     __syncthreads();
@@ -986,13 +1014,13 @@ __device__ __forceinline__ bool tile_tma(const LatArgs<T> &A, int bx, int by, co
 // One tile of a block's walk (pp carries the TMA barrier phases and whether
 // this tile's h group was already requested; next is the block's next tile).
 // False when a bounded wait gave up.
-template <typename T>
+template <typename T, bool LAP64 = false>
 __device__ __forceinline__ bool lat_tile(const LatArgs<T> &A, const LatCoef<T> &C, int bx, int by, StepSmem<T> &S,
                                          unsigned char *dsm, TilePipe &pp, const NextTile &next) {
-    if (tile_tma(A, bx, by, dsm)) return lat_tile_impl<T, true, true>(A, C, bx, by, S, dsm, pp, next);
+    if (tile_tma(A, bx, by, dsm)) return lat_tile_impl<T, true, true, LAP64>(A, C, bx, by, S, dsm, pp, next);
     if (tile_interior(A, bx * kLTX, A.ylo + by * kLTY))
-        return lat_tile_impl<T, true, false>(A, C, bx, by, S, dsm, pp, next);
-    return lat_tile_impl<T, false, false>(A, C, bx, by, S, dsm, pp, next);
+        return lat_tile_impl<T, true, false, LAP64>(A, C, bx, by, S, dsm, pp, next);
+    return lat_tile_impl<T, false, false, LAP64>(A, C, bx, by, S, dsm, pp, next);
 }
 
 // After a tile: the published next tile (false: none), and whether its h
@@ -1008,14 +1036,15 @@ __device__ __forceinline__ bool take_next(const StepSmem<T> &S, TilePipe &pp) {
 // by TMA; walking several tiles per block with the next tile's h group
 // requested early measured slower for a single mesh (more instructions per
 // node, no better issue rate), so that walk is left to the batched kernel.
-template <typename T>
+// LAP64: the kappa lap rho term of mu in FP64 (FELBM_PARAM_LAP_FP64).
+template <typename T, bool LAP64 = false>
 __global__ void __launch_bounds__(kNT, (sizeof(T) == 4 ? 1024 : 512) / kNT) k_lat_step(LatArgs<T> A) {
     __shared__ StepSmem<T> S;
     extern __shared__ __align__(128) unsigned char lat_dsm[];
     lat_block_init<T>(S);
     TilePipe pp;
     const NextTile none{0, 0, 0, false, false};
-    lat_tile<T>(A, A.c, blockIdx.x, blockIdx.y, S, lat_dsm, pp, none);
+    lat_tile<T, LAP64>(A, A.c, blockIdx.x, blockIdx.y, S, lat_dsm, pp, none);
 }
 
 }  // namespace felbm

@@ -305,14 +305,20 @@ class Mesh:
             pass
 
 
-def make_params(rho_l, rho_v, sigma, xi, tau_l, tau_v, dt, gravity=(0.0, 0.0), precision="fp64"):
+FELBM_PARAM_LAP_FP64 = 0x1
+
+
+def make_params(rho_l, rho_v, sigma, xi, tau_l, tau_v, dt, gravity=(0.0, 0.0), precision="fp64",
+                lap_fp64=False):
+    """felbm_params; lap_fp64: FP32 states form the kappa lap rho term of mu
+    in FP64 (FELBM_PARAM_LAP_FP64)."""
     p = felbm_params()
     p.rho_l, p.rho_v, p.sigma, p.xi = rho_l, rho_v, sigma, xi
     p.tau_l, p.tau_v, p.dt = tau_l, tau_v, dt
     g = tuple(gravity) + (0.0,) * (3 - len(gravity))
     p.gravity[0], p.gravity[1], p.gravity[2] = g
     p.precision = FELBM_FP64 if precision in ("fp64", FELBM_FP64) else FELBM_FP32
-    p.flags = 0
+    p.flags = FELBM_PARAM_LAP_FP64 if lap_fp64 else 0
     return p
 
 

@@ -28,10 +28,10 @@ def _lib():
     felbm.load()
 
 
-def run_gpu(prob, precision, steps, general=False):
+def run_gpu(prob, precision, steps, general=False, lap_fp64=False):
     mesh = felbm.Mesh(prob.xy, prob.tri, prob.box, prob.tag, general=general)
-    st = felbm.State(mesh, felbm.make_params(precision=precision, **prob.params), prob.rho0,
-                     prob.u0, prob.p0)
+    st = felbm.State(mesh, felbm.make_params(precision=precision, lap_fp64=lap_fp64, **prob.params),
+                     prob.rho0, prob.u0, prob.p0)
     st.step(steps)
     m = st.moments()
     kind = mesh.info()["kind"]
@@ -306,12 +306,53 @@ def test_fullsize_rayleigh_taylor_fp32_steps():
     assert e["rho"] <= 1e-6 and e["C"] <= 1e-6 and e["p"] <= 1e-5 and du <= 1e-5, (e, du)
 
 
-def test_fullsize_unstructured_fp32_1000_steps():
-    # 256x256 jittered Delaunay droplet, density ratio 1000, 1000 steps
+@pytest.mark.parametrize("lap_fp64", [False, True])
+def test_fullsize_unstructured_fp32_1000_steps(lap_fp64):
+    # 256x256 jittered Delaunay droplet, density ratio 1000, 1000 steps; with
+    # lap_fp64 the kappa lap rho term of mu is formed in FP64
     prob = configs.c2_unstructured_droplet()
-    m, kind = run_gpu(prob, "fp32", 1000)
+    m, kind = run_gpu(prob, "fp32", 1000, lap_fp64=lap_fp64)
     assert kind == 0
     o = run_oracle(prob, 1000)
     e = errors(m, o)
-    print("c2 1000-step fp32 errors", e)
+    print("c2 1000-step fp32 errors (lap_fp64=%s)" % lap_fp64, e)
     assert e["C"] <= 1e-6 and e["u"] <= 1e-5, e
+
+
+def test_fp64_laplacian_term_on_the_structured_lattice_ratio_1000():
+    """FELBM_PARAM_LAP_FP64 on the lattice kernel (interior, TMA and wrap
+    tiles) with the C2 physics (ratio 1000, xi 12) on a 96 x 80 split, 1000
+    FP32 steps against the FP64 oracle, beside the plain FP32 run; the FP64
+    term changes the arithmetic (the runs differ) and both hold the bounds."""
+    xy, tri, box, tag = inputs.structured_mesh(96, 80)
+    rho0, u0, p0 = inputs.droplet_fields(xy, box, (48, 40), 20.0, 1.0, 1e-3, 12.0)
+    prob = configs.Problem("s", xy, tri, box, tag, rho0, u0, p0,
+                           configs.params(1.0, 1e-3, 0.01, 12.0, 0.0025, 0.1, 0.4), 0, "fp32")
+    o = run_oracle(prob, 1000)
+    res = {}
+    for flag in (False, True):
+        m, kind = run_gpu(prob, "fp32", 1000, lap_fp64=flag)
+        assert kind == 1
+        res[flag] = (m, errors(m, o))
+    print("structured ratio-1000 fp32 errors: plain", res[False][1], "lap_fp64", res[True][1])
+    assert not np.array_equal(res[False][0]["u"], res[True][0]["u"])
+    for flag in (False, True):
+        e = res[flag][1]
+        assert e["C"] <= 1e-6 and e["u"] <= 1e-5, (flag, e)
+
+
+def test_fp64_laplacian_flag_is_refused_where_not_built():
+    prob = _droplet(32, 32, 8.0)
+    mesh = felbm.Mesh(prob.xy, prob.tri, prob.box, prob.tag)
+    st = felbm.State(mesh, felbm.make_params(precision="fp32", lap_fp64=True, **prob.params), prob.rho0)
+    with pytest.raises(felbm.FelbmError) as e:
+        felbm.Batch([st])
+    assert e.value.status == felbm.FELBM_ERR_UNSUPPORTED
+    st.close()
+    mesh.close()
+    xyz, tet, box, _ = inputs.structured_tet_mesh(4, 4, 4)
+    tm = felbm.Mesh(xyz, tet, box)
+    with pytest.raises(felbm.FelbmError) as e:
+        felbm.State(tm, felbm.make_params(precision="fp32", lap_fp64=True, **prob.params), np.ones(len(xyz)))
+    assert e.value.status == felbm.FELBM_ERR_UNSUPPORTED
+    tm.close()
