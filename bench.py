@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true",
                     help="leave out the FP64 rate of the same workload")
     ap.add_argument("--fp64-steps", type=int, default=500)
+    ap.add_argument("--lap-fp64", default="auto", choices=["auto", "on", "off"],
+                    help="FP64 kappa lap rho term of mu in FP32 runs (auto: at density ratio >= 1000)")
     ap.add_argument("--shards", type=int, default=2,
                     help="slabs of the halo-sharded run of the same lattice on this GPU (<= 1: none)")
     ap.add_argument("--skip-batched", action="store_true")
@@ -193,6 +195,9 @@ def workload(name="rayleigh_taylor_512x2048"):
                                           0.1, 0.5, 0, "fp32", name)
     if name == "delaunay_droplet_256x256":
         return configs.c2_unstructured_droplet()
+    if name == "delaunay_droplet_1024x1024":
+        # the C2 physics on a 4x wider box (state beyond L2), radius scaled
+        return configs.c2_unstructured_droplet(n=1024, R=192.0)
     if name == "droplet3d_64x64x64":
         return configs.droplet_3d(64)
     if name == "droplet3d_128x128x128":
@@ -215,9 +220,9 @@ def config_dict(prob, precision, name="rayleigh_taylor_512x2048"):
         side = int(round(prob.n_nodes ** (1.0 / 3.0)))
         phys = {"mesh": "%d^3 cube, 6 Kuhn tetrahedra per cube, periodic x, y, z" % side,
                 "ratio": 10.0, "radius": side / 4.0, "xi": prob.params["xi"]}
-    elif name == "delaunay_droplet_256x256":
+    elif name.startswith("delaunay_droplet_"):
         phys = {"mesh": "jittered Delaunay (seed 1608), periodic x and y", "ratio": 1000.0,
-                "radius": 48.0, "xi": prob.params["xi"], "nu_ratio": 40.0}
+                "radius": 192.0 if "1024" in name else 48.0, "xi": prob.params["xi"], "nu_ratio": 40.0}
     else:
         phys = {"mesh": "structured P1 split, walls y, periodic x", "Re": 3000, "atwood": 0.5}
     return {"workload": name, "nodes": prob.n_nodes, "triangles": int(len(prob.tri)),
@@ -337,10 +342,10 @@ def run_reference(args):
                                           0.5, 0, "fp32", "droplet_sample")
         sample = ("oracle (FP64 C, 1 thread) time step of a 128x128 periodic droplet with the "
                   "physics of the 2048x2048 case (16,384 nodes) per step")
-    elif args.workload == "delaunay_droplet_256x256":
+    elif args.workload.startswith("delaunay_droplet_"):
         samp = configs.c2_unstructured_droplet(n=64, R=12.0)
         sample = ("oracle (FP64 C, 1 thread) time step of a 64x64 jittered Delaunay droplet "
-                  "with the physics of the 256x256 case (4,096 nodes) per step")
+                  "with the physics of the %s case (4,096 nodes) per step" % args.workload)
     elif args.workload.startswith("droplet3d_"):
         samp = configs.droplet_3d(16)
         sample = ("3-D oracle (FP64 C, 1 thread) time step of a 16^3 tetrahedral droplet with "
@@ -458,10 +463,14 @@ def main():
     from paper_1608_01906_gb300 import felbm
 
     prob = workload(args.workload)
+    dim0 = int(np.shape(prob.xy)[1])
     stream = torch.cuda.Stream()
     mesh = felbm.Mesh(prob.xy, prob.tri, prob.box, prob.tag, general=args.general,
                       stream=stream.cuda_stream)
-    params = felbm.make_params(precision=args.precision, **prob.params)
+    # FP64 kappa lap rho term of mu at density ratio >= 1000 (FP32 states)
+    lap64 = args.precision == "fp32" and dim0 == 2 and (
+        args.lap_fp64 == "on" or (args.lap_fp64 == "auto" and prob.params["rho_l"] >= 1000.0 * prob.params["rho_v"]))
+    params = felbm.make_params(precision=args.precision, lap_fp64=lap64, **prob.params)
     st = felbm.State(mesh, params, prob.rho0, prob.u0, prob.p0)
     st.step(args.warmup)
     st.sync()
@@ -529,6 +538,21 @@ def main():
                 "kernel_ms": dom_avg_ms, "peak_source": peak_kind + " copy bandwidth",
                 "step_gbs": algo * args.steps / (ms * 1e-3) / 1e9,
                 "kernel_share": dom_ms / max(sum(v[0] for v in prof.values()), 1e-12)}
+    if kind == 0:
+        # general meshes: CSR metadata, reported apart from the algorithmic
+        # state bytes: per node a row offset, and per neighbour a column
+        # index and 5 coefficients (a_x, a_y, b_xx, b_xy, b_yy) in the
+        # state's precision; the four launches read it 2 + 2 x 3/5 times
+        tri = np.asarray(prob.tri, dtype=np.int64)
+        ed = np.sort(np.stack([tri[:, [0, 1, 2]].ravel(), tri[:, [1, 2, 0]].ravel()], 1), axis=1)
+        nnz = 2 * len(np.unique(ed[:, 0] * prob.n_nodes + ed[:, 1]))
+        es = 4 if args.precision == "fp32" else 8
+        deg = nnz / prob.n_nodes
+        once = 4 + deg * (4 + 5 * es)
+        meta_step = 2 * once + 2 * (4 + deg * (4 + 2 * es))
+        roofline["metadata"] = {
+            "nnz_per_node": deg, "csr_bytes_per_node": once, "read_per_step_bytes_per_node": meta_step,
+            "achieved_with_metadata_gbs": (algo + meta_step * prob.n_nodes) / (dom_avg_ms * 1e-3) / 1e9}
     if multi:
         roofline["note"] = ("step of %d dependent launches rated as one: algorithmic bytes of the "
                             "step over the summed launch times" % len(per_step))
@@ -666,7 +690,7 @@ def main():
                 "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64",
                 "data": "synthetic", "config": dict(config_dict(prob, args.precision, args.workload),
-                                                    mesh_kind=kind),
+                                                    mesh_kind=kind, kappa_lap_fp64=lap64),
                 "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},

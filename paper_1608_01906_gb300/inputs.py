@@ -119,52 +119,45 @@ def jittered_delaunay_mesh(nx, ny, jitter=0.25, seed=1608, h=1.0):
     xy = xy0 + rng.uniform(-jitter * h, jitter * h, size=xy0.shape)
     xy[:, 0] %= box[0]
     xy[:, 1] %= box[1]
-    tri = [list(t) for t in tri.tolist()]
+    tri = tri.astype(np.int64)
+    n = len(xy)
     Lx, Ly = box
+    k0 = np.arange(3)
+    # Lawson flips in rounds: every round tests all edges, then flips a set of
+    # strictly non-Delaunay edges no two of which share a triangle.  For
+    # points in general position the Delaunay triangulation is unique, so the
+    # order of the flips does not change the result.
+    while True:
+        a_ = tri[:, k0].ravel()
+        b_ = tri[:, (k0 + 1) % 3].ravel()
+        key = np.minimum(a_, b_) * n + np.maximum(a_, b_)
+        order = np.argsort(key, kind="stable")
+        ks = key[order]
+        first = np.nonzero(ks[:-1] == ks[1:])[0]  # each interior edge: two sides
+        e1, e2 = order[first], order[first + 1]
+        t1, j1 = e1 // 3, e1 % 3
+        t2, j2 = e2 // 3, e2 % 3
+        u, v = tri[t1, j1], tri[t1, (j1 + 1) % 3]
+        c = tri[t1, (j1 + 2) % 3]
+        d = tri[t2, (j2 + 2) % 3]
 
-    def rel(o, p):
-        return (_wrap(xy[p, 0] - xy[o, 0], Lx), _wrap(xy[p, 1] - xy[o, 1], Ly))
+        def rel(o, q):
+            return (_wrap(xy[q, 0] - xy[o, 0], Lx), _wrap(xy[q, 1] - xy[o, 1], Ly))
 
-    # edge -> (triangle, local index of the edge's first vertex); edge (u, v) is
-    # the directed edge t[k] -> t[k+1] of triangle t.
-    def build_edges():
-        e = {}
-        for ti, t in enumerate(tri):
-            for k in range(3):
-                e[(t[k], t[(k + 1) % 3])] = ti
-        return e
-
-    edges = build_edges()
-    queue = list(edges.keys())
-    flips = 0
-    while queue:
-        u, v = queue.pop()
-        t1 = edges.get((u, v))
-        t2 = edges.get((v, u))
-        if t1 is None or t2 is None:
-            continue
-        A = tri[t1]
-        B = tri[t2]
-        c = [p for p in A if p != u and p != v][0]
-        d = [p for p in B if p != u and p != v][0]
-        # coordinates relative to u: triangle (u, v, c) is CCW
         vx, vy = rel(u, v)
         cx, cy = rel(u, c)
         dx, dy = rel(u, d)
-        if _incircle(0.0, 0.0, vx, vy, cx, cy, dx, dy) <= 0.0:
-            continue
+        bad = np.nonzero(_incircle(0.0, 0.0, vx, vy, cx, cy, dx, dy) > 0.0)[0]
+        if len(bad) == 0:
+            break
+        # keep a flip only where it is the first candidate of both triangles
+        owner = np.full(len(tri), len(first), dtype=np.int64)
+        np.minimum.at(owner, t1[bad], bad)
+        np.minimum.at(owner, t2[bad], bad)
+        sel = bad[(owner[t1[bad]] == bad) & (owner[t2[bad]] == bad)]
         # flip edge (u, v) -> (c, d): new CCW triangles (u, d, c) and (d, v, c)
-        for t in (A, B):
-            for k in range(3):
-                edges.pop((t[k], t[(k + 1) % 3]), None)
-        tri[t1] = [u, d, c]
-        tri[t2] = [d, v, c]
-        for ti in (t1, t2):
-            t = tri[ti]
-            for k in range(3):
-                edges[(t[k], t[(k + 1) % 3])] = ti
-        queue.extend([(u, d), (d, v), (v, c), (c, u)])
-        flips += 1
+        tri[t1[sel]] = np.stack([u[sel], d[sel], c[sel]], axis=1)
+        tri[t2[sel]] = np.stack([d[sel], v[sel], c[sel]], axis=1)
     tri = np.asarray(tri, dtype=np.int32)
     return xy, tri, box, tag
 
