@@ -68,7 +68,7 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=40)
     ap.add_argument("--workload", default="rayleigh_taylor_512x2048",
                     choices=["rayleigh_taylor_512x2048", "droplet_2048x2048",
-                             "delaunay_droplet_256x256", "droplet3d_64x64x64",
+                             "delaunay_droplet_256x256", "delaunay_droplet_1024x1024", "droplet3d_64x64x64",
                              "droplet3d_128x128x128"],
                     help="droplet_2048x2048: supplementary single-mesh case (periodic, 4.2 M "
                          "nodes); delaunay_droplet_256x256: the unstructured case (general "
