@@ -33,14 +33,16 @@ METRIC = "MNUPS"
 UNIT = "MNUPS"
 ALGO_BYTES_PER_NODE = {"fp32": 144, "fp64": 288}  # 18 populations read + 18 written
 FALLBACK_HBM_GBS = 6800.0
-# FP64 runs are bound by the FP64 pipe (about 85% busy), not by HBM.  Peak:
+# FP64 runs are bound by the FP64 pipe (about 86% busy), not by HBM.  Peak:
 # the FP64 FMA rate measured on the device (felbm_alu_peak), else the nominal
-# dense FP64 rate of the part.  Algorithmic flops per node update
-# in FP64: the 1251 flops ncu counts per node (2 DFMA + DADD + DMUL) less the
-# halo recompute of the tile step (h streaming on the depth-3 halo, 1.08x
-# extra; grad rho 0.69x; mu 0.33x; about 220 flops)
+# dense FP64 rate of the part.  Algorithmic flops per node update in FP64:
+# the 1,000 flops ncu counts per node on the current step (DADD + DMUL +
+# 2 DFMA) less the halo recompute of the tile step (h streaming on the
+# depth-3 density region, 1.08x extra: about 136; grad rho 0.69x and mu
+# 0.33x: about 16), which agrees with an operator-by-operator count of the
+# streaming, recovery, mu, force, moment and collision arithmetic (854)
 FP64_PEAK_TFLOPS = 1.25
-FP64_ALGO_FLOPS_PER_NODE = 1030
+FP64_ALGO_FLOPS_PER_NODE = 850
 
 
 def parse():

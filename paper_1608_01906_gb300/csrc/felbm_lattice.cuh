@@ -474,7 +474,9 @@ constexpr int kGW = kLTX + 4, kGH = kLTY + 4;     // grad rho: halo 2
 constexpr int kMW = kLTX + 2, kMH = kLTY + 2;     // mu: halo 1
 constexpr int kNT = kLTX * kLTY;
 // row groups of three of the blocked stages on interior tiles (one pass each)
-constexpr int kDG = (kQH + 2) / 3, kGG = (kGH + 2) / 3, kMG = (kMH + 2) / 3;
+// (rows per thread: kGR in the gradient stage, kMR in the mu stage)
+constexpr int kGR = 3, kMR = 3;
+constexpr int kDG = (kQH + 2) / 3, kGG = (kGH + kGR - 1) / kGR, kMG = (kMH + kMR - 1) / kMR;
 static_assert(kRW * kDG <= kNT && kRW * kGG <= kNT && kRW * kMG <= kNT, "one pass per blocked stage");
 
 // Shared memory of one tile: the scalar chain (static) and the population
@@ -813,18 +815,18 @@ __device__ __forceinline__ bool lat_tile_impl(const LatArgs<T> &A, const LatCoef
         if (tid < kRW * kGG) {
             const int g = tid / kRW, lw = tid - g * kRW;
             if (lw >= 2 && lw < kGW + 2) {
-                const int lx = lw - 2, ly0 = 3 * g;
-                // s_rho rows ly0 .. ly0 + 4 (rows a - 1 .. a + 1 of a = ly + 1)
-                T cx[5], cl[4], cr[4];
+                const int lx = lw - 2, ly0 = kGR * g;
+                // s_rho rows ly0 .. ly0 + kGR + 1 (rows a - 1 .. a + 1 of a = ly + 1)
+                T cx[kGR + 2], cl[kGR + 1], cr[kGR + 1];
 #pragma unroll
-                for (int j = 0; j < 5; ++j) cx[j] = s_rho[min(ly0 + j, kRH - 1)][lw];
+                for (int j = 0; j < kGR + 2; ++j) cx[j] = s_rho[min(ly0 + j, kRH - 1)][lw];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
+                for (int j = 0; j < kGR + 1; ++j) {
                     cl[j] = s_rho[min(ly0 + j, kRH - 1)][lw - 1];
                     cr[j] = s_rho[min(ly0 + 1 + j, kRH - 1)][lw + 1];
                 }
 #pragma unroll
-                for (int i = 0; i < 3; ++i) {
+                for (int i = 0; i < kGR; ++i) {
                     if (ly0 + i < kGH) {
                         T sx, sy;
                         rec_uni<T>(cr[i], cr[i + 1], cx[i + 2], cl[i + 1], cl[i], cx[i], sx, sy);
@@ -859,17 +861,17 @@ __device__ __forceinline__ bool lat_tile_impl(const LatArgs<T> &A, const LatCoef
         if (tid < kRW * kMG) {
             const int g = tid / kRW, lw = tid - g * kRW;
             if (lw >= 1 && lw < kMW + 1) {
-                const int lx = lw - 1, ly0 = 3 * g;
-                V2<T> cx[5], cl[4], cr[4];
+                const int lx = lw - 1, ly0 = kMR * g;
+                V2<T> cx[kMR + 2], cl[kMR + 1], cr[kMR + 1];
 #pragma unroll
-                for (int j = 0; j < 5; ++j) cx[j] = s_g[min(ly0 + j, kGH - 1)][lw];
+                for (int j = 0; j < kMR + 2; ++j) cx[j] = s_g[min(ly0 + j, kGH - 1)][lw];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
+                for (int j = 0; j < kMR + 1; ++j) {
                     cl[j] = s_g[min(ly0 + j, kGH - 1)][lw - 1];
                     cr[j] = s_g[min(ly0 + 1 + j, kGH - 1)][lw + 1];
                 }
 #pragma unroll
-                for (int i = 0; i < 3; ++i) {
+                for (int i = 0; i < kMR; ++i) {
                     const int ly = ly0 + i;
                     if (ly < kMH) {
                         const V2<T> E0 = vsub<T>(cr[i], cl[i + 1]);
