@@ -341,6 +341,28 @@ def test_fp64_laplacian_term_on_the_structured_lattice_ratio_1000():
         assert e["C"] <= 1e-6 and e["u"] <= 1e-5, (flag, e)
 
 
+def test_fp64_laplacian_term_on_wall_and_ragged_tiles():
+    """FELBM_PARAM_LAP_FP64 on the lattice kernel's table path: a droplet
+    between bounce-back walls on a 72 x 48 split (wall rows, a ragged x tile,
+    cp.async fills), 500 FP32 steps against the FP64 oracle beside the plain
+    FP32 run, at the FP32 bounds; and the same on the general kernels."""
+    xy, tri, box, tag = inputs.structured_mesh(72, 48, periodic_y=False)
+    rho0, u0, p0 = inputs.droplet_fields(xy, box, (36, 24), 10.0, 1.0, 0.1, 4.0)
+    prob = configs.Problem("w", xy, tri, box, tag, rho0, u0, p0, configs.params(), 0, "fp32")
+    o = run_oracle(prob, 500)
+    for general in (False, True):
+        res = {}
+        for flag in (False, True):
+            m, kind = run_gpu(prob, "fp32", 500, general=general, lap_fp64=flag)
+            assert kind == (0 if general else 1)
+            res[flag] = (m, errors(m, o))
+        print("walled droplet fp32 errors (general=%s): plain" % general, res[False][1], "lap_fp64", res[True][1])
+        assert not np.array_equal(res[False][0]["p"], res[True][0]["p"])
+        for flag in (False, True):
+            e = res[flag][1]
+            assert e["C"] <= 1e-6 and e["u"] <= 1e-5, (general, flag, e)
+
+
 def test_fp64_laplacian_flag_is_refused_where_not_built():
     prob = _droplet(32, 32, 8.0)
     mesh = felbm.Mesh(prob.xy, prob.tri, prob.box, prob.tag)
