@@ -574,7 +574,7 @@ def main():
     # ---- the same workload in FP64 (after the FP32 timed region): its rate
     # and its roofline against the measured FP64 FMA ceiling
     fp64 = None
-    if args.precision == "fp32" and not args.no_fp64:
+    if args.precision == "fp32" and not args.no_fp64 and world == 1:
         p64 = felbm.make_params(precision="fp64", **prob.params)
         s64 = felbm.State(mesh, p64, prob.rho0, prob.u0, prob.p0)
         s64.step(args.warmup)
@@ -609,7 +609,7 @@ def main():
     # ---- the same lattice cut into halo-sharded slabs on this device: each
     # step is every slab's step plus the halo exchange (pack, copies, unpack)
     sharded = None
-    if kind == 1 and dim == 2 and args.shards > 1:
+    if kind == 1 and dim == 2 and args.shards > 1 and world == 1:
         from paper_1608_01906_gb300 import sharding
 
         try:
