@@ -65,12 +65,16 @@ def parse():
                     help="slabs of the halo-sharded run of the same lattice on this GPU (<= 1: none)")
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-serving", action="store_true")
+    ap.add_argument("--split-step", action="store_true",
+                    help="general triangle meshes: always the four-launch step")
+    ap.add_argument("--patch-step", action="store_true",
+                    help="general triangle meshes: always the one-launch patch step")
     ap.add_argument("--general", action="store_true",
                     help="force the general CSR kernels on a structured mesh")
     ap.add_argument("--serve-requests", type=int, default=40)
     ap.add_argument("--workload", default="rayleigh_taylor_512x2048",
                     choices=["rayleigh_taylor_512x2048", "droplet_2048x2048",
-                             "delaunay_droplet_256x256", "delaunay_droplet_1024x1024", "droplet3d_64x64x64",
+                             "delaunay_droplet_256x256", "delaunay_droplet_512x512", "delaunay_droplet_1024x1024", "droplet3d_64x64x64",
                              "droplet3d_128x128x128"],
                     help="droplet_2048x2048: supplementary single-mesh case (periodic, 4.2 M "
                          "nodes); delaunay_droplet_256x256: the unstructured case (general "
@@ -197,6 +201,8 @@ def workload(name="rayleigh_taylor_512x2048"):
                                           0.1, 0.5, 0, "fp32", name)
     if name == "delaunay_droplet_256x256":
         return configs.c2_unstructured_droplet()
+    if name == "delaunay_droplet_512x512":
+        return configs.c2_unstructured_droplet(n=512, R=96.0)
     if name == "delaunay_droplet_1024x1024":
         # the C2 physics on a 4x wider box (state beyond L2), radius scaled
         return configs.c2_unstructured_droplet(n=1024, R=192.0)
@@ -224,7 +230,8 @@ def config_dict(prob, precision, name="rayleigh_taylor_512x2048"):
                 "ratio": 10.0, "radius": side / 4.0, "xi": prob.params["xi"]}
     elif name.startswith("delaunay_droplet_"):
         phys = {"mesh": "jittered Delaunay (seed 1608), periodic x and y", "ratio": 1000.0,
-                "radius": 192.0 if "1024" in name else 48.0, "xi": prob.params["xi"], "nu_ratio": 40.0}
+                "radius": {"delaunay_droplet_512x512": 96.0, "delaunay_droplet_1024x1024": 192.0}.get(name, 48.0),
+                "xi": prob.params["xi"], "nu_ratio": 40.0}
     else:
         phys = {"mesh": "structured P1 split, walls y, periodic x", "Re": 3000, "atwood": 0.5}
     return {"workload": name, "nodes": prob.n_nodes, "triangles": int(len(prob.tri)),
@@ -468,7 +475,7 @@ def main():
     dim0 = int(np.shape(prob.xy)[1])
     stream = torch.cuda.Stream()
     mesh = felbm.Mesh(prob.xy, prob.tri, prob.box, prob.tag, general=args.general,
-                      stream=stream.cuda_stream)
+                      stream=stream.cuda_stream, split_step=args.split_step, patch_step=args.patch_step)
     # FP64 kappa lap rho term of mu at density ratio >= 1000 (FP32 states)
     lap64 = args.precision == "fp32" and dim0 == 2 and (
         args.lap_fp64 == "on" or (args.lap_fp64 == "auto" and prob.params["rho_l"] >= 1000.0 * prob.params["rho_v"]))

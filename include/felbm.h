@@ -63,6 +63,8 @@ typedef enum felbm_status {
 #define FELBM_PERIODIC_Y 0x2u   /* box[1] > 0 is the period in y */
 #define FELBM_MESH_GENERAL 0x4u /* never use the structured-lattice kernels */
 #define FELBM_PERIODIC_Z 0x8u   /* tetrahedral meshes: box[2] > 0 is the period in z */
+#define FELBM_MESH_SPLIT_STEP 0x10u /* general triangle meshes: always four launches per step */
+#define FELBM_MESH_PATCH_STEP 0x20u /* general triangle meshes: always the one-launch patch step */
 
 /* precision of the stored distributions and of the bulk arithmetic */
 #define FELBM_FP64 0
@@ -107,14 +109,21 @@ typedef struct felbm_params {
  *   box       host, 2 doubles: period in x and y; read only for the
  *             directions flagged periodic.  Every element edge must be shorter
  *             than half the period.
- *   flags     FELBM_PERIODIC_X | FELBM_PERIODIC_Y | FELBM_MESH_GENERAL.
+ *   flags     FELBM_PERIODIC_X | FELBM_PERIODIC_Y | FELBM_MESH_GENERAL |
+ *             FELBM_MESH_SPLIT_STEP or FELBM_MESH_PATCH_STEP.
  *   node_tag  host, n_nodes uint8 or NULL: 0 = fluid; k in 1..8 = no-slip
  *             wall node whose inward normal is e_k.
  *   stream    cudaStream_t (as void*) all work of this mesh and its states is
  *             issued on; NULL = legacy default stream.
  * The library computes element geometry, the lumped mass, the assembled
- * streaming/recovery coefficients and an internal node order (reverse
- * Cuthill-McKee); a mesh that is the structured split of a unit lattice
+ * streaming/recovery coefficients and an internal node order: patches of
+ * 256 nodes along a Hilbert curve over the domain, reverse Cuthill-McKee
+ * order within a patch.  A general mesh of up to 2^18 nodes steps in one
+ * launch per step, one block per patch with the patch's nodes up to 4 edges
+ * away staged in shared memory; larger ones in four launches per step over
+ * global fields (measured faster there).  FELBM_MESH_SPLIT_STEP and
+ * FELBM_MESH_PATCH_STEP force one of the two; both give the same results bit
+ * for bit.  A mesh that is the structured split of a unit lattice
  * (node i at ((i mod nx) h, (i div nx) h), each square cut along its
  * (i,j)-(i+1,j+1) diagonal, periodic in x, periodic or walled in y) is served
  * by the structured-lattice kernels unless FELBM_MESH_GENERAL is set.
@@ -266,7 +275,8 @@ void felbm_batch_destroy(felbm_batch *batch);
  *   0 stream h + rho, 1 grad rho, 2 lap rho / stress / mu,
  *   3 grad mu + stream + collide (the general four-pass step),
  *   4 lattice step (one launch per step on structured meshes),
- *   5-7 unused. */
+ *   5 patch step (one launch per step on general triangle meshes),
+ *   6-7 unused. */
 #define FELBM_PROFILE_KINDS 8
 
 /* on != 0: every kernel launched by later felbm_step calls is bracketed by a

@@ -27,7 +27,20 @@ struct HostCSR {
     std::vector<uint8_t> tag;      // internal order, empty if no walls
     std::vector<int32_t> perm;     // perm[internal] = caller id
     std::vector<int32_t> iperm;    // iperm[caller] = internal id
+    // Patches of the one-launch step (internal order is patch-major: patch p
+    // owns the nodes [p kPatch, min(n, (p + 1) kPatch))).  Per patch its
+    // region: its own nodes, then the nodes 1, 2, 3 and 4 edges away, as
+    // internal ids in pnode[pnbase[p] ..); pcount[4 p ..] the cumulative
+    // counts of rings <= 0, 1, 2, 3.  For the region nodes of rings <= 3,
+    // prowbase gives the offset in plcol of the region indices of their CSR
+    // columns (in CSR order).
+    std::vector<int32_t> pnbase, pcount, pnode, prowbase;
+    std::vector<uint16_t> plcol;
+    int32_t rmax = 0, r1max = 0, r2max = 0, r3max = 0;  // largest region / ring <= 1, 2, 3 sizes
 };
+
+constexpr int kPatch = 256;  // nodes per patch of the general one-launch step
+constexpr int64_t kPatchStepMaxNodes = 1 << 18;  // default patch step up to this size
 
 // General tetrahedral mesh (3-D), same conventions: for each neighbour j != i
 // a_ij = sum_{T∋i,j} |T| grad N_j / (4 m_i) (3 components) and the symmetric
@@ -273,6 +286,10 @@ struct felbm_mesh {
     float *d_coef32 = nullptr;
     double *d_mass = nullptr;
     uint8_t *d_tag = nullptr;
+    // patches of the one-launch step of general triangle meshes (HostCSR)
+    int32_t *d_pnbase = nullptr, *d_pcount = nullptr, *d_pnode = nullptr, *d_prowbase = nullptr;
+    uint16_t *d_plcol = nullptr;
+    bool patch_step = false;
     int64_t device_bytes = 0;
 };
 

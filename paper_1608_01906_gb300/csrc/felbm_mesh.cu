@@ -107,6 +107,142 @@ std::vector<int32_t> rcm_order(int32_t n, const std::vector<int32_t> &rp,
     return order;
 }
 
+// Index of cell (x, y) along the Hilbert curve over a 2^k x 2^k grid (n =
+// 2^k): descend through the quadrants, adding the cells of the quadrants the
+// curve visits first, and turn the coordinates into the visited quadrant's
+// own frame (Hilbert's construction, as in the usual iterative form).
+static uint64_t hilbert_index(uint32_t n, uint32_t x, uint32_t y) {
+    uint64_t d = 0;
+    for (uint32_t s = n / 2; s > 0; s /= 2) {
+        const uint32_t rx = (x & s) ? 1u : 0u, ry = (y & s) ? 1u : 0u;
+        d += (uint64_t)s * s * ((3u * rx) ^ ry);
+        if (ry == 0) {
+            if (rx == 1) {
+                x = s - 1 - (x & (s - 1));
+                y = s - 1 - (y & (s - 1));
+            } else {
+                x &= s - 1;
+                y &= s - 1;
+            }
+            const uint32_t t = x;
+            x = y;
+            y = t;
+        } else {
+            x &= s - 1;
+            y &= s - 1;
+        }
+    }
+    return d;
+}
+
+// Internal order of a general mesh: nodes sorted along a Hilbert curve over
+// a grid about twice as fine as the node spacing, cut into patches of kPatch
+// consecutive nodes (compact pieces of the mesh), each patch in the reverse
+// Cuthill-McKee order of rcm (rcm[k] = caller id of RCM rank k).
+static std::vector<int32_t> patch_order(const double *xy, int32_t N, const double Lp[2],
+                                        const std::vector<int32_t> &rcm) {
+    double lo[2] = {0, 0}, ext[2] = {0, 0};
+    for (int d = 0; d < 2; ++d) {
+        if (Lp[d] > 0.0) {
+            ext[d] = Lp[d];
+            continue;
+        }
+        double a = xy[d], b = xy[d];
+        for (int32_t i = 1; i < N; ++i) {
+            a = std::min(a, xy[2 * i + d]);
+            b = std::max(b, xy[2 * i + d]);
+        }
+        lo[d] = a;
+        ext[d] = std::max(b - a, 1e-300);
+    }
+    uint32_t n = 1;
+    while ((double)n * n < 4.0 * N && n < (1u << 16)) n *= 2;
+    const double cell = std::max(ext[0], ext[1]) / n;
+    std::vector<int32_t> rank((size_t)N);
+    for (int32_t k = 0; k < N; ++k) rank[rcm[k]] = k;
+    std::vector<std::pair<uint64_t, int32_t>> key((size_t)N);
+    for (int32_t i = 0; i < N; ++i) {
+        uint32_t q[2];
+        for (int d = 0; d < 2; ++d) {
+            double v = xy[2 * i + d] - lo[d];
+            if (Lp[d] > 0.0) v -= Lp[d] * std::floor(v / Lp[d]);
+            const double c = std::floor(v / cell);
+            q[d] = (uint32_t)std::min(std::max(c, 0.0), (double)(n - 1));
+        }
+        key[i] = {hilbert_index(n, q[0], q[1]), rank[i]};
+    }
+    std::vector<int32_t> order((size_t)N);
+    for (int32_t i = 0; i < N; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+    for (int32_t p0 = 0; p0 < N; p0 += kPatch) {
+        const int32_t p1 = std::min(N, p0 + kPatch);
+        std::sort(order.begin() + p0, order.begin() + p1,
+                  [&](int32_t a, int32_t b) { return rank[a] < rank[b]; });
+    }
+    return order;
+}
+
+// Rings of every patch over the CSR in internal (patch-major) order.
+static void build_patches(HostCSR &H) {
+    const int32_t N = H.n, np = (N + kPatch - 1) / kPatch;
+    H.pnbase.assign((size_t)np + 1, 0);
+    H.pcount.assign((size_t)4 * np, 0);
+    H.pnode.clear();
+    H.prowbase.clear();
+    H.plcol.clear();
+    H.rmax = H.r1max = H.r2max = H.r3max = 0;
+    std::vector<int32_t> stamp((size_t)N, -1), loc((size_t)N, 0);
+    std::vector<int32_t> reg;
+    for (int32_t p = 0; p < np; ++p) {
+        reg.clear();
+        for (int32_t i = p * kPatch; i < std::min(N, (p + 1) * kPatch); ++i) {
+            stamp[i] = p;
+            loc[i] = (int32_t)reg.size();
+            reg.push_back(i);
+        }
+        int32_t cnt[4];
+        size_t ring0 = 0;
+        for (int ring = 1; ring <= 4; ++ring) {
+            cnt[ring - 1] = (int32_t)reg.size();
+            const size_t ring1 = reg.size();
+            for (size_t k = ring0; k < ring1; ++k)
+                for (int32_t e = H.rowptr[reg[k]]; e < H.rowptr[reg[k] + 1]; ++e) {
+                    const int32_t j = H.col[e];
+                    if (stamp[j] != p) {
+                        stamp[j] = p;
+                        loc[j] = (int32_t)reg.size();
+                        reg.push_back(j);
+                    }
+                }
+            ring0 = ring1;
+        }
+        if (reg.size() > 65535) {  // region indices are 16-bit: no patch step
+            H.pnbase.clear();
+            H.pcount.clear();
+            H.pnode.clear();
+            H.prowbase.clear();
+            H.plcol.clear();
+            return;
+        }
+        for (int r = 0; r < 4; ++r) H.pcount[4 * p + r] = cnt[r];
+        H.pnbase[p + 1] = H.pnbase[p] + (int32_t)reg.size();
+        for (size_t r = 0; r < reg.size(); ++r) {
+            H.pnode.push_back(reg[r]);
+            if ((int32_t)r < cnt[3]) {
+                H.prowbase.push_back((int32_t)H.plcol.size());
+                for (int32_t e = H.rowptr[reg[r]]; e < H.rowptr[reg[r] + 1]; ++e)
+                    H.plcol.push_back((uint16_t)loc[H.col[e]]);
+            } else {
+                H.prowbase.push_back(-1);
+            }
+        }
+        H.rmax = std::max(H.rmax, (int32_t)reg.size());
+        H.r1max = std::max(H.r1max, cnt[1]);
+        H.r2max = std::max(H.r2max, cnt[2]);
+        H.r3max = std::max(H.r3max, cnt[3]);
+    }
+}
+
 // Conformity of a P1 triangulation (the Galerkin streaming of Sec. 2.2.1
 // assumes a conforming mesh): every edge lies in at most two triangles, an
 // edge of two triangles is traversed in opposite directions by them (both
@@ -227,7 +363,7 @@ int build_csr(const double *xy, int64_t n_nodes, const int32_t *tri, int64_t n_t
     for (const Entry &e : m) rp0[e.i + 1]++;
     for (int32_t i = 0; i < N; ++i) rp0[i + 1] += rp0[i];
     for (size_t k = 0; k < m.size(); ++k) cl0[k] = m[k].j;  // m sorted by (i, j)
-    std::vector<int32_t> order = rcm_order(N, rp0, cl0);
+    std::vector<int32_t> order = patch_order(xy, N, Lp, rcm_order(N, rp0, cl0));
     out.n = N;
     out.perm = order;
     out.iperm.assign((size_t)N, 0);
@@ -264,6 +400,7 @@ int build_csr(const double *xy, int64_t n_nodes, const int32_t *tri, int64_t n_t
         out.tag.resize(N);
         for (int32_t k = 0; k < N; ++k) out.tag[k] = tag[order[k]];
     }
+    build_patches(out);
     return FELBM_OK;
 }
 

@@ -28,6 +28,8 @@ FELBM_PERIODIC_X = 0x1
 FELBM_PERIODIC_Y = 0x2
 FELBM_MESH_GENERAL = 0x4
 FELBM_PERIODIC_Z = 0x8
+FELBM_MESH_SPLIT_STEP = 0x10
+FELBM_MESH_PATCH_STEP = 0x20
 FELBM_FP64 = 0
 FELBM_FP32 = 1
 
@@ -238,7 +240,7 @@ def alu_peak(kind):
 
 # ---- owning wrappers ------------------------------------------------------
 
-def flags_for(box, general=False):
+def flags_for(box, general=False, split_step=False, patch_step=False):
     f = 0
     if box[0] > 0:
         f |= FELBM_PERIODIC_X
@@ -246,6 +248,10 @@ def flags_for(box, general=False):
         f |= FELBM_PERIODIC_Y
     if general:
         f |= FELBM_MESH_GENERAL
+    if split_step:
+        f |= FELBM_MESH_SPLIT_STEP
+    if patch_step:
+        f |= FELBM_MESH_PATCH_STEP
     return f
 
 
@@ -253,7 +259,8 @@ class Mesh:
     """Triangles (dim 2, D2Q9) or, given (N, 3) coordinates and (T, 4)
     tetrahedra, a tetrahedral mesh (dim 3, D3Q19)."""
 
-    def __init__(self, xy, tri, box, node_tag=None, general=False, stream=None):
+    def __init__(self, xy, tri, box, node_tag=None, general=False, stream=None, split_step=False,
+                 patch_step=False):
         self.n_nodes = len(xy)
         self.dim = np.shape(xy)[1]
         if self.dim == 3:
@@ -264,7 +271,8 @@ class Mesh:
             st, h = felbm_mesh_create_tet(xy, tri, box, f, node_tag, stream)
             _check(st, "felbm_mesh_create_tet")
         else:
-            st, h = felbm_mesh_create(xy, tri, box, flags_for(box, general), node_tag, stream)
+            st, h = felbm_mesh_create(xy, tri, box, flags_for(box, general, split_step, patch_step), node_tag,
+                                      stream)
             _check(st, "felbm_mesh_create")
         self.q = 19 if self.dim == 3 else 9
         self.handle = h

@@ -378,3 +378,36 @@ def test_fp64_laplacian_flag_is_refused_where_not_built():
         felbm.State(tm, felbm.make_params(precision="fp32", lap_fp64=True, **prob.params), np.ones(len(xyz)))
     assert e.value.status == felbm.FELBM_ERR_UNSUPPORTED
     tm.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("mesh", ["delaunay", "walled_split"])
+def test_patch_step_equals_four_launch_step_bitwise(precision, mesh):
+    """The one-launch patch step of general meshes (regions of rings <= 4
+    staged in shared memory) against the four-launch step over global
+    fields (FELBM_MESH_SPLIT_STEP): the same per-node arithmetic in the same
+    order, so the same bits, on a jittered Delaunay mesh with a moving drop
+    and on a walled split forced onto the general kernels (bounce-back)."""
+    if mesh == "delaunay":
+        xy, tri, box, tag = inputs.jittered_delaunay_mesh(70, 52, 0.25, seed=8)
+        rho0, u0, p0 = inputs.droplet_fields(xy, box, (35, 26), 12.0, 1.0, 0.1, 4.0, u0=(0.01, 0.005))
+        prm = configs.params(dt=0.4)
+    else:
+        xy, tri, box, tag = inputs.structured_mesh(40, 70, periodic_y=False)
+        rho0, u0, p0 = inputs.droplet_fields(xy, box, (20, 35), 10.0, 1.0, 0.1, 4.0)
+        prm = configs.params(gravity=(0.0, -1e-5))
+    out = []
+    for split in (False, True):
+        m_ = felbm.Mesh(xy, tri, box, tag, general=True, split_step=split)
+        st = felbm.State(m_, felbm.make_params(precision=precision, **prm), rho0, u0, p0)
+        st.profile_enable(True)
+        st.step(30)
+        prof = st.profile_read()
+        out.append((st.moments(), st.export(), prof))
+        st.close()
+        m_.close()
+    (ma, (ha, ga), pa), (mb, (hb, gb), pb) = out
+    assert pa["k_patch_step"][2] == 30 and pb["k_patch_step"][2] == 0 and pb["k_collide"][2] == 30
+    for k in ("rho", "C", "u", "p", "totals"):
+        assert np.array_equal(ma[k], mb[k]), k
+    assert np.array_equal(ha, hb) and np.array_equal(ga, gb)
