@@ -558,10 +558,20 @@ def main():
         es = 4 if args.precision == "fp32" else 8
         deg = nnz / prob.n_nodes
         once = 4 + deg * (4 + 5 * es)
-        meta_step = 2 * once + 2 * (4 + deg * (4 + 2 * es))
-        roofline["metadata"] = {
-            "nnz_per_node": deg, "csr_bytes_per_node": once, "read_per_step_bytes_per_node": meta_step,
-            "achieved_with_metadata_gbs": (algo + meta_step * prob.n_nodes) / (dom_avg_ms * 1e-3) / 1e9}
+        patch = prof.get("k_patch_step", (0, 0, 0))[2] > 0
+        if patch:
+            # one launch: each patch reads the CSR rows of its region (rings
+            # <= 3, shared with neighbouring patches through L2) and its
+            # region lists; counted once per node here
+            roofline["metadata"] = {"step": "patch", "nnz_per_node": deg, "csr_bytes_per_node": once,
+                                    "achieved_with_metadata_gbs": (algo + once * prob.n_nodes) /
+                                    (dom_avg_ms * 1e-3) / 1e9}
+        else:
+            meta_step = 2 * once + 2 * (4 + deg * (4 + 2 * es))
+            roofline["metadata"] = {
+                "step": "split", "nnz_per_node": deg, "csr_bytes_per_node": once,
+                "read_per_step_bytes_per_node": meta_step,
+                "achieved_with_metadata_gbs": (algo + meta_step * prob.n_nodes) / (dom_avg_ms * 1e-3) / 1e9}
     if multi:
         roofline["note"] = ("step of %d dependent launches rated as one: algorithmic bytes of the "
                             "step over the summed launch times" % len(per_step))

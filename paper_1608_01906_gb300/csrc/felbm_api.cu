@@ -296,13 +296,13 @@ static cudaError_t lat_smem_attr() {
 // One launch per step over the patches of a general triangle mesh; false
 // when its shared memory exceeds what a block can have (the four-launch
 // step then runs).
-template <typename T>
+template <typename T, bool LAP64>
 static bool patch_steps(felbm_state *s, int64_t n, cudaError_t &err) {
     const felbm_mesh *m = s->mesh;
     const HostCSR &H = m->host;
     const size_t smem = patch_smem<T>(H.rmax, H.r1max, H.r2max, H.r3max);
     if (smem > 227 * 1024) return false;
-    err = cudaFuncSetAttribute(k_patch_step<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    err = cudaFuncSetAttribute(k_patch_step<T, LAP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) {
         cudaGetLastError();
         return true;
@@ -320,13 +320,16 @@ static bool patch_steps(felbm_state *s, int64_t n, cudaError_t &err) {
     A.r3max = H.r3max;
     A.P = phys_of<T>(s->params);
     A.flag = s->d_flag;
+    A.ax64 = m->d_coef64;  // SoA: a_x, a_y, b_xx, b_xy, b_yy
+    A.ay64 = m->d_coef64 + m->host.col.size();
+    A.kappa64 = kappa64(s->params);
     const unsigned blocks = (unsigned)(H.pnbase.size() - 1);
     for (int64_t k = 0; k < n; ++k) {
         A.fin = reinterpret_cast<const T *>(s->f[s->cur]);
         A.fout = reinterpret_cast<T *>(s->f[s->cur ^ 1]);
         A.mom = k == n - 1 ? reinterpret_cast<T *>(s->mom) : nullptr;
         const int sl = prof_begin(s, 5);
-        k_patch_step<T><<<blocks, kPatch, smem, m->stream>>>(A);
+        k_patch_step<T, LAP64><<<blocks, kPatch, smem, m->stream>>>(A);
         prof_end(s, sl);
         s->cur ^= 1;
     }
@@ -336,9 +339,14 @@ static bool patch_steps(felbm_state *s, int64_t n, cudaError_t &err) {
 template <typename T>
 static int do_steps(felbm_state *s, int64_t n) {
     const felbm_mesh *m = s->mesh;
-    if (m->kind == 0 && m->patch_step && !lap_fp64(s)) {
+    if (m->kind == 0 && m->patch_step) {
         cudaError_t err = cudaSuccess;
-        if (patch_steps<T>(s, n, err)) return cuda_status(err);
+        bool done;
+        if constexpr (sizeof(T) == 4)
+            done = lap_fp64(s) ? patch_steps<T, true>(s, n, err) : patch_steps<T, false>(s, n, err);
+        else
+            done = patch_steps<T, false>(s, n, err);
+        if (done) return cuda_status(err);
     }
     if (m->kind == 1) {
         const bool l64 = lap_fp64(s);

@@ -38,6 +38,10 @@ struct PatchArgs {
     Phys<T> P;
     T *mom;  // 4N or nullptr
     int *flag;
+    // FP64 kappa lap rho term (FELBM_PARAM_LAP_FP64, LAP64 kernels only): the
+    // CSR's a coefficients in FP64 and kappa
+    const double *ax64, *ay64;
+    double kappa64;
 };
 
 // Shared-memory bytes of one block (layout of k_patch_step).
@@ -47,7 +51,8 @@ inline size_t patch_smem(int32_t rmax, int32_t r1max, int32_t r2max, int32_t r3m
            (size_t)r3max;
 }
 
-template <typename T>
+// LAP64: the kappa lap rho term of mu in FP64, as k_mu_lap64 forms it.
+template <typename T, bool LAP64>
 __global__ void __launch_bounds__(kPatch, sizeof(T) == 4 ? 3 : 1) k_patch_step(const __grid_constant__ PatchArgs<T> A) {
     extern __shared__ __align__(16) unsigned char psm[];
     const DevCSR<T> &m = A.m;
@@ -154,18 +159,31 @@ __global__ void __launch_bounds__(kPatch, sizeof(T) == 4 ? 3 : 1) k_patch_step(c
         const V2<T> gi = grd[r];
         const T gxi = gi.x, gyi = gi.y;
         T lap = T(0), kx = T(0), ky = T(0);
+        double lap64 = 0.0;
 #pragma unroll 4
         for (int32_t e = e0; e < e1; ++e) {
             const V2<T> gj = grd[lc[e - e0]];
             const T gxj = gj.x, gyj = gj.y;
-            const T ax = __ldg(m.ax + e), ay = __ldg(m.ay + e);
-            lap += ax * (gxj - gxi) + ay * (gyj - gyi);
+            T ax, ay;
+            if (LAP64) {
+                const double ax_ = __ldg(A.ax64 + e), ay_ = __ldg(A.ay64 + e);
+                lap64 += ax_ * ((double)gxj - (double)gxi) + ay_ * ((double)gyj - (double)gyi);
+                ax = (T)ax_;
+                ay = (T)ay_;
+            } else {
+                ax = __ldg(m.ax + e);
+                ay = __ldg(m.ay + e);
+                lap += ax * (gxj - gxi) + ay * (gyj - gyi);
+            }
             const T ddx = gxj - gxi, ddy = gyj - gyi;
             const T dxx = ddx * (gxj + gxi), dxy = gxj * ddy + gyi * ddx, dyy = ddy * (gyj + gyi);
             kx += ax * dyy - ay * dxy;
             ky += ay * dxx - ax * dxy;
         }
-        mu[r] = mu_bulk<T>(P, rho[r]) - P.kappa * lap;
+        if (LAP64)
+            mu[r] = (T)((double)mu_bulk<T>(P, rho[r]) - A.kappa64 * lap64);
+        else
+            mu[r] = mu_bulk<T>(P, rho[r]) - P.kappa * lap;
         if (r < n0) {
             kx_own = P.kappa * kx;
             ky_own = P.kappa * ky;

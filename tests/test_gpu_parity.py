@@ -411,3 +411,23 @@ def test_patch_step_equals_four_launch_step_bitwise(precision, mesh):
     for k in ("rho", "C", "u", "p", "totals"):
         assert np.array_equal(ma[k], mb[k]), k
     assert np.array_equal(ha, hb) and np.array_equal(ga, gb)
+
+
+def test_patch_step_with_fp64_laplacian_equals_four_launch_step_bitwise():
+    """FELBM_PARAM_LAP_FP64 on both general steps: the patch kernel's FP64
+    kappa lap rho term is k_mu_lap64's arithmetic, so the bits agree."""
+    xy, tri, box, tag = inputs.jittered_delaunay_mesh(48, 40, 0.25, seed=9)
+    rho0, u0, p0 = inputs.droplet_fields(xy, box, (24, 20), 10.0, 1.0, 1e-3, 12.0)
+    prm = configs.params(1.0, 1e-3, 0.01, 12.0, 0.0025, 0.1, 0.4)
+    out = []
+    for split in (False, True):
+        m_ = felbm.Mesh(xy, tri, box, tag, general=True, split_step=split)
+        st = felbm.State(m_, felbm.make_params(precision="fp32", lap_fp64=True, **prm), rho0, u0, p0)
+        st.step(25)
+        out.append((st.moments(), st.export()))
+        st.close()
+        m_.close()
+    (ma, (ha, ga)), (mb, (hb, gb)) = out
+    for k in ("rho", "C", "u", "p"):
+        assert np.array_equal(ma[k], mb[k]), k
+    assert np.array_equal(ha, hb) and np.array_equal(ga, gb)
