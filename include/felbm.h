@@ -396,6 +396,19 @@ int felbm_slab_unpack(felbm_state *state);
  * chain), CUDA. */
 int felbm_slab_exchange(felbm_state *const *slabs, int32_t n_slabs);
 
+/* Checked build (library compiled with FELBM_CHECKED, libfelbm_checked.so):
+ * the kernels bounds-check the indices they gather with -- node and slot
+ * indices of the CSR, lattice and patch neighbours, shared-memory region
+ * indices, the cp.async fill plans, the TMA boxes' 16-byte x rule, the slab
+ * halo copies -- and, instead of an out-of-range access, skip it and record
+ * a bit of a device status word (no assert, no trap).  This call waits for
+ * the device, reads and clears that word: *bits = 1 a node or slot index out
+ * of range, 2 a shared-memory index out of range, 4 a TMA coordinate off its
+ * rule (that tile loaded by cp.async), 8 a slab copy out of range;
+ * *checked_build = 1 in the checked build.  The regular build returns 0 for
+ * both (its checks compile away).  Errors: INVALID_ARG (NULL pointer). */
+int felbm_check_status(int32_t *checked_build, int32_t *bits);
+
 /* Short static description of a status code. */
 const char *felbm_status_string(int status);
 

@@ -15,6 +15,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libfelbm.so")
 BUILD = os.path.join(HERE, "_build")
+# the checked build: every kernel bounds-checks its gathered indices
+OUT_CHECKED = os.path.join(HERE, "libfelbm_checked.so")
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xptxas", "-warn-spills"]
@@ -36,24 +39,27 @@ def _deps():
         os.path.join(HERE, "..", "include", "felbm.h")]
 
 
-def needs_build() -> bool:
-    if not os.path.exists(OUT):
+def needs_build(out: str = OUT) -> bool:
+    if not os.path.exists(out):
         return True
-    t = os.path.getmtime(OUT)
+    t = os.path.getmtime(out)
     return any(os.path.getmtime(d) > t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not needs_build():
-        return OUT
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Compile libfelbm.so (checked: libfelbm_checked.so with FELBM_CHECKED)."""
+    out, bdir = (OUT_CHECKED, BUILD_CHECKED) if checked else (OUT, BUILD)
+    if not force and not needs_build(out):
+        return out
+    os.makedirs(bdir, exist_ok=True)
     nvcc = _nvcc()
     objs = []
     cmds = []
+    extra = ["-DFELBM_CHECKED"] if checked else []
     for src in _sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
-        cmds.append([nvcc, *ARCH, *FLAGS, "-c", src, "-o", obj])
+        cmds.append([nvcc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -67,10 +73,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
         for lg in logs:
             if lg.strip():
                 print(lg)
-    tmp = OUT + ".tmp"
+    tmp = out + ".tmp"
     run([nvcc, *ARCH, "-shared", "-o", tmp, *objs])
-    os.replace(tmp, OUT)
-    return OUT
+    os.replace(tmp, out)
+    return out
 
 
 if __name__ == "__main__":

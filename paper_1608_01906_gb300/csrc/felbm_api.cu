@@ -468,10 +468,23 @@ __global__ void k_wait_selftest(int *flag, uint64_t limit_ns) {
     if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(flag, 4);
 }
 
+FELBM_CHECK_READER(check_bits_api)
+
 }  // namespace felbm
 
 // ============================================================================
 extern "C" {
+
+int felbm_check_status(int32_t *checked_build, int32_t *bits) {
+    if (!checked_build || !bits) return FELBM_ERR_INVALID_ARG;
+#ifdef FELBM_CHECKED
+    *checked_build = 1;
+#else
+    *checked_build = 0;
+#endif
+    *bits = (int32_t)(check_bits_api() | check_bits_api3() | check_bits_batch() | check_bits_slab());
+    return FELBM_OK;
+}
 
 int felbm_wait_selftest(felbm_state *s, int64_t limit_ns) {
     if (!s || limit_ns < 1 || limit_ns > 2000000000LL) return FELBM_ERR_INVALID_ARG;

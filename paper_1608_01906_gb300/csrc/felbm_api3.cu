@@ -311,6 +311,8 @@ int import3(felbm_state *s, const double *hbar, const double *gbar) {
     return FELBM_OK;
 }
 
+FELBM_CHECK_READER(check_bits_api3)
+
 }  // namespace felbm
 
 using namespace felbm;

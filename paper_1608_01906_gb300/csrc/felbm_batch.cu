@@ -179,6 +179,8 @@ static Phys<T> phys_b(const felbm_params &p) {
     return P;
 }
 
+FELBM_CHECK_READER(check_bits_batch)
+
 }  // namespace felbm
 
 using namespace felbm;

@@ -10,6 +10,42 @@
 
 namespace felbm {
 
+// ---- checked build (FELBM_CHECKED) -----------------------------------------
+// Kernels bounds-check the indices they gather with and record a violation
+// as a bit of a device status word (no assert, no trap: the access is
+// skipped); felbm_check_status reads and clears it.  Bits: 1 a gathered node
+// or slot index out of range, 2 a shared-memory (region) index out of range,
+// 4 a TMA box coordinate off its 16-byte rule (the tile then loads by
+// cp.async), 8 a slab halo copy out of range.  Without FELBM_CHECKED every
+// check is the constant true.  Each translation unit holds its own status
+// word (no relocatable device code) and a reader, check_bits_<unit>().
+#ifdef __CUDACC__
+#ifdef FELBM_CHECKED
+static __device__ unsigned g_check_bits;
+__device__ __forceinline__ bool chk_idx(long long i, long long n, unsigned bit) {
+    if (i >= 0 && i < n) return true;
+    atomicOr(&g_check_bits, bit);
+    return false;
+}
+#define FELBM_CHECK_READER(name)                                                  \
+    unsigned name() {                                                             \
+        unsigned v = 0, z = 0;                                                    \
+        cudaDeviceSynchronize();                                                  \
+        if (cudaMemcpyFromSymbol(&v, g_check_bits, sizeof v) != cudaSuccess) v = ~0u; \
+        cudaMemcpyToSymbol(g_check_bits, &z, sizeof z);                           \
+        return v;                                                                 \
+    }
+#else
+__device__ __forceinline__ constexpr bool chk_idx(long long, long long, unsigned) { return true; }
+#define FELBM_CHECK_READER(name) \
+    unsigned name() { return 0u; }
+#endif
+#endif
+unsigned check_bits_api();
+unsigned check_bits_api3();
+unsigned check_bits_batch();
+unsigned check_bits_slab();
+
 // ---- host-side mesh preprocessing (felbm_mesh.cu) -------------------------
 
 // Assembled per-node operators in the internal (reverse Cuthill-McKee) order.
@@ -142,9 +178,11 @@ struct DevCSR {
     template <typename Fn>
     __device__ __forceinline__ void for_each(int32_t i, Fn &&fn) const {
         const int32_t p1 = __ldg(rowptr + i + 1);
-        for (int32_t p = __ldg(rowptr + i); p < p1; ++p)
-            fn(__ldg(col + p), __ldg(ax + p), __ldg(ay + p), __ldg(bxx + p), __ldg(bxy + p),
-               __ldg(byy + p));
+        for (int32_t p = __ldg(rowptr + i); p < p1; ++p) {
+            const int32_t j = __ldg(col + p);
+            if (!chk_idx(j, n, 1u)) continue;
+            fn(j, __ldg(ax + p), __ldg(ay + p), __ldg(bxx + p), __ldg(bxy + p), __ldg(byy + p));
+        }
     }
     __device__ __forceinline__ int tag_of(int32_t i) const { return tag ? (int)tag[i] : 0; }
     // population storage: slot of node i, slots per population array
@@ -188,6 +226,7 @@ struct DevLattice {
             yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
             int32_t xx = x + lat_dx(o);
             xx = xx < 0 ? xx + nx : (xx >= nx ? xx - nx : xx);
+            if (!chk_idx(xx + nx * yy, n, 1u)) continue;
             fn(xx + nx * yy, c[kind][o][0], c[kind][o][1], c[kind][o][2], c[kind][o][3],
                c[kind][o][4]);
         }

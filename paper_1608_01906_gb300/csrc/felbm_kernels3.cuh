@@ -83,10 +83,12 @@ struct DevCSR3 {
     __device__ __forceinline__ void for_each(int32_t i, Fn &&fn) const {
         const int32_t p1 = __ldg(rowptr + i + 1);
         for (int32_t p = __ldg(rowptr + i); p < p1; ++p) {
+            const int32_t j = __ldg(col + p);
+            if (!chk_idx(j, n, 1u)) continue;
             T cf[9];
 #pragma unroll
             for (int k = 0; k < 9; ++k) cf[k] = __ldg(c[k] + p);
-            fn(__ldg(col + p), cf);
+            fn(j, cf);
         }
     }
     template <int K, typename Fn>
@@ -166,7 +168,8 @@ struct DevLattice3 {
         nbrs(i, j);
         const int kd = K >= 0 ? K : kind_of(i);
 #pragma unroll
-        for (int o = 0; o < 14; ++o) fn(j[o], k.a[kd][o]);
+        for (int o = 0; o < 14; ++o)
+            if (chk_idx(j[o], n, 1u)) fn(j[o], k.a[kd][o]);
     }
     template <int K, typename Fn>
     __device__ __forceinline__ void for_each_pair(int32_t i, T, Fn &&fn) const {
@@ -174,7 +177,8 @@ struct DevLattice3 {
         nbrs(i, j);
         const int kd = K >= 0 ? K : kind_of(i);
 #pragma unroll
-        for (int o = 0; o < 14; ++o) fn(j[o], k.pc[kd][o]);
+        for (int o = 0; o < 14; ++o)
+            if (chk_idx(j[o], n, 1u)) fn(j[o], k.pc[kd][o]);
     }
 #endif
 };

@@ -252,6 +252,13 @@ __device__ __forceinline__ FillPlan fill_plan(int tid, int nthreads, int gx0, in
             f.src[t] = inside ? gx + pitch * gy : 0;
             f.ok[t] = inside;
             f.dst[t] = r * W + col;
+            // (checked build: a slot outside the window or the arrays copies
+            // nothing and zero-fills the window's first element)
+            if (!chk_idx(f.src[t], (long long)pitch * ny, 1u) || !chk_idx(f.dst[t], W * H, 2u)) {
+                f.src[t] = 0;
+                f.dst[t] = 0;
+                f.ok[t] = 0;
+            }
             f.n = t + 1;
         }
     }
@@ -1009,8 +1016,13 @@ __device__ __forceinline__ void lat_block_init(StepSmem<T> &S) {
 template <typename T>
 __device__ __forceinline__ bool tile_tma(const LatArgs<T> &A, int bx, int by, const unsigned char *dsm) {
     const int x0 = bx * kLTX, y0 = A.ylo + by * kLTY;
+    // the boxes' x coordinates (4-byte words) on 16-byte boundaries (by
+    // construction; the checked build verifies it and falls back to cp.async)
+    constexpr int WPN = (int)sizeof(V2<T>) / 4, SPN = (int)sizeof(T) / 4;
+    const bool aligned = ((x0 - PairTile<T, kHD>::XH) * WPN) % 4 == 0 && ((x0 - 4) * SPN) % 4 == 0 &&
+                         ((x0 - PairTile<T, 1>::XH) * WPN) % 4 == 0;
     return A.tmap && tile_interior(A, x0, y0) && tile_unwrapped(x0, y0, A.nx, A.ny) &&
-           (smem_u32(dsm) & 127u) == 0;
+           (smem_u32(dsm) & 127u) == 0 && chk_idx(aligned ? 0 : -1, 1, 4u);
 }
 
 // One tile of a block's walk (pp carries the TMA barrier phases and whether

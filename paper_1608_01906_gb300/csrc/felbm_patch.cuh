@@ -75,6 +75,7 @@ __global__ void __launch_bounds__(kPatch, sizeof(T) == 4 ? 3 : 1) k_patch_step(c
     // 0. the region's populations (own nodes first: contiguous)
     for (int32_t r = tid; r < nreg; r += kPatch) {
         const int32_t g = A.node[base + r];
+        if (!chk_idx(g, m.n, 1u) || !chk_idx(r, rmax, 2u)) continue;
 #pragma unroll
         for (int q = 0; q < 4; ++q) hP[q * rmax + r] = hb[q * np + g];
         h0[r] = A.fin[g];
@@ -105,6 +106,7 @@ __global__ void __launch_bounds__(kPatch, sizeof(T) == 4 ? 3 : 1) k_patch_step(c
 #pragma unroll 4
         for (int32_t e = e0; e < e1; ++e) {
             const int j = lc[e - e0];
+            if (!chk_idx(j, nreg, 2u)) continue;
             const T ax = __ldg(m.ax + e), ay = __ldg(m.ay + e);
             const T hbxx = hdt * __ldg(m.bxx + e), hbxy = hdt * __ldg(m.bxy + e), hbyy = hdt * __ldg(m.byy + e);
 #pragma unroll
@@ -142,7 +144,9 @@ __global__ void __launch_bounds__(kPatch, sizeof(T) == 4 ? 3 : 1) k_patch_step(c
         T sx = T(0), sy = T(0);
 #pragma unroll 4
         for (int32_t e = e0; e < e1; ++e) {
-            const T d = rho[lc[e - e0]] - fi;
+            const int j = lc[e - e0];
+            if (!chk_idx(j, n3, 2u)) continue;
+            const T d = rho[j] - fi;
             sx += __ldg(m.ax + e) * d;
             sy += __ldg(m.ay + e) * d;
         }
@@ -162,7 +166,9 @@ __global__ void __launch_bounds__(kPatch, sizeof(T) == 4 ? 3 : 1) k_patch_step(c
         double lap64 = 0.0;
 #pragma unroll 4
         for (int32_t e = e0; e < e1; ++e) {
-            const V2<T> gj = grd[lc[e - e0]];
+            const int j = lc[e - e0];
+            if (!chk_idx(j, n2, 2u)) continue;
+            const V2<T> gj = grd[j];
             const T gxj = gj.x, gyj = gj.y;
             T ax, ay;
             if (LAP64) {
@@ -202,7 +208,9 @@ __global__ void __launch_bounds__(kPatch, sizeof(T) == 4 ? 3 : 1) k_patch_step(c
         T sx = T(0), sy = T(0);
 #pragma unroll 4
         for (int32_t e = e0; e < e1; ++e) {
-            const T d = mu[lc[e - e0]] - fi;
+            const int j = lc[e - e0];
+            if (!chk_idx(j, n1, 2u)) continue;
+            const T d = mu[j] - fi;
             sx += __ldg(m.ax + e) * d;
             sy += __ldg(m.ay + e) * d;
         }
@@ -220,6 +228,7 @@ __global__ void __launch_bounds__(kPatch, sizeof(T) == 4 ? 3 : 1) k_patch_step(c
 #pragma unroll 4
         for (int32_t e = e0; e < e1; ++e) {
             const int j = lc[e - e0];
+            if (!chk_idx(j, n1, 2u)) continue;
             const T ax = __ldg(m.ax + e), ay = __ldg(m.ay + e);
             const T hbxx = hdt * __ldg(m.bxx + e), hbxy = hdt * __ldg(m.bxy + e), hbyy = hdt * __ldg(m.byy + e);
 #pragma unroll

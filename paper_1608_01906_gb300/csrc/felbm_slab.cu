@@ -49,6 +49,7 @@ __global__ void k_slab_halo(T *f, size_t np, int pitch, int r0, int r1, T *m0, T
             const size_t q = (m - 10 * p4) / (2 * p4), k = (m - 10 * p4) - q * 2 * p4;
             off = 10 * np + 2 * np * q + 2 * row + k;
         }
+        if (!chk_idx(off, 18 * np - CE + 1, 8u)) continue;
         uint4 *msg = reinterpret_cast<uint4 *>((side ? m1 : m0) + m);
         uint4 *pop = reinterpret_cast<uint4 *>(f + off);
         if (PACK)
@@ -97,6 +98,8 @@ static int slab_pack_unpack(felbm_state *s, bool pack) {
         slab_copy<float>(s, pack);
     return cuda_status(cudaGetLastError());
 }
+
+FELBM_CHECK_READER(check_bits_slab)
 
 }  // namespace felbm
 

@@ -13,7 +13,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libfelbm.so")
+# FELBM_LIB names another build of the library (the checked build,
+# libfelbm_checked.so) for the process
+LIB_PATH = os.environ.get("FELBM_LIB") or os.path.join(_HERE, "libfelbm.so")
 
 FELBM_OK = 0
 FELBM_ERR_INVALID_ARG = -1
@@ -41,7 +43,7 @@ EXPORTED = [
     "felbm_batch_create", "felbm_batch_step", "felbm_batch_sync", "felbm_batch_info",
     "felbm_batch_destroy", "felbm_totals_nalloc", "felbm_alu_peak", "felbm_wait_selftest",
     "felbm_mesh_slab", "felbm_slab_info", "felbm_slab_halo", "felbm_slab_pack", "felbm_slab_unpack",
-    "felbm_slab_exchange",
+    "felbm_slab_exchange", "felbm_check_status",
 ]
 FELBM_BATCH_AUTOTUNE = 0x1
 FELBM_PROFILE_KINDS = 8
@@ -135,6 +137,8 @@ def _declare_extra(lib):
         lib.felbm_totals_nalloc.argtypes = [vp, vp, vp, vp, i64, i32, vp, vp]
     lib.felbm_alu_peak.restype = C.c_int
     lib.felbm_alu_peak.argtypes = [C.c_int, vp]
+    lib.felbm_check_status.restype = C.c_int
+    lib.felbm_check_status.argtypes = [vp, vp]
     lib.felbm_mesh_slab.restype = C.c_int
     lib.felbm_mesh_slab.argtypes = [vp, i64, i64, vp, pp]
     lib.felbm_slab_info.restype = C.c_int
@@ -405,6 +409,14 @@ class State:
             self.close()
         except Exception:
             pass
+
+
+def check_status():
+    """(checked build?, bits recorded by the kernels' bounds checks since
+    the last call); reading clears the bits."""
+    cb, bits = C.c_int32(), C.c_int32()
+    _check(load().felbm_check_status(C.byref(cb), C.byref(bits)), "felbm_check_status")
+    return bool(cb.value), bits.value
 
 
 def slab_exchange(states):
