@@ -649,6 +649,7 @@ void felbm_mesh_destroy(felbm_mesh *m) { mesh_free(m); }
 
 int felbm_state_init(const felbm_mesh *mesh, const felbm_params *params, const double *rho0,
                      const double *u0, const double *p0, felbm_state **out) {
+    felbm::NvtxRange nvtx_range("felbm_state_init");
     if (!mesh || !params || !rho0 || !out) return FELBM_ERR_INVALID_ARG;
     if (!params_ok(params)) return FELBM_ERR_INVALID_ARG;
     if (mesh->kind >= 2) return state_init3(mesh, params, rho0, u0, p0, out);
@@ -720,6 +721,7 @@ int felbm_state_init(const felbm_mesh *mesh, const felbm_params *params, const d
 }
 
 int felbm_step(felbm_state *s, int64_t n_steps) {
+    felbm::NvtxRange nvtx_range("felbm_step");
     if (!s || n_steps < 0) return FELBM_ERR_INVALID_ARG;
     if (n_steps == 0) return FELBM_OK;
     if (s->mesh->kind >= 2) {
@@ -747,6 +749,7 @@ int felbm_state_sync(felbm_state *s) {
 }
 
 int felbm_moments_get(felbm_state *s, double *rho, double *C, double *u, double *p, double totals[3]) {
+    felbm::NvtxRange nvtx_range("felbm_moments_get");
     if (!s) return FELBM_ERR_INVALID_ARG;
     if (!s->have_moments) return FELBM_ERR_INVALID_ARG;
     if (s->mesh->kind >= 2) {

@@ -490,6 +490,7 @@ static int autotune(felbm_batch *b, int trial, int64_t *used) {
 }
 
 int felbm_batch_step(felbm_batch *b, int64_t n_steps) {
+    felbm::NvtxRange nvtx_range("felbm_batch_step");
     if (!b || n_steps < 0) return FELBM_ERR_INVALID_ARG;
     if (n_steps == 0) return FELBM_OK;
     int st0 = sync_descriptors(b);

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <vector>
@@ -41,6 +42,14 @@ __device__ __forceinline__ constexpr bool chk_idx(long long, long long, unsigned
     unsigned name() { return 0u; }
 #endif
 #endif
+// NVTX range around an entry point (seen by nsys / ncu; a no-op otherwise).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 unsigned check_bits_api();
 unsigned check_bits_api3();
 unsigned check_bits_batch();

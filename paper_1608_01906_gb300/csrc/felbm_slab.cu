@@ -170,6 +170,7 @@ int felbm_slab_pack(felbm_state *s) { return slab_pack_unpack(s, true); }
 int felbm_slab_unpack(felbm_state *s) { return slab_pack_unpack(s, false); }
 
 int felbm_slab_exchange(felbm_state *const *slabs, int32_t n_slabs) {
+    felbm::NvtxRange nvtx_range("felbm_slab_exchange");
     if (!slabs || n_slabs < 1) return FELBM_ERR_INVALID_ARG;
     const felbm_state *s0 = slabs[0];
     if (!s0 || !is_slab(s0->mesh)) return FELBM_ERR_INVALID_ARG;
