@@ -279,10 +279,13 @@ void felbm_batch_destroy(felbm_batch *batch);
  *   6-7 unused. */
 #define FELBM_PROFILE_KINDS 8
 
-/* on != 0: every kernel launched by later felbm_step calls is bracketed by a
- * pair of CUDA events on the state's stream, for the first 4096 launches after
- * the call (later launches are counted, not timed).  on == 0 stops
- * recording.  Errors: INVALID_ARG, OOM (event creation), CUDA. */
+/* on >= 1: every on-th launch of each kernel kind issued by later
+ * felbm_step calls (the first, the (on+1)-th, ...) is bracketed by a pair of
+ * CUDA events on the state's stream, up to 4096 timed launches after the
+ * call; the others are counted, not timed (a stride spreads the timed
+ * launches over a long run and keeps the event records out of most
+ * launches).  on == 0 stops recording.  Errors: INVALID_ARG (NULL, on < 0),
+ * OOM (event creation), CUDA. */
 int felbm_profile_enable(felbm_state *state, int on);
 
 /* Synchronise, then report per kernel kind the summed device milliseconds of

@@ -117,7 +117,8 @@ static constexpr size_t kProfMaxLaunches = 4096;
 
 int prof_begin(felbm_state *s, int kind) {
     s->launches[kind]++;
-    if (!s->prof_on || s->prof_used >= kProfMaxLaunches) return -1;
+    if (!s->prof_on || (s->prof_seen[kind]++ % s->prof_stride) != 0 || s->prof_used >= kProfMaxLaunches)
+        return -1;
     const size_t slot = s->prof_used++;
     s->prof_kind[slot] = kind;
     cudaEventRecord(s->prof_ev[2 * slot], s->mesh->stream);
@@ -831,7 +832,7 @@ void felbm_state_destroy(felbm_state *s) {
 }
 
 int felbm_profile_enable(felbm_state *s, int on) {
-    if (!s) return FELBM_ERR_INVALID_ARG;
+    if (!s || on < 0) return FELBM_ERR_INVALID_ARG;
     if (on && s->prof_ev.empty()) {
         try {
             s->prof_ev.assign(2 * kProfMaxLaunches, nullptr);
@@ -845,8 +846,10 @@ int felbm_profile_enable(felbm_state *s, int on) {
         }
     }
     s->prof_on = on != 0;
+    s->prof_stride = on > 0 ? on : 1;
     s->prof_used = 0;
     for (auto &c : s->launches) c = 0;
+    for (auto &c : s->prof_seen) c = 0;
     return FELBM_OK;
 }
 

@@ -371,6 +371,8 @@ struct felbm_state {
     int64_t steps_done = 0;
     // profiling: event pairs around launches (felbm_profile_enable)
     bool prof_on = false;
+    int prof_stride = 1;                  // time every prof_stride-th launch of a kind
+    int64_t prof_seen[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     std::vector<cudaEvent_t> prof_ev;     // 2 per timed launch
     std::vector<int> prof_kind;           // kind of each timed launch
     size_t prof_used = 0;

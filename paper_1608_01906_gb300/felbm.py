@@ -386,7 +386,9 @@ class State:
         _check(felbm_state_import(self.handle, h, g), "felbm_state_import")
 
     def profile_enable(self, on=True):
-        _check(load().felbm_profile_enable(self.handle, 1 if on else 0), "felbm_profile_enable")
+        # on: True / False, or the stride of timed launches (every on-th of a kind)
+        _check(load().felbm_profile_enable(self.handle, int(on) if not isinstance(on, bool) else (1 if on else 0)),
+               "felbm_profile_enable")
 
     def profile_read(self):
         """Per kernel kind: (summed ms of timed launches, timed, issued)."""

@@ -431,3 +431,17 @@ def test_patch_step_with_fp64_laplacian_equals_four_launch_step_bitwise():
     for k in ("rho", "C", "u", "p"):
         assert np.array_equal(ma[k], mb[k]), k
     assert np.array_equal(ha, hb) and np.array_equal(ga, gb)
+
+
+def test_profile_stride_times_every_kth_launch():
+    prob = _droplet(32, 32, 8.0)
+    mesh = felbm.Mesh(prob.xy, prob.tri, prob.box, prob.tag)
+    st = felbm.State(mesh, felbm.make_params(precision="fp32", **prob.params), prob.rho0)
+    st.profile_enable(3)
+    st.step(10)
+    ms, timed, issued = st.profile_read()["k_lattice_step"]
+    assert issued == 10 and timed == 4 and ms > 0.0  # launches 0, 3, 6 and 9
+    with pytest.raises(felbm.FelbmError):
+        st.profile_enable(-1)
+    st.close()
+    mesh.close()
