@@ -522,6 +522,15 @@ def main():
     if multi:
         dom_name = "+".join(per_step)
         dom_avg_ms = sum(v[0] / max(v[1], 1) for v in per_step.values())
+    # the event-sampled average of the dominant kernel's timed launches; when
+    # it is the only kernel the region launched, its average launch duration
+    # is also the region's event time over its launches (no event records
+    # between those launches), and that figure is used
+    dom_event_ms = dom_avg_ms
+    issued = {k: v[2] for k, v in prof.items() if v[2]}
+    only_kernel = len(issued) == 1 and not multi
+    if only_kernel:
+        dom_avg_ms = ms / issued[dom_name]
     peak, peak_kind = hbm_peak()
     # measured ALU ceilings (after the timed region: a few ms of FMA streams)
     alu = {}
@@ -546,7 +555,10 @@ def main():
             traffic = ent["bytes_per_launch"]
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "kernel": dom_name,
-                "kernel_ms": dom_avg_ms, "peak_source": peak_kind + " copy bandwidth",
+                "kernel_ms": dom_avg_ms, "kernel_ms_events": dom_event_ms,
+                "kernel_ms_source": ("timed region over launches (the only kernel launched)" if only_kernel
+                                     else "CUDA events around its sampled launches"),
+                "peak_source": peak_kind + " copy bandwidth",
                 "step_gbs": algo * args.steps / (ms * 1e-3) / 1e9,
                 "kernel_share": dom_ms / max(sum(v[0] for v in prof.values()), 1e-12)}
     if kind == 0:
@@ -611,6 +623,8 @@ def main():
         s64.close()
         per64 = {k: v for k, v in pr64.items() if v[2] >= args.fp64_steps}
         k64_ms = sum(v[0] / max(v[1], 1) for v in per64.values())
+        if len([v for v in pr64.values() if v[2]]) == 1:  # the only kernel: region time per launch
+            k64_ms = ms64 / args.fp64_steps
         algo64 = ALGO_BYTES_PER_NODE["fp64"] * (19 if dim == 3 else 9) // 9 * prob.n_nodes
         hbm64 = algo64 / (k64_ms * 1e-3) / 1e9
         fp64 = {"value": job_rate(1, prob.n_nodes, args.fp64_steps, ms64 * 1e-3), "unit": UNIT,
