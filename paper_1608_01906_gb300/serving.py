@@ -56,6 +56,7 @@ class Result:
     nodes: int
     moments: dict
     status: str = "ok"      # "ok" or "diverged"
+    mass_drift: float = 0.0  # |M_end - M_0| / M_0 of the FP64 mass total (completed runs)
 
     @property
     def latency(self):
@@ -179,14 +180,17 @@ class Server:
         st = felbm.State(mesh, felbm.make_params(precision=self.precision, **prob.params),
                          prob.rho0, prob.u0, prob.p0)
         self.used += run_bytes(req.side, self.precision)
-        self.active.append({"req": req, "state": st, "done": 0, "admitted": now})
+        # the FP64 mass total at admission, for the mass-drift check at the end
+        mass0 = float(st.moments()["totals"][0])
+        self.active.append({"req": req, "state": st, "done": 0, "admitted": now, "mass0": mass0})
         self.dirty = True
 
     def _retire(self, slot, now, status="ok"):
         req = slot["req"]
         m = slot["state"].moments() if status == "ok" else {}
+        drift = abs(float(m["totals"][0]) - slot["mass0"]) / abs(slot["mass0"]) if m else 0.0
         self.results.append(Result(req.rid, req.arrival, slot["admitted"], now, slot["done"],
-                                   req.nodes, m, status))
+                                   req.nodes, m, status, drift))
         slot["state"].close()
         self._release_mesh(req.side)
         self.used -= run_bytes(req.side, self.precision)
@@ -245,6 +249,9 @@ class Server:
         self.meshes.clear()
 
 
+MASS_DRIFT_TOL = 1e-5  # relative FP64 mass-total change over a served run
+
+
 def serve(requests, budget_bytes, chunk=200, stream=None, time_scale=1.0, autotune=True,
           max_wall=None):
     """Serve a request stream in real time.  time_scale stretches arrival
@@ -288,5 +295,10 @@ def serve(requests, budget_bytes, chunk=200, stream=None, time_scale=1.0, autotu
         "aggregate_mnups": node_steps / wall / 1e6 if wall > 0 else 0.0,
         "p50_s": float(np.percentile(lat, 50)) if len(lat) else None,
         "p99_s": float(np.percentile(lat, 99)) if len(lat) else None,
+        # mass-drift check: the collision keeps each node's mass to one
+        # rounding, so a completed run whose total drifted beyond
+        # MASS_DRIFT_TOL points at a fault
+        "max_mass_drift": max((r.mass_drift for r in done), default=0.0),
+        "mass_drift_flagged": sum(r.mass_drift > MASS_DRIFT_TOL for r in done),
     }
     return results, stats

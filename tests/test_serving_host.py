@@ -1,6 +1,7 @@
 """Host-side logic of the serving loop (no GPU): the request stream and the
 scheduler's admission, chunking and retirement, with the device calls faked."""
 import numpy as np
+import pytest
 
 from paper_1608_01906_gb300 import serving
 
@@ -22,7 +23,7 @@ class FakeState:
         self.closed = False
 
     def moments(self):
-        return {"rho": np.zeros(1)}
+        return {"rho": np.zeros(1), "totals": np.array([1.0, 0.0, 0.0])}
 
     def close(self):
         self.closed = True
@@ -145,3 +146,37 @@ def test_budget_counts_meshes_and_batch_memory(monkeypatch):
     srv.active[0]["done"] = 100
     srv.retire_finished(1.0)
     assert srv.used == 0 and not srv.meshes
+
+
+def test_mass_drift_is_measured_and_flagged(monkeypatch):
+    """Each completed run reports the relative change of its FP64 mass total
+    from admission to completion; runs beyond MASS_DRIFT_TOL are counted."""
+    class MState(FakeState):
+        count = 0
+
+        def __init__(self, *a, **k):
+            super().__init__()
+            self.rid = MState.count
+            MState.count += 1
+            self.calls = 0
+
+        def moments(self):
+            self.calls += 1
+            drift = 3e-5 if (self.rid == 1 and self.calls > 1) else 0.0
+            return {"rho": np.zeros(1), "totals": np.array([2.0 * (1.0 + drift), 0.0, 0.0])}
+
+    monkeypatch.setattr(serving.felbm, "Mesh", FakeMesh)
+    monkeypatch.setattr(serving.felbm, "State", MState)
+    monkeypatch.setattr(serving.felbm, "Batch", FakeBatch)
+    monkeypatch.setattr(serving, "problem_for", lambda req: type(
+        "P", (), {"xy": None, "tri": None, "box": None, "tag": None, "rho0": None, "u0": None,
+                  "p0": None, "params": {"rho_l": 1.0, "rho_v": 0.1, "sigma": 0.01, "xi": 4.0,
+                                         "tau_l": 0.1, "tau_v": 0.1, "dt": 0.5,
+                                         "gravity": (0.0, 0.0)}})())
+    reqs = [serving.Request(k, 0.0, 64, 10.0, 0.3, 50) for k in range(3)]
+    budget = 3 * serving.run_bytes(64) + serving.mesh_bytes(64) + serving.BATCH_FIXED_BYTES
+    results, stats = serving.serve(reqs, budget, chunk=50, autotune=False)
+    by = {r.rid: r for r in results}
+    assert stats["completed"] == 3
+    assert by[1].mass_drift == pytest.approx(3e-5) and by[0].mass_drift == 0.0
+    assert stats["mass_drift_flagged"] == 1 and stats["max_mass_drift"] == pytest.approx(3e-5)
