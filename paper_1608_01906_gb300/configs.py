@@ -13,8 +13,8 @@ restated in 2-D.  Readings fixed here (documented in the design notes):
   with tau << 1 (over-relaxation) dt = 0.5 diverges there.
 * rho_l = 1, rho_v = rho_l / ratio; sigma = 0.01.
 * Interface width xi (mesh units): 4 where stated (64x64 droplet, ratio 10);
-  12 for the ratio-1000 Delaunay droplet and 16 for the batched / served
-  droplets (ratios up to 1000).  The P1 scheme cancels the ideal-gas
+  12 for the ratio-1000 Delaunay droplet and 24 for the batched / served
+  droplets (ratios up to 1000; see the last item).  The P1 scheme cancels the ideal-gas
   pressure of the order-parameter streaming only to O(h^2 d^4 rho); on
   interfaces of 4 to 8 mesh units that residual outgrows the capillary
   forces and ratios >= 30 diverge, so the width is the smallest tried
@@ -148,3 +148,39 @@ def c4_batched(count=64, seed=1609, lo=32, hi=512):
         out.append(droplet_structured(side, rfrac * side, ratio, DROPLET_XI, 0.01, 0.1, 0.1, 0.5, 0,
                                       "fp32", "batch_%02d_%d" % (k, side)))
     return out
+
+
+# ---- the workloads as JSON files (workloads/*.json) -----------------------
+WORKLOAD_DIR = __import__("os").path.join(__import__("os").path.dirname(__file__), "workloads")
+
+
+def load_workload(path_or_name, capacity_mnups=None):
+    """Build a workload from its JSON description (a path, or a file name in
+    workloads/ without .json).  The file names a builder of this module (or
+    serving.poisson_stream) and its arguments; it also records the physical
+    parameters the builder yields, for the reader (tests check they agree).
+    Returns a Problem (c1-c3), a list of Problems (c4), or the request list
+    of the serving stream (c5, whose arrival rate is rate_fraction x the
+    batched capacity in MNUPS: pass capacity_mnups)."""
+    import json
+    import math
+    import os
+
+    path = path_or_name if os.path.exists(str(path_or_name)) else os.path.join(
+        WORKLOAD_DIR, str(path_or_name) + ".json")
+    with open(path) as f:
+        w = json.load(f)
+    args = dict(w.get("args", {}))
+    if w["builder"] == "serving.poisson_stream":
+        from . import serving
+
+        if capacity_mnups is None:
+            raise ValueError("the serving workload needs capacity_mnups")
+        lo, hi = args["side"]
+        mean_nodes = (hi * hi - lo * lo) / (2.0 * math.log(hi / lo))  # E[side^2], log-uniform
+        mean_work = mean_nodes * (args["steps"][0] + args["steps"][1]) / 2.0
+        rate = w["rate_fraction"] * capacity_mnups * 1e6 / mean_work
+        return serving.poisson_stream(w["requests"], rate, seed=args["seed"], side=tuple(args["side"]),
+                                      ratio=tuple(args["ratio"]), steps=tuple(args["steps"]),
+                                      radius=tuple(args["radius"]))
+    return globals()[w["builder"]](**args)
