@@ -445,3 +445,34 @@ def test_profile_stride_times_every_kth_launch():
         st.profile_enable(-1)
     st.close()
     mesh.close()
+
+
+@pytest.mark.parametrize("path", ["lattice", "patch", "split", "tet"])
+def test_uniform_state_is_stationary_on_every_path(path):
+    """The degenerate case of no interface: a uniform density moving at a
+    uniform velocity on a periodic mesh stays exactly that (no gradients, no
+    force; the collision returns the equilibria).  FP64, 50 steps, every
+    kernel path: the structured lattice step, the general patch and
+    four-launch steps, and the tetrahedral lattice."""
+    prm = configs.params(rho_l=1.0, rho_v=0.1, dt=0.4)
+    if path == "tet":
+        xy, tri, box, tag = inputs.structured_tet_mesh(8, 6, 5)
+        prm = dict(prm, gravity=(0.0, 0.0, 0.0))
+        u = np.tile([0.02, -0.01, 0.015], (len(xy), 1))
+    elif path == "lattice":
+        xy, tri, box, tag = inputs.structured_mesh(40, 24)
+        u = np.tile([0.02, -0.01], (len(xy), 1))
+    else:
+        xy, tri, box, tag = inputs.jittered_delaunay_mesh(24, 20, 0.25, seed=6)
+        u = np.tile([0.02, -0.01], (len(xy), 1))
+    rho0 = np.full(len(xy), 0.55)
+    mesh = felbm.Mesh(xy, tri, box, tag, general=path in ("patch", "split"), split_step=path == "split",
+                      patch_step=path == "patch")
+    st = felbm.State(mesh, felbm.make_params(precision="fp64", **prm), rho0, u, np.zeros(len(xy)))
+    st.step(50)
+    m = st.moments()
+    st.close()
+    mesh.close()
+    assert np.abs(m["rho"] - 0.55).max() <= 1e-13
+    assert np.abs(m["u"] - u).max() <= 1e-13
+    assert np.abs(m["p"] - m["p"].mean()).max() <= 1e-13
