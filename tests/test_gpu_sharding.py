@@ -153,3 +153,24 @@ def test_slab_errors():
     finally:
         whole.close()
         gen.close()
+
+
+def test_slabs_with_fp64_laplacian_term_equal_whole_lattice_bitwise():
+    """FP32 slabs on the lattice kernel with the FP64 kappa lap rho term
+    (FELBM_PARAM_LAP_FP64) reproduce the whole lattice's run with it."""
+    nx, ny = 96, 64
+    xy, tri, box, tag, rho0, u0, p0, prm = droplet(nx, ny, "fp32")
+    params = felbm.make_params(precision="fp32", lap_fp64=True, **prm)
+    mesh = felbm.Mesh(xy, tri, box, tag)
+    st = felbm.State(mesh, params, rho0, u0, p0)
+    st.step(10)
+    whole = (st.moments(), st.export())
+    st.close()
+    mesh.close()
+    run = sharding.SlabRun(xy, tri, box, tag, nx, ny, params, rho0, u0, p0, rows=sharding.slab_rows(ny, 2))
+    try:
+        run.step(10)
+        part = (run.moments(), run.export())
+    finally:
+        run.close()
+    assert_bitwise(part, whole)
