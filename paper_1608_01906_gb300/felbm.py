@@ -162,6 +162,24 @@ def _check(st, where):
         raise FelbmError(st, where)
 
 
+def _rows_of(a, n, cols):
+    """Whether host array a holds n rows of cols values, as an (n, cols)
+    array or flat (None passes)."""
+    if a is None:
+        return True
+    if a.ndim == 1:
+        return a.shape[0] == n * cols
+    return a.ndim == 2 and a.shape == (n, cols)
+
+
+def _mesh_arrays_ok(x, cells, box, tag, dim):
+    # the C side takes the node and cell counts from the caller and reads
+    # dim values per node and dim + 1 per cell: arrays of another shape
+    # would be read past their end
+    return (x.ndim == 2 and x.shape[1] == dim and cells.ndim == 2 and cells.shape[1] == dim + 1 and
+            box.size >= dim and _rows_of(tag, len(x), 1))
+
+
 def status_string(st: int) -> str:
     return load().felbm_status_string(int(st)).decode()
 
@@ -178,6 +196,8 @@ def felbm_mesh_create(xy, tri, box, flags, node_tag=None, stream=None):
     box = np.ascontiguousarray(box, dtype=np.float64)
     tag = None if node_tag is None else np.ascontiguousarray(node_tag, dtype=np.uint8)
     out = C.c_void_p()
+    if not _mesh_arrays_ok(xy, tri, box, tag, 2):
+        return FELBM_ERR_INVALID_ARG, out
     st = lib.felbm_mesh_create(_p(xy), len(xy), _p(tri), len(tri), _p(box), int(flags), _p(tag),
                                C.c_void_p(stream) if stream else None, C.byref(out))
     return st, out
@@ -190,6 +210,8 @@ def felbm_mesh_create_tet(xyz, tet, box, flags, node_tag=None, stream=None):
     box = np.ascontiguousarray(box, dtype=np.float64)
     tag = None if node_tag is None else np.ascontiguousarray(node_tag, dtype=np.uint8)
     out = C.c_void_p()
+    if not _mesh_arrays_ok(xyz, tet, box, tag, 3):
+        return FELBM_ERR_INVALID_ARG, out
     st = lib.felbm_mesh_create_tet(_p(xyz), len(xyz), _p(tet), len(tet), _p(box), flags, _p(tag),
                                    stream, C.byref(out))
     return st, out
@@ -201,6 +223,14 @@ def felbm_state_init(mesh, params: felbm_params, rho0, u0=None, p0=None):
     u0 = None if u0 is None else np.ascontiguousarray(u0, dtype=np.float64)
     p0 = None if p0 is None else np.ascontiguousarray(p0, dtype=np.float64)
     out = C.c_void_p()
+    # the C side reads n_nodes values of rho0 and p0 and n_nodes x dim of u0
+    n, kind = C.c_int64(), C.c_int32()
+    st = lib.felbm_mesh_info(mesh, C.byref(n), None, C.byref(kind), None)
+    if st != FELBM_OK:
+        return st, out
+    dim = 3 if kind.value in (2, 3) else 2
+    if not (_rows_of(rho0, n.value, 1) and _rows_of(u0, n.value, dim) and _rows_of(p0, n.value, 1)):
+        return FELBM_ERR_INVALID_ARG, out
     st = lib.felbm_state_init(mesh, C.byref(params), _p(rho0), _p(u0), _p(p0), C.byref(out))
     return st, out
 
@@ -383,6 +413,8 @@ class State:
     def import_(self, h, g):
         h = np.ascontiguousarray(h, dtype=np.float64)
         g = np.ascontiguousarray(g, dtype=np.float64)
+        if not (_rows_of(h, self.mesh.q, self.n) and _rows_of(g, self.mesh.q, self.n)):
+            raise FelbmError(FELBM_ERR_INVALID_ARG, "felbm_state_import: h and g must be (q, n_nodes)")
         _check(felbm_state_import(self.handle, h, g), "felbm_state_import")
 
     def profile_enable(self, on=True):

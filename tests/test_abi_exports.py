@@ -3,6 +3,8 @@ point declared in include/felbm.h."""
 import os
 import re
 
+import pytest
+
 from paper_1608_01906_gb300 import build, felbm
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -128,3 +130,35 @@ def test_triangle_mesh_conformity_needs_no_gpu():
     over[1] = [a, b, over[1][2]]                                        # [(0,0),(1,0),(0,1)]
     assert status(sx, over, sbox, stag) == bad                          # overlap, same orientation
     assert status(sx, np.delete(stri, 1, axis=0), sbox, stag) == bad     # hole next to a wall
+
+
+def test_binding_rejects_misshaped_host_arrays_without_gpu():
+    """The C side takes node and cell counts from the caller and reads a
+    fixed number of values per node and per cell; the binding refuses
+    arrays of another shape (INVALID_ARG) before the call, so no read runs
+    past a numpy buffer."""
+    import numpy as np
+
+    from paper_1608_01906_gb300 import inputs
+
+    felbm.load()
+    xy, tri, box, tag = inputs.structured_mesh(6, 5, periodic_y=False)
+    flags = felbm.flags_for(box)
+    cases = [
+        (np.hstack([xy, np.zeros((len(xy), 1))]), tri, box, tag),  # 3 coordinates per node
+        (xy, np.hstack([tri, tri[:, :1]]), box, tag),               # 4 vertices per triangle
+        (xy, tri, box[:1], tag),                                     # one box length
+        (xy, tri, box, tag[:-1]),                                    # one tag short
+        (xy.ravel(), tri, box, tag),                                 # flat coordinates
+    ]
+    for x, t, b, g in cases:
+        st, h = felbm.felbm_mesh_create(x, t, b, flags, g)
+        assert st == felbm.FELBM_ERR_INVALID_ARG and not h.value
+    with pytest.raises(felbm.FelbmError) as exc:
+        felbm.Mesh(xy, tri, box, tag[:-1])
+    assert exc.value.status == felbm.FELBM_ERR_INVALID_ARG
+    xyz, tet, box3, _ = inputs.structured_tet_mesh(4, 4, 4)
+    flags3 = felbm.FELBM_PERIODIC_X | felbm.FELBM_PERIODIC_Y | felbm.FELBM_PERIODIC_Z
+    for x, t, b in ((xyz[:, :2], tet, box3), (xyz, tet[:, :3], box3), (xyz, tet, box3[:2])):
+        st, h = felbm.felbm_mesh_create_tet(x, t, b, flags3)
+        assert st == felbm.FELBM_ERR_INVALID_ARG and not h.value
