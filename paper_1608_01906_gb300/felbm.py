@@ -180,6 +180,22 @@ def _mesh_arrays_ok(x, cells, box, tag, dim):
             box.size >= dim and _rows_of(tag, len(x), 1))
 
 
+# (n_nodes, dim) of each live state created through felbm_state_init: the
+# sizes its host-array calls read and write
+_STATE_SHAPES = {}
+
+
+def _hv(h):
+    return h.value if isinstance(h, C.c_void_p) else h
+
+
+def _f64_rows(a, n, cols):
+    """Whether a is a C-contiguous float64 host array of n rows of cols
+    values (None passes): the C side writes doubles into it."""
+    return a is None or (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous and
+                         _rows_of(a, n, cols))
+
+
 def status_string(st: int) -> str:
     return load().felbm_status_string(int(st)).decode()
 
@@ -232,6 +248,8 @@ def felbm_state_init(mesh, params: felbm_params, rho0, u0=None, p0=None):
     if not (_rows_of(rho0, n.value, 1) and _rows_of(u0, n.value, dim) and _rows_of(p0, n.value, 1)):
         return FELBM_ERR_INVALID_ARG, out
     st = lib.felbm_state_init(mesh, C.byref(params), _p(rho0), _p(u0), _p(p0), C.byref(out))
+    if st == FELBM_OK:
+        _STATE_SHAPES[out.value] = (n.value, dim)
     return st, out
 
 
@@ -244,15 +262,38 @@ def felbm_state_sync(state):
 
 
 def felbm_moments_get(state, rho=None, Cf=None, u=None, p=None, totals=None):
-    return load().felbm_moments_get(state, _p(rho), _p(Cf), _p(u), _p(p), _p(totals))
+    lib = load()
+    shp = _STATE_SHAPES.get(_hv(state))
+    if shp is not None:
+        n, d = shp
+        if not (_f64_rows(rho, n, 1) and _f64_rows(Cf, n, 1) and _f64_rows(u, n, d) and _f64_rows(p, n, 1) and
+                _f64_rows(totals, 1 + d, 1)):
+            return FELBM_ERR_INVALID_ARG
+    return lib.felbm_moments_get(state, _p(rho), _p(Cf), _p(u), _p(p), _p(totals))
+
+
+def _pops_ok(state, hbar, gbar, need):
+    # q x n_nodes doubles each (q = 9 on triangles, 19 on tetrahedra)
+    shp = _STATE_SHAPES.get(_hv(state))
+    if shp is None:
+        return True
+    n, d = shp
+    q = 19 if d == 3 else 9
+    return all(need(a, q, n) for a in (hbar, gbar))
 
 
 def felbm_state_export(state, hbar, gbar):
-    return load().felbm_state_export(state, _p(hbar), _p(gbar))
+    lib = load()
+    if not _pops_ok(state, hbar, gbar, _f64_rows):
+        return FELBM_ERR_INVALID_ARG
+    return lib.felbm_state_export(state, _p(hbar), _p(gbar))
 
 
 def felbm_state_import(state, hbar, gbar):
-    return load().felbm_state_import(state, _p(hbar), _p(gbar))
+    lib = load()
+    if not _pops_ok(state, hbar, gbar, _f64_rows):
+        return FELBM_ERR_INVALID_ARG
+    return lib.felbm_state_import(state, _p(hbar), _p(gbar))
 
 
 def felbm_alu_peak(kind):
@@ -435,6 +476,7 @@ class State:
 
     def close(self):
         if getattr(self, "handle", None):
+            _STATE_SHAPES.pop(_hv(self.handle), None)
             load().felbm_state_destroy(self.handle)
             self.handle = None
 
